@@ -1,0 +1,170 @@
+"""Seeded synthetic quaternion inputs, shared by the tests, the benchmark and
+the oracle's callers.  This module holds no arithmetic of the pseudoinverse
+method itself: only random draws and the construction of test matrices with a
+prescribed singular value decomposition.
+
+Conventions
+-----------
+* A quaternion matrix is a ``(4, rows, cols)`` float64 array of real component
+  planes (s, x, y, z), each row-major.
+* Random numbers come from a counter-based splitmix64 stream: draw ``c`` of
+  stream ``seed`` is ``splitmix64(seed + (c + 1) * 0x9E3779B97F4A7C15)``;
+  uniforms take the top 53 bits; normals are Box-Muller pairs.  Draw order for
+  a Gaussian quaternion matrix is plane s, x, y, z, each row-major.
+* Matrices with a prescribed spectrum are built through the interleaved
+  complex representation chi(q) = [[s + x i, y + z i], [-y + z i, s - x i]]
+  (a *-homomorphism from quaternions to 2x2 complex matrices, Sec. 2).
+  Orthonormal quaternion factors come from CholeskyQR2 of Gaussian quaternion
+  matrices in that representation: the complex Cholesky factor of chi(G^H G)
+  is chi(L) of the quaternion Cholesky factor L (unique, positive real
+  diagonal), so Q = G L^{-H} is the Q factor of a quaternion QR with positive
+  real diagonal in R (Haar distributed).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Draws offset .. offset+count-1 of the splitmix64 stream `seed` (uint64)."""
+    c = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + c * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) with 53 random bits."""
+    return (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Standard normals by Box-Muller; normal t uses uniforms 2*(t//2), 2*(t//2)+1."""
+    pairs = (count + 1) // 2
+    u = uniform(seed, 2 * pairs, 2 * ((offset + 1) // 2) if offset else 0)
+    u1, u2 = u[0::2], u[1::2]
+    r = np.sqrt(-2.0 * np.log1p(-u1))
+    g = np.empty(2 * pairs)
+    g[0::2] = r * np.cos(2.0 * math.pi * u2)
+    g[1::2] = r * np.sin(2.0 * math.pi * u2)
+    return g[:count]
+
+
+def gaussian_quaternion(m: int, n: int, seed: int) -> np.ndarray:
+    """(4, m, n) planes, every component i.i.d. N(0, 1)."""
+    return normal(seed, 4 * m * n).reshape(4, m, n)
+
+
+# ---------------------------------------------------------------- chi tools
+
+def chi(Q: np.ndarray) -> np.ndarray:
+    """Interleaved complex representation, (4, m, n) -> (2m, 2n) complex128."""
+    s, x, y, z = Q
+    m, n = s.shape
+    C = np.empty((2 * m, 2 * n), dtype=np.complex128)
+    C[0::2, 0::2] = s + 1j * x
+    C[0::2, 1::2] = y + 1j * z
+    C[1::2, 0::2] = -y + 1j * z
+    C[1::2, 1::2] = s - 1j * x
+    return C
+
+
+def unchi(C) -> np.ndarray:
+    """Inverse of chi (reads the first row of every 2x2 block)."""
+    C = np.asarray(C)
+    a = C[0::2, 0::2]
+    b = C[0::2, 1::2]
+    return np.ascontiguousarray(np.stack([a.real, a.imag, b.real, b.imag]))
+
+
+def _torch_device(device):
+    import torch  # local import: numpy-only callers never need torch
+    return torch, torch.device(device)
+
+
+def _cholqr_chi(C, device):
+    """Q factor (in chi form) of CholeskyQR2 applied to chi-form C."""
+    torch, dev = _torch_device(device)
+    Ct = torch.as_tensor(C, device=dev)
+    for _ in range(2):
+        H = Ct.mH @ Ct
+        H = 0.5 * (H + H.mH)
+        L = torch.linalg.cholesky(H)
+        # Q = C L^{-H}  <=>  Q^H = L^{-1} C^H
+        Ct = torch.linalg.solve_triangular(L, Ct.mH, upper=False).mH
+    return Ct
+
+
+def orthonormal_columns(m: int, r: int, seed: int, device="cpu") -> np.ndarray:
+    """(4, m, r) quaternion matrix with orthonormal columns (Haar for m == r)."""
+    G = gaussian_quaternion(m, r, seed)
+    return unchi(_cholqr_chi(chi(G), device).resolve_conj().cpu().numpy())
+
+
+def with_spectrum(U: np.ndarray, sigma: np.ndarray, V: np.ndarray, device="cpu") -> np.ndarray:
+    """A = U diag(sigma) V^H for U (4,m,r), V (4,n,r), sigma (r,)."""
+    torch, dev = _torch_device(device)
+    cu = torch.as_tensor(chi(U), device=dev)
+    cv = torch.as_tensor(chi(V), device=dev)
+    s2 = torch.as_tensor(np.repeat(np.asarray(sigma, dtype=np.float64), 2), device=dev)
+    return unchi(((cu * s2[None, :]) @ cv.mH).resolve_conj().cpu().numpy())
+
+
+# ------------------------------------------------------------ workloads
+
+def dense_gaussian(m: int = 64, n: int = 48, seed: int = 0) -> np.ndarray:
+    """Dense Gaussian workload: every component i.i.d. N(0,1) (full rank a.s.)."""
+    return gaussian_quaternion(m, n, seed)
+
+
+def logspaced_square(n: int = 2048, smin: float = 1e-6, seed_u: int = 1, seed_v: int = 2,
+                     device="cpu"):
+    """Square A = U diag(sigma) V^H, U, V Haar quaternion unitaries, sigma
+    log-spaced from 1 down to smin.  Returns (A, U, sigma, V)."""
+    sigma = np.logspace(0.0, math.log10(smin), n) if n > 1 else np.ones(1)
+    U = orthonormal_columns(n, n, seed_u, device)
+    V = orthonormal_columns(n, n, seed_v, device)
+    return with_spectrum(U, sigma, V, device), U, sigma, V
+
+
+def rank_deficient(m: int = 8192, n: int = 4096, r: int = 2048, smin: float = 1e-4,
+                   seed_l: int = 4, seed_r: int = 5, device="cpu"):
+    """Rank-r A = QL diag(sigma) QR^H with orthonormal Gaussian-derived factors
+    and sigma geometric from 1 to smin.  Returns (A, QL, sigma, QR)."""
+    sigma = np.geomspace(1.0, smin, r) if r > 1 else np.ones(1)
+    QL = orthonormal_columns(m, r, seed_l, device)
+    QR = orthonormal_columns(n, r, seed_r, device)
+    return with_spectrum(QL, sigma, QR, device), QL, sigma, QR
+
+
+def pure_quaternion_batch(count: int = 4096, seed: int = 3, lo: int = 16, hi: int = 256,
+                          rmin: int = 4):
+    """Batch of pure-quaternion matrices A = B W (zero real part): B is m x r
+    with i/j/k components uniform in [0, 1], W is r x n real with Dirichlet(1)
+    columns, so entries stay in [0, 1] and rank(A) = r almost surely.
+    m, n ~ U{lo..hi}, r ~ U{rmin..min(m, n)}.  Matrix b uses stream
+    (seed, draws from offset b * 2**32)."""
+    mats = []
+    for b in range(count):
+        off = b << 32
+        u = uniform(seed, 3, off)
+        m = lo + int(u[0] * (hi - lo + 1))
+        n = lo + int(u[1] * (hi - lo + 1))
+        rhi = min(m, n)
+        r = rmin + int(u[2] * (rhi - rmin + 1))
+        Bx = uniform(seed, 3 * m * r, off + 3).reshape(3, m, r)
+        e = -np.log1p(-uniform(seed, r * n, off + 3 + 3 * m * r)).reshape(r, n)
+        W = e / e.sum(axis=0, keepdims=True)
+        A = np.zeros((4, m, n))
+        A[1:] = Bx @ W
+        mats.append(A)
+    return mats

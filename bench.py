@@ -1,0 +1,287 @@
+"""Benchmark: quaternion pseudoinverse solves per second on one GB300.
+
+Workload (one "step"): a full qpinv_solve of a square 2048 x 2048 quaternion
+matrix A = U diag(sigma) V^H (U, V Haar quaternion unitaries, sigma
+log-spaced from 1 to 1e-6) with QHPI19 in mixed precision: BF16-split
+tensor-core products with FP32 accumulation, then FP64-residual polish
+iterations, then the four Penrose residuals in FP64.  Inputs are resident in
+HBM; A alone (134 MB of FP64 planes) exceeds the 129 MB L2, and every step
+streams several times that through HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
+timed on the host cores on a bounded sample of the same workload (rank 0
+only; other ranks exit 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pinv solves/s & quaternion-GEMM TFLOP/s (% TC peak) to rel. Penrose res <=1e-10"
+# Quaternion GEMMs of the workload's QHPI19 solve that the CPU-baseline
+# sample extrapolates to: iterations x 7 products + 4 Penrose products.  The
+# iteration count is the one the GPU arm reports for this workload
+# ("iters" in its JSON line).
+WORKLOAD_ITERS = 13
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p.get("bf16_tflops", 1900.0), p.get("bf16_tflops_sustained", 1700.0), p.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(n, device):
+    from paper_2605_01464_gb300 import inputs
+    A, U, s, V = inputs.logspaced_square(n, 1e-6, seed_u=1, seed_v=2, device=device)
+    return A
+
+
+def cpu_baseline_sample(A, iters, budget_s=30.0):
+    """Times one QHPI19 iteration (7 quaternion GEMMs) of the FP64 oracle on
+    the full-size input and extrapolates to a full solve of `iters`
+    iterations plus the 4 Penrose products."""
+    import numpy as np
+
+    import oracle
+
+    m, n = A.shape[1], A.shape[2]
+    X0 = oracle.init_x0(A, oracle.alpha(A, "safe"))
+    t0 = time.perf_counter()
+    oracle.step(A, X0, "qhpi19")
+    t_iter = time.perf_counter() - t0
+    gemm_count = 7 * iters + 4
+    t_solve = t_iter * gemm_count / 7.0
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one QHPI19 iteration (7 quaternion GEMMs, %dx%d, FP64 oracle, %.1f s) extrapolated by "
+                      "quaternion-GEMM count to %d iterations + 4 Penrose products" % (m, n, t_iter, iters),
+            "sample_seconds": t_iter}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    from oracle import build as obuild
+    obuild.build()
+    A = make_workload(args.n, "cpu")
+    steps = []
+    for k in range(args.warmup + args.steps):
+        s = cpu_baseline_sample(A, WORKLOAD_ITERS)
+        if k >= args.warmup:
+            steps.append(s["sample_seconds"])
+    t_iter = statistics.mean(steps)
+    t_solve = t_iter * (7 * WORKLOAD_ITERS + 4) / 7.0
+    value = 1.0 / t_solve
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "each step: one QHPI19 iteration (7 quaternion GEMMs) of the FP64 oracle "
+                                       "on the full %dx%d input, extrapolated to %d iterations + 4 Penrose "
+                                       "products" % (args.n, args.n, WORKLOAD_ITERS)},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": "square %dx%d quaternion A = U diag(sigma) V^H, Haar U and V, sigma log-spaced 1..1e-6; "
+                        "%s, mixed precision (BF16x6 tensor cores, %d FP64-residual polish iterations), "
+                        "safe fixed alpha, rel. tol %g, FP64 Penrose residuals" %
+                        (args.n, args.n, args.method.upper(), args.polish, args.tol),
+            "m": args.n, "n": args.n, "method": args.method, "precision": "mixed",
+            "l2": "inputs exceed L2 (A alone is 134 MB of FP64 planes; no flush)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--method", default="qhpi19", choices=["ns", "qsai", "qrapid", "qhpi19"])
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--polish", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2605_01464_gb300 import build as libbuild
+    from paper_2605_01464_gb300 import qpinv
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    A_host = make_workload(args.n, "cuda:%d" % local)
+    A = torch.from_numpy(A_host).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = qpinv.Context(local, precision="mixed", polish_iters=args.polish, profile=True)
+    for _ in range(args.warmup):
+        X, info = ctx.solve(A, args.method, tol=args.tol, max_iter=200, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.reset_stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            X, info = ctx.solve(A, args.method, tol=args.tol, max_iter=200, stream=stream)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = ctx.stats()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # end to end: host (pinned) A in, host X out, through the same C-ABI call
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A_host).pin_memory()
+        Xh = torch.empty((4, args.n, args.n), dtype=torch.float64).pin_memory()
+        ctx.configure(profile=False)
+        ctx.solve(Ah, args.method, tol=args.tol, max_iter=200, X=Xh, stream=stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, info_h = ctx.solve(Ah, args.method, tol=args.tol, max_iter=200, X=Xh, stream=stream)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        nbytes = 4 * args.n * args.n * 8
+        e2e = {"value": world * args.steps / te, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + 8 * 4 * 3}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    bf16_burst, bf16_sust, hbm, src = peaks()
+    tc_launch_ms = st["tc_gemm_ms"] / max(st["tc_gemm_launches"], 1)
+    tc_alg = st["tc_gemm_flops"] / max(st["tc_gemm_launches"], 1)
+    tc_iss = st["tc_gemm_flops_issued"] / max(st["tc_gemm_launches"], 1)
+    achieved = tc_alg / (tc_launch_ms * 1e-3) / 1e12 if tc_launch_ms > 0 else 0.0
+    issued = tc_iss / (tc_launch_ms * 1e-3) / 1e12 if tc_launch_ms > 0 else 0.0
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x6-split f32-acc + f64 residuals", "data": "synthetic",
+        "config": workload_config(args),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                     "frac": achieved / bf16_sust, "traffic": None,
+                     "kernel": "k_qgemm_tc (tcgen05 quaternion GEMM)",
+                     "achieved_issued": issued, "frac_issued": issued / bf16_sust,
+                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src},
+        "gpu_launches": st["kernel_launches"],
+        "kernel_time_ms": {"tc_gemm": st["tc_gemm_ms"], "f64_gemm": st["f64_gemm_ms"], "elementwise": st["ew_ms"]},
+        "result": {"iters": last["iters"], "tc_iters": last["tc_iters"], "polish_iters": last["polish_iters"],
+                   "status": last["status"], "E_rel": last["E_rel"], "alpha": last["alpha"]},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(A_host, last["iters"])
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

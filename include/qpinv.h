@@ -1,0 +1,203 @@
+/*
+ * qpinv.h -- C ABI of the GB300 (sm_103a) quaternion pseudoinverse library.
+ *
+ * The library computes X ~ A^dagger, the Moore-Penrose pseudoinverse of an
+ * m x n quaternion matrix A (Definition 2.1: AXA = A, XAX = X, (AX)^H = AX,
+ * (XA)^H = XA), with the hyperpower iterations of the paper: QRAPID
+ * (Algorithm 1), QSAI (Algorithm 2), QHPI19 (Algorithm 3, factorized
+ * order-19 form of Sec. 3.3) and the Newton-Schulz baseline
+ * X_{j+1} = X_j (2I - A X_j) (Sec. 1).  Every iteration starts from
+ * X_0 = alpha A^H (Theorem 1) and is dominated by quaternion matrix-matrix
+ * products, which run in the library's own CUDA kernels.
+ *
+ * Data layout (every entry point): a quaternion matrix is passed as four
+ * real component planes s, x, y, z (q = s + x i + y j + z k, Sec. 2), each a
+ * row-major array of doubles with a leading dimension (elements between
+ * consecutive rows).  A is m x n with leading dimension lda >= n; X is n x m
+ * with leading dimension ldx >= m.  Plane pointers may be device pointers
+ * (cudaMalloc / torch CUDA tensors) or host pointers (pageable or pinned);
+ * the library detects which with cudaPointerGetAttributes and, for host
+ * pointers, copies through device buffers it owns, inside the call.
+ *
+ * Ownership: the caller owns A and X and every array passed in.  The
+ * context owns all scratch memory (residual powers, polynomial blocks,
+ * tensor-core operand splits, reduction partials), grown on demand and
+ * released by qpinv_free.  The library never frees caller memory.
+ *
+ * Errors: every int-returning entry point returns QPINV_OK (0) or a
+ * negative QPINV_E_* code; qpinv_last_error(ctx) gives a message.  Solver
+ * outcomes (converged, plateau, not converged, diverged) are not errors:
+ * they are reported in qpinv_result.status, and X is always written.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Calls are synchronous with respect to the host: they
+ * return after the result has been read back (the stop test needs two
+ * scalars per iteration).
+ */
+#ifndef QPINV_H
+#define QPINV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define QPINV_OK 0
+#define QPINV_E_INVALID (-1)      /* bad size, leading dimension, pointer or option */
+#define QPINV_E_CUDA (-2)         /* a CUDA runtime/driver call failed */
+#define QPINV_E_NOMEM (-3)        /* device workspace could not be allocated */
+#define QPINV_E_NONFINITE (-4)    /* A contains NaN or Inf */
+#define QPINV_E_TIMEOUT (-5)      /* a device-side bounded wait expired (kernel aborted cleanly) */
+#define QPINV_E_UNSUPPORTED (-6)  /* option combination not available on this device */
+
+/* ---- solver outcome (qpinv_result.status) ----------------------------- */
+#define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
+#define QPINV_PLATEAU 1       /* relative step stopped decreasing below 1e-6; X is the iterate before that step */
+#define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
+#define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
+
+/* ---- methods ----------------------------------------------------------- */
+typedef enum {
+  QPINV_NS = 0,     /* Newton-Schulz, order 2, 2 products per iteration (Sec. 1) */
+  QPINV_QSAI = 1,   /* Algorithm 2, order 10, 6 products per iteration */
+  QPINV_QRAPID = 2, /* Algorithm 1 with step parameter N, 8+2N products per iteration */
+  QPINV_QHPI19 = 3  /* Algorithm 3, order 19, 7 products per iteration */
+} qpinv_method;
+
+/* ---- options --------------------------------------------------------- */
+enum {
+  QPINV_PREC_FP64 = 0,  /* every product in FP64 on the CUDA cores */
+  QPINV_PREC_MIXED = 1, /* tensor-core BF16-split products with FP32 accumulation, then
+                           polish iterations whose residual R = I - A X and update X t are
+                           FP64-accurate (QPINV_PREC_EMU products) */
+  QPINV_PREC_TC = 2,    /* tensor-core products only (FP32-level output) */
+  QPINV_PREC_EMU = 3    /* every product FP64-accurate on the tensor cores: exact 7-bit slices
+                           per operand (power-of-two row and column scaling; 8 slices in a
+                           solve, `split_level` = 2..8 in qpinv_qgemm), K-chunked so every FP32
+                           partial sum is exact, accumulated in 64-bit fixed point.  Use it for
+                           rank-deficient A, whose null-space rounding noise the iteration
+                           multiplies by its order each step */
+};
+enum { QPINV_ALPHA_SAFE = 0,     /* 1 / (||A||_1 ||A||_inf), entry moduli; always < 2/sigma_1^2 */
+       QPINV_ALPHA_SPECTRAL = 1, /* 1 / sigma_1^2 (Algorithms 1-3), sigma_1 by power iteration */
+       QPINV_ALPHA_FRO = 2,      /* 1 / ||A||_F^2 (Sec. 4 text) */
+       QPINV_ALPHA_USER = 3,     /* alpha_user (Example 3 uses a fixed alpha) */
+       QPINV_ALPHA_LEARNED = 4   /* MLP on sketched features; falls back to SAFE on a failed check */ };
+enum { QPINV_SIDE_AUTO = 0,  /* residual on the smaller side */
+       QPINV_SIDE_RIGHT = 1, /* paper's form: R = I_m - A X, X_{j+1} = X p(R) */
+       QPINV_SIDE_LEFT = 2   /* R = I_n - X A, X_{j+1} = p(R) X (same iterates in exact arithmetic) */ };
+enum { QPINV_STOP_PAPER_ABS = 0,  /* ||X_{j+1} - X_j||_F < tol (Algorithms 1-3) */
+       QPINV_STOP_REL_PLATEAU = 1 /* ||X_{j+1}-X_j||_F / ||X_{j+1}||_F <= tol, with plateau detection */ };
+
+typedef struct {
+  int precision;     /* QPINV_PREC_FP64, _MIXED, _TC or _EMU; default MIXED */
+  int split_level;   /* tensor-core operand terms: 1 = bf16, 2 = bf16x3, 3 = bf16x6; 0 = automatic (default) */
+  int polish_iters;  /* MIXED: iterations with an FP64 residual at the end (default 2) */
+  int alpha_mode;    /* QPINV_ALPHA_*, default SAFE */
+  double alpha_user; /* used with QPINV_ALPHA_USER */
+  int qrapid_N;      /* QRAPID step parameter N >= 0 (default 5) */
+  int side;          /* QPINV_SIDE_*, default AUTO; a residual forced onto the larger side runs
+                        MIXED / TC solves as QPINV_PREC_EMU (its complement behaves like a
+                        rank-deficient residual) */
+  int stop_rule;     /* QPINV_STOP_*, default REL_PLATEAU */
+  int penrose;       /* 1: compute E1..E4 in FP64 after the solve (default 1) */
+  int profile;       /* 1: time every kernel launch with CUDA events (qpinv_get_stats) */
+} qpinv_options;
+
+typedef struct {
+  int status;        /* QPINV_CONVERGED / _PLATEAU / _NOT_CONVERGED / _DIVERGED */
+  int iters;         /* X-updates contained in the returned X */
+  int tc_iters;      /* ... of which with tensor-core residuals */
+  int polish_iters;  /* ... of which with an FP64 residual */
+  double alpha;      /* scaling used in X_0 = alpha A^H */
+  int alpha_source;  /* QPINV_ALPHA_* actually used */
+  int side;          /* QPINV_SIDE_RIGHT or QPINV_SIDE_LEFT actually used */
+  double delta;      /* ||X_{j+1} - X_j||_F of the last computed step */
+  double delta_rel;  /* delta / ||X_{j+1}||_F */
+  double E[4];       /* Sec. 4: ||AXA-A||_F, ||XAX-X||_F, ||(AX)^H-AX||_F, ||(XA)^H-XA||_F */
+  double E_rel[4];   /* E divided by ||A||_F, ||X||_F, ||AX||_F, ||XA||_F */
+  long long gemms;   /* quaternion matrix products issued */
+  double time_ms;    /* wall time of the call */
+} qpinv_result;
+
+typedef struct {
+  long long kernel_launches;  /* every kernel of this library launched since the last reset */
+  long long tc_gemm_launches; /* tcgen05 quaternion GEMM launches */
+  double tc_gemm_ms;          /* their summed duration (CUDA events on the launch stream; profile=1) */
+  double tc_gemm_flops;       /* algorithmic real flops: 32 per quaternion multiply-add */
+  double tc_gemm_flops_issued;/* tensor-core flops issued (split products count each pass) */
+  long long f64_gemm_launches;
+  double f64_gemm_ms;
+  double f64_gemm_flops;
+  long long ew_launches;      /* fused elementwise / reduction kernels */
+  double ew_ms;
+  double ew_bytes;            /* algorithmic HBM bytes of those kernels */
+} qpinv_stats;
+
+typedef struct qpinv_ctx qpinv_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void qpinv_default_options(qpinv_options* opt);
+
+/* Creates a context bound to CUDA device `device` (the caller's current
+ * device is restored on return from every call).  opt may be NULL (defaults).
+ * *ctx receives the context; release it with qpinv_free. */
+int qpinv_init(qpinv_ctx** ctx, int device, const qpinv_options* opt);
+
+/* Replaces the options of an existing context. */
+int qpinv_set_options(qpinv_ctx* ctx, const qpinv_options* opt);
+
+/* Single solve (Algorithms 1-3 and Newton-Schulz; stop rules of Sec. 4 and
+ * the plateau rule).  A: four planes of an m x n matrix (lda >= n); X: four
+ * planes of the n x m output (ldx >= m), caller-owned.  tol: stop tolerance
+ * of the chosen rule; max_iter >= 1 bounds the X-updates.  out (host,
+ * may be NULL) receives the outcome.  Returns QPINV_E_NONFINITE if A holds
+ * NaN or Inf (X is then left untouched). */
+int qpinv_solve(qpinv_ctx* ctx, void* stream, int m, int n, const double* const A[4], long lda,
+                qpinv_method method, double tol, int max_iter, double* const X[4], long ldx,
+                qpinv_result* out);
+
+/* Batched solve of `batch` independent matrices of uneven shapes.  m[b],
+ * n[b] (host arrays): shape of matrix b, each in [1, 256]; A[4*b + c] and
+ * X[4*b + c] (host arrays of device pointers): plane c of matrix b, with
+ * leading dimensions lda[b] >= n[b] and ldx[b] >= m[b].  All matrices are
+ * solved in one persistent kernel launch with FP32 arithmetic (tensor-core
+ * products where the tile pays); out[b] (host array, may be NULL) receives
+ * each outcome (E1..E4 are computed in FP64).  Matrices are independent: a
+ * failure of one does not affect the others. */
+int qpinv_solve_batched(qpinv_ctx* ctx, void* stream, int batch, const int* m, const int* n,
+                        const double* const* A, const long* lda, qpinv_method method, double tol,
+                        int max_iter, double* const* X, const long* ldx, qpinv_result* out);
+
+/* Releases the context and all device memory it owns.  NULL is ignored. */
+void qpinv_free(qpinv_ctx* ctx);
+
+/* Message for the last error on this context (never NULL). */
+const char* qpinv_last_error(qpinv_ctx* ctx);
+
+/* ---- building blocks, exposed for tests and measurement ---------------- */
+
+/* C = A B for quaternion matrices (Hamilton product, Sec. 2): A is m x k
+ * (lda >= k), B is k x n (ldb >= n), C is m x n (ldc >= n), all four-plane
+ * FP64 arrays (device or host).  precision: QPINV_PREC_FP64 (CUDA-core FP64
+ * kernel), QPINV_PREC_TC (tcgen05 kernel on BF16 splits of A and B with
+ * `split_level` = 1..3 terms, FP32 accumulation) or QPINV_PREC_EMU (tcgen05,
+ * `split_level` = 2..8 exact slices, FP64-accurate for 8).  C must not alias A or B. */
+int qpinv_qgemm(qpinv_ctx* ctx, void* stream, int m, int k, int n, const double* const A[4],
+                long lda, const double* const B[4], long ldb, double* const C[4], long ldc,
+                int precision, int split_level);
+
+/* Penrose residuals of Sec. 4 for a given pair (A, X), computed in FP64:
+ * E[0..3] = ||AXA-A||_F, ||XAX-X||_F, ||(AX)^H-AX||_F, ||(XA)^H-XA||_F and
+ * E_rel = E / (||A||_F, ||X||_F, ||AX||_F, ||XA||_F).  E, E_rel: host arrays of 4. */
+int qpinv_penrose(qpinv_ctx* ctx, void* stream, int m, int n, const double* const A[4], long lda,
+                  const double* const X[4], long ldx, double* E, double* E_rel);
+
+/* Kernel counters and (with profile = 1) CUDA-event timings since the last reset. */
+int qpinv_get_stats(qpinv_ctx* ctx, qpinv_stats* stats);
+int qpinv_reset_stats(qpinv_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QPINV_H */

@@ -1,0 +1,129 @@
+// common.cuh -- internal types shared by the CUDA sources of libqpinv.
+//
+// A quaternion matrix lives in HBM as four real planes (s, x, y, z), the
+// layout of the C ABI.  Besides the FP64 "master" planes, a matrix that
+// feeds the tensor cores also carries BF16 split copies:
+//   A-form: row-major rows x cols (K-major when the matrix is the left
+//           operand, K = cols);
+//   B-form: the plane-wise transpose, cols x rows (K-major when the matrix
+//           is the right operand, K = rows).
+// Split level L stores L BF16 terms v = t0 + t1 + ... (each the BF16
+// rounding of the remainder), level-major then component-major.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qp {
+
+typedef __nv_bfloat16 bf16;
+
+// Row-major plane set: element (c, i, j) at p[c * ps + i * ld + j].
+template <typename T>
+struct Planes {
+  T* p = nullptr;
+  long ld = 0;  // elements between rows
+  long ps = 0;  // elements between component planes
+};
+
+// BF16 split forms of one matrix (either pointer may be null).
+struct Split16 {
+  bf16* a = nullptr;  // A-form [level][comp][rows][lda]
+  long lda = 0, psa = 0;
+  bf16* b = nullptr;  // B-form [level][comp][cols][ldb]
+  long ldb = 0, psb = 0;
+  int levels = 0;
+};
+
+// Output specification of the fused combine kernel:
+//   out = cacc * acc + sum_t caux[t] * aux_t + diag * I   (diag on plane s)
+// The master output (and every aux input) has the master type of the pass:
+// float (tensor-core phase) or double (FP64 phase).  BF16 outputs are either
+// round-to-nearest splits of the FP32 value (t0 = bf16(v), t1 = bf16(v - t0),
+// ...) or, when exp_a / exp_b are given, exact 7-bit slices of v * 2^-e
+// (e = exponent of the row (A-form) or column (B-form) maximum): slice s is
+// an integer in [-64, 64] ([-128, 128] for s = 0) times 2^(-7(s+1)), which
+// BF16 holds exactly.  Slicing is done in integer arithmetic.
+struct OutSpec {
+  void* mp = nullptr;  // master output planes (type of the pass), may be null
+  long mld = 0, mps = 0;
+  Split16 s16;         // BF16 outputs (a and/or b may be null)
+  const int* exp_a = nullptr;  // per-row exponents: exact slicing of the A-form
+  const int* exp_b = nullptr;  // per-column exponents: exact slicing of the B-form
+  double cacc = 0.0;
+  double caux[4] = {0, 0, 0, 0};
+  double diag = 0.0;
+};
+
+enum { ACC_F32 = 0, ACC_F64 = 1, ACC_I64 = 2 };
+
+constexpr int kMaxOut = 3;
+
+struct CombineArgs {
+  int rows = 0, cols = 0;
+  int f64 = 0;                // master type of aux inputs and outputs: 0 float, 1 double
+  const void* acc = nullptr;  // accumulator planes, may be null
+  int acc_kind = ACC_F32;     // ACC_I64: fixed point, value = acc * 2^(erow[i] + ecol[j] - shift)
+  long ld_acc = 0, ps_acc = 0;
+  const int* acc_erow = nullptr;
+  const int* acc_ecol = nullptr;
+  int acc_shift = 0;
+  const void* aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  long ld_aux[4] = {0, 0, 0, 0}, ps_aux[4] = {0, 0, 0, 0};
+  OutSpec out[kMaxOut];
+  int nout = 0;
+  double* partials = nullptr;  // per block: ||out0 - aux0||^2, ||out0||^2, non-finite count
+};
+
+}  // namespace qp
+
+// Host-side launch helpers implemented in elementwise.cu / qgemm_*.cu.
+namespace qp {
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_out);
+cudaError_t launch_reduce_partials(const double* partials, int nblocks, int nvals, double* out,
+                                   cudaStream_t st);
+cudaError_t launch_abs_sums(const Planes<const double>& A, int m, int n, double* rowsum,
+                            double* colsum, cudaStream_t st);
+cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st);
+cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m,
+                                 int n, double* partials, cudaStream_t st, int* blocks_out);
+cudaError_t launch_antiherm_partials(const Planes<const double>& M, int n, double* partials,
+                                     cudaStream_t st, int* blocks_out);
+cudaError_t launch_init_x0(const Planes<const double>& A, int m, int n, double alpha, const Planes<double>& X,
+                           cudaStream_t st);
+cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e,
+                              cudaStream_t st);
+cudaError_t launch_f64_to_f32(const Planes<const double>& src, int rows, int cols, const Planes<float>& dst,
+                              cudaStream_t st);
+cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e,
+                          cudaStream_t st);
+cudaError_t launch_f32_to_f64(const Planes<const float>& src, int rows, int cols,
+                              const Planes<double>& dst, cudaStream_t st);
+
+cudaError_t launch_qgemm_f64(int M, int K, int N, const Planes<const double>& A,
+                             const Planes<const double>& B, const Planes<double>& C,
+                             cudaStream_t st);
+
+// Tensor-core quaternion GEMM on BF16 split operands.  acc (FP32) = sum over
+// the listed (i, j) term pairs of A_i * B_j, restricted to k in [k0, k1).
+struct TcGemmArgs {
+  int M = 0, N = 0, K = 0;
+  // Output: FP32 store into C, or (C64 != null) int64 fixed-point
+  // accumulation C64 += rint(acc * 2^shift).
+  long long* C64 = nullptr;
+  long ld64 = 0, ps64 = 0;
+  int shift = 0;
+  int k0 = 0, k1 = 0;
+  const Split16* A = nullptr;  // uses the A-form
+  const Split16* B = nullptr;  // uses the B-form
+  int npairs = 0;
+  int pair_i[16] = {0}, pair_j[16] = {0};
+  Planes<float> C;  // FP32 output
+  int* err = nullptr;  // device error word (bounded-wait expiry)
+};
+cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);
+bool tc_supported();
+
+}  // namespace qp

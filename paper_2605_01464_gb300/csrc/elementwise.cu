@@ -1,0 +1,447 @@
+// elementwise.cu -- HBM-bound kernels of the solve: the fused combine pass
+// that follows every quaternion product (residual R = I - AX, polynomial
+// blocks, X update with the stop-test norms), BF16 operand splitting and
+// exact slicing with transposed copies, initialisation X_0 = alpha A^H, and
+// the norm and Penrose-residual reductions.
+//
+// GB300's FP64 pipe is a small fraction of its FP32 rate, so the
+// tensor-core phase runs these passes on FP32 masters; only the FP64 phase
+// (polish, Penrose) uses double arithmetic, and exact slicing and exponent
+// extraction use integer operations on the bit patterns.  Reductions are
+// deterministic: each block writes partial sums and one block adds them in a
+// fixed order.
+#include "common.cuh"
+
+namespace qp {
+
+namespace {
+
+constexpr int TILE = 32;
+constexpr int TROWS = 8;  // block = 32 x 8 threads, each thread 4 rows of the tile
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) r += sh[w];
+  return r;  // valid in thread 0 only
+}
+
+// Round-to-nearest BF16 split of the FP32 value: 3 terms cover all 24 bits.
+__device__ __forceinline__ void split_store(bf16* base, long idx, long lstride, int levels, float v) {
+  float r = v;
+  for (int l = 0; l < levels; l++) {
+    const bf16 t = __float2bfloat16_rn(r);
+    base[l * lstride + idx] = t;
+    r -= __bfloat162float(t);
+  }
+}
+
+// round(v * 2^sh) as an integer, from the bits of v (integer arithmetic only).
+// Requires |v * 2^sh| < 2^62; subnormal inputs count as zero.
+__device__ __forceinline__ long long to_fixed(double v, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int k = ex - 1075 + sh;  // v * 2^sh = mant * 2^k
+  long long F;
+  if (k >= 0) F = mant << k;
+  else if (k <= -55) F = 0;
+  else F = (mant + (1ll << (-k - 1))) >> (-k);
+  return (b >> 63) ? -F : F;
+}
+__device__ __forceinline__ long long to_fixed(float v, int sh) {
+  const unsigned b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 0xFF);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0x7FFFFFu) | (1u << 23));
+  const int k = ex - 150 + sh;
+  long long F;
+  if (k >= 0) F = mant << k;
+  else if (k <= -26) F = 0;
+  else F = (mant + (1ll << (-k - 1))) >> (-k);
+  return (b >> 31) ? -F : F;
+}
+
+// Binary exponent e with |v| < 2^e (0 for zero / subnormal), from the bits.
+__device__ __forceinline__ int exp_of(double v) {
+  const int ex = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
+  return ex == 0 ? -100000 : ex - 1022;
+}
+__device__ __forceinline__ int exp_of(float v) {
+  const int ex = (int)((__float_as_uint(v) >> 23) & 0xFF);
+  return ex == 0 ? -100000 : ex - 126;
+}
+
+// Exact slices of v * 2^-e (|v| < 2^e): F = round(v * 2^(7S - e)) written in
+// balanced base 128, least significant digit first; slice s = digit_s * 2^-(7(s+1)).
+template <typename T>
+__device__ __forceinline__ void slice_store(bf16* base, long idx, long lstride, int S, T v, int e) {
+  long long F = to_fixed(v, 7 * S - e);
+  for (int l = S - 1; l >= 1; l--) {
+    int d = (int)(F & 127);
+    if (d >= 64) d -= 128;
+    F = (F - d) >> 7;
+    base[l * lstride + idx] = __float2bfloat16_rn(ldexpf((float)d, -7 * (l + 1)));
+  }
+  base[idx] = __float2bfloat16_rn(ldexpf((float)F, -7));
+}
+
+template <typename T>
+__device__ __forceinline__ T acc_value(const CombineArgs& a, int c, int i, int j) {
+  const long off = c * a.ps_acc + (long)i * a.ld_acc + j;
+  if (a.acc_kind == ACC_F64) return (T)((const double*)a.acc)[off];
+  if (a.acc_kind == ACC_I64) {
+    const long long q = ((const long long*)a.acc)[off];
+    const int e = a.acc_erow[i] + a.acc_ecol[j] - a.acc_shift;
+    if (sizeof(T) == 4) return (T)ldexpf((float)q, e);
+    return (T)ldexp((double)q, e);
+  }
+  return (T)((const float*)a.acc)[off];
+}
+
+// One 32x32 tile per block; threads (tx, ty), tid = ty * 32 + tx.
+template <typename T>
+__global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
+  __shared__ T stage[4][TILE][TILE + 1];
+  __shared__ double red[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;
+  T s_dx = 0, s_x = 0;
+  int s_bad = 0;
+
+  for (int o = 0; o < a.nout; o++) {
+    const OutSpec& O = a.out[o];
+    const T cacc = (T)O.cacc, diag = (T)O.diag;
+    for (int q = 0; q < TILE / TROWS; q++) {
+      const int i = r0 + ty + q * TROWS, j = c0 + tx;
+      T v[4] = {0, 0, 0, 0};
+      if (i < a.rows && j < a.cols) {
+        if (a.acc && O.cacc != 0.0)
+          for (int c = 0; c < 4; c++) v[c] = cacc * acc_value<T>(a, c, i, j);
+        for (int t = 0; t < 4; t++) {
+          if (!a.aux[t] || O.caux[t] == 0.0) continue;
+          const T* ap = (const T*)a.aux[t];
+          const T ct = (T)O.caux[t];
+          for (int c = 0; c < 4; c++) v[c] += ct * ap[c * a.ps_aux[t] + (long)i * a.ld_aux[t] + j];
+        }
+        if (i == j) v[0] += diag;
+        if (o == 0 && a.partials) {
+          const T* x0p = (const T*)a.aux[0];
+          for (int c = 0; c < 4; c++) {
+            const T x0 = x0p ? x0p[c * a.ps_aux[0] + (long)i * a.ld_aux[0] + j] : (T)0;
+            s_dx += (v[c] - x0) * (v[c] - x0);
+            s_x += v[c] * v[c];
+            s_bad += isfinite(v[c]) ? 0 : 1;
+          }
+        }
+        if (O.mp)
+          for (int c = 0; c < 4; c++) ((T*)O.mp)[c * O.mps + (long)i * O.mld + j] = v[c];
+        if (O.s16.a) {
+          for (int c = 0; c < 4; c++) {
+            const long idx = c * O.s16.psa + (long)i * O.s16.lda + j;
+            if (O.exp_a) slice_store<T>(O.s16.a, idx, 4 * O.s16.psa, O.s16.levels, v[c], O.exp_a[i]);
+            else split_store(O.s16.a, idx, 4 * O.s16.psa, O.s16.levels, (float)v[c]);
+          }
+        }
+      }
+      if (O.s16.b)
+        for (int c = 0; c < 4; c++) stage[c][ty + q * TROWS][tx] = v[c];
+    }
+    if (O.s16.b) {
+      __syncthreads();
+      for (int q = 0; q < TILE / TROWS; q++) {
+        const int jj = c0 + ty + q * TROWS, ii = r0 + tx;  // B-form element (jj, ii) = out(ii, jj)
+        if (ii < a.rows && jj < a.cols) {
+          for (int c = 0; c < 4; c++) {
+            const long idx = c * O.s16.psb + (long)jj * O.s16.ldb + ii;
+            const T val = stage[c][tx][ty + q * TROWS];
+            if (O.exp_b) slice_store<T>(O.s16.b, idx, 4 * O.s16.psb, O.s16.levels, val, O.exp_b[jj]);
+            else split_store(O.s16.b, idx, 4 * O.s16.psb, O.s16.levels, (float)val);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (a.partials) {
+    const long b = (long)blockIdx.y * gridDim.x + blockIdx.x;
+    const double t0 = block_sum((double)s_dx, red);
+    const double t1 = block_sum((double)s_x, red);
+    const double t2 = block_sum((double)s_bad, red);
+    if (threadIdx.x == 0) {
+      a.partials[3 * b + 0] = t0;
+      a.partials[3 * b + 1] = t1;
+      a.partials[3 * b + 2] = t2;
+    }
+  }
+}
+
+__global__ void k_reduce_partials(const double* p, int nblocks, int nvals, double* out) {
+  __shared__ double sh[8];
+  for (int v = 0; v < nvals; v++) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += p[(long)b * nvals + v];
+    const double t = block_sum(s, sh);
+    if (threadIdx.x == 0) out[v] = t;
+  }
+}
+
+__global__ void k_row_abs_sums(Planes<const double> A, int m, int n, double* rowsum) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    double q = 0.0;
+    for (int c = 0; c < 4; c++) {
+      const double x = A.p[c * A.ps + (long)warp * A.ld + j];
+      q += x * x;
+    }
+    s += sqrt(q);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) rowsum[warp] = s;
+}
+
+__global__ void k_col_abs_sums(Planes<const double> A, int m, int n, double* colsum) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < m; i++) {
+    double q = 0.0;
+    for (int c = 0; c < 4; c++) {
+      const double x = A.p[c * A.ps + (long)i * A.ld + j];
+      q += x * x;
+    }
+    s += sqrt(q);
+  }
+  colsum[j] = s;
+}
+
+__global__ void k_max(const double* v, int n, double* out) {
+  __shared__ double sh[256];
+  double mx = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) mx = fmax(mx, v[t]);
+  sh[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// partials per block: sum |A - B|^2 (or |A|^2 if B is null), non-finite count of A.
+__global__ void k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m, int n,
+                       double* partials) {
+  __shared__ double sh[8];
+  const long total = (long)m * n;
+  double s = 0.0, bad = 0.0;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long i = t / n, j = t % n;
+    for (int c = 0; c < 4; c++) {
+      double x = A.p[c * A.ps + i * A.ld + j];
+      bad += isfinite(x) ? 0.0 : 1.0;
+      if (hasB) x -= B.p[c * B.ps + i * B.ld + j];
+      s += x * x;
+    }
+  }
+  const double t0 = block_sum(s, sh);
+  const double t1 = block_sum(bad, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = t0;
+    partials[2 * blockIdx.x + 1] = t1;
+  }
+}
+
+// sum over (i, j) of |conj(M_ji) - M_ij|^2 for square M: ||M^H - M||_F^2.
+__global__ void __launch_bounds__(256) k_antiherm(Planes<const double> M, int n, double* partials) {
+  __shared__ double t[4][TILE][TILE + 1];
+  __shared__ double sh[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;
+  // load the mirrored tile M[c0.., r0..] transposed into shared memory
+  for (int q = 0; q < TILE / TROWS; q++) {
+    const int i = c0 + ty + q * TROWS, j = r0 + tx;
+    for (int c = 0; c < 4; c++)
+      t[c][tx][ty + q * TROWS] = (i < n && j < n) ? M.p[c * M.ps + (long)i * M.ld + j] : 0.0;
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < TILE / TROWS; q++) {
+    const int i = r0 + ty + q * TROWS, j = c0 + tx;
+    if (i < n && j < n) {
+      for (int c = 0; c < 4; c++) {
+        const double mij = M.p[c * M.ps + (long)i * M.ld + j];
+        const double mji = t[c][ty + q * TROWS][tx];  // M[j][i]
+        const double d = (c == 0 ? mji : -mji) - mij;
+        s += d * d;
+      }
+    }
+  }
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[(long)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// X (n x m) = alpha * A^H, A m x n: X[j][i] = alpha * conj(A[i][j]).
+__global__ void __launch_bounds__(256) k_init_x0(Planes<const double> A, int m, int n, double al,
+                                                 Planes<double> X) {
+  __shared__ double t[4][TILE][TILE + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;  // tile of A: rows r0.., cols c0..
+  for (int q = 0; q < TILE / TROWS; q++) {
+    const int i = r0 + ty + q * TROWS, j = c0 + tx;
+    for (int c = 0; c < 4; c++)
+      t[c][ty + q * TROWS][tx] = (i < m && j < n) ? A.p[c * A.ps + (long)i * A.ld + j] : 0.0;
+  }
+  __syncthreads();
+  for (int q = 0; q < TILE / TROWS; q++) {
+    const int j = c0 + ty + q * TROWS, i = r0 + tx;  // X element (j, i)
+    if (i < m && j < n)
+      for (int c = 0; c < 4; c++) {
+        const double v = t[c][tx][ty + q * TROWS];
+        X.p[c * X.ps + (long)j * X.ld + i] = al * (c == 0 ? v : -v);
+      }
+  }
+}
+
+// Exponent e with |v| < 2^e for every v of a row (A-operand scaling) or a
+// column (B-operand scaling), over all four planes; integer ops on the bits.
+template <typename T>
+__global__ void k_row_maxexp(Planes<const T> A, int rows, int cols, int* e) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  int mx = -100000;
+  for (int j = lane; j < cols; j += 32)
+    for (int c = 0; c < 4; c++) mx = max(mx, exp_of(A.p[c * A.ps + (long)warp * A.ld + j]));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) e[warp] = mx == -100000 ? 0 : mx;
+}
+
+template <typename T>
+__global__ void k_col_maxexp(Planes<const T> A, int rows, int cols, int* e) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cols) return;
+  int mx = -100000;
+  for (int i = 0; i < rows; i++)
+    for (int c = 0; c < 4; c++) mx = max(mx, exp_of(A.p[c * A.ps + (long)i * A.ld + j]));
+  e[j] = mx == -100000 ? 0 : mx;
+}
+
+__global__ void k_f32_to_f64(Planes<const float> S, int rows, int cols, Planes<double> D) {
+  const long total = (long)rows * cols;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long i = t / cols, j = t % cols;
+    for (int c = 0; c < 4; c++) D.p[c * D.ps + i * D.ld + j] = (double)S.p[c * S.ps + i * S.ld + j];
+  }
+}
+
+__global__ void k_f64_to_f32(Planes<const double> S, int rows, int cols, Planes<float> D) {
+  const long total = (long)rows * cols;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long i = t / cols, j = t % cols;
+    for (int c = 0; c < 4; c++) D.p[c * D.ps + i * D.ld + j] = (float)S.p[c * S.ps + i * S.ld + j];
+  }
+}
+
+int grid_for(long total) {
+  long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_out) {
+  dim3 grid((a.cols + TILE - 1) / TILE, (a.rows + TILE - 1) / TILE);
+  if (blocks_out) *blocks_out = grid.x * grid.y;
+  if (a.rows <= 0 || a.cols <= 0) return cudaSuccess;
+  if (a.f64)
+    k_combine<double><<<grid, TILE * TROWS, 0, st>>>(a);
+  else
+    k_combine<float><<<grid, TILE * TROWS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int nblocks, int nvals, double* out,
+                                   cudaStream_t st) {
+  k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, nvals, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_abs_sums(const Planes<const double>& A, int m, int n, double* rowsum, double* colsum,
+                            cudaStream_t st) {
+  k_row_abs_sums<<<(m + 7) / 8, 256, 0, st>>>(A, m, n, rowsum);
+  k_col_abs_sums<<<(n + 127) / 128, 128, 0, st>>>(A, m, n, colsum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st) {
+  k_max<<<1, 256, 0, st>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m, int n,
+                                 double* partials, cudaStream_t st, int* blocks_out) {
+  const long total = (long)m * n;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  *blocks_out = blocks;
+  Planes<const double> Bz = B ? *B : Planes<const double>();
+  k_fro2<<<blocks, 256, 0, st>>>(A, Bz, B ? 1 : 0, m, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_antiherm_partials(const Planes<const double>& M, int n, double* partials, cudaStream_t st,
+                                     int* blocks_out) {
+  dim3 grid((n + TILE - 1) / TILE, (n + TILE - 1) / TILE);
+  *blocks_out = grid.x * grid.y;
+  k_antiherm<<<grid, TILE * TROWS, 0, st>>>(M, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_x0(const Planes<const double>& A, int m, int n, double alpha, const Planes<double>& X,
+                           cudaStream_t st) {
+  dim3 grid((n + TILE - 1) / TILE, (m + TILE - 1) / TILE);
+  k_init_x0<<<grid, TILE * TROWS, 0, st>>>(A, m, n, alpha, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e,
+                          cudaStream_t st) {
+  if (by_col)
+    k_col_maxexp<double><<<(cols + 127) / 128, 128, 0, st>>>(A, rows, cols, e);
+  else
+    k_row_maxexp<double><<<(rows + 7) / 8, 256, 0, st>>>(A, rows, cols, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e,
+                              cudaStream_t st) {
+  if (by_col)
+    k_col_maxexp<float><<<(cols + 127) / 128, 128, 0, st>>>(A, rows, cols, e);
+  else
+    k_row_maxexp<float><<<(rows + 7) / 8, 256, 0, st>>>(A, rows, cols, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const Planes<const float>& src, int rows, int cols, const Planes<double>& dst,
+                              cudaStream_t st) {
+  k_f32_to_f64<<<grid_for((long)rows * cols), 256, 0, st>>>(src, rows, cols, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const Planes<const double>& src, int rows, int cols, const Planes<float>& dst,
+                              cudaStream_t st) {
+  k_f64_to_f32<<<grid_for((long)rows * cols), 256, 0, st>>>(src, rows, cols, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace qp

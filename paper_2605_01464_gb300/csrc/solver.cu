@@ -1,0 +1,1237 @@
+// solver.cu -- C ABI of libqpinv: context, device workspace, the per-method
+// iteration schedules, the precision schedule and the stop rules.
+//
+// Every iteration is a fixed list of quaternion GEMMs, each followed by one
+// fused combine pass (elementwise.cu).  The schedules are Algorithms 1-3 and
+// Newton-Schulz rewritten with small quantities, which is exact algebra and
+// keeps low-precision products from rounding away the corrections:
+//   QHPI19 (Alg. 3): R = I - AX, R2, R4; (I + d1R2 + R4)(I + d2R2 + R4) = I + u
+//     with u = a + b + ab (a = d1R2 + R4, b = d2R2 + R4); V = I + v,
+//     W = I + w; Gamma = VW + c1R2 + c2R4 = I + gamma;
+//     X_{j+1} = X (I + (R + R2) Gamma) = X + X t,  t = S + S gamma, S = R + R2.
+//     Seven products: AX, RR, R2R2, ab, vw, S gamma, X t.
+//   QSAI (Alg. 2): Q = (I + b1R2 + R4)(I + b2R2 + R4) = I + q,
+//     X (I + R) Q = X + X t with t = R + q + R q.  Six products.
+//   Newton-Schulz: X (2I - AX) = X + X R.  Two products.
+//   QRAPID (Alg. 1): U = X (13I - P(15I - P(7I - P)))/4 = X + X (R + R2 + R3/4)
+//     (P = I - R); V = U + X(I - AU); Z_l = W + Y(I - AW); X_{j+1} = Z + X(I - AZ).
+//     8 + 2N products.
+// Side: the paper's right form (R = I_m - A X, m x m) or the left form
+// (R = I_n - X A, X_{j+1} = p(R) X), identical in exact arithmetic since
+// X (AX)^k = (XA)^k X; AUTO picks the smaller residual.
+//
+// Precision.  Products of polynomials in R ("R-products") carry errors that
+// are relative to R-sized quantities; products with A or X ("X-products":
+// the residual A X and the update X t) carry errors that the next residual
+// multiplies by about ||A|| ||X||.  Hence:
+//   tensor-core phase: FP32 masters; R-products on BF16 splits (split_level
+//     terms); X-products on BF16 splits while kappa_est = ||A|| ||X_j||_F is
+//     small, then as exact-slice products with 4 slices (about FP32 level);
+//   polish phase (MIXED): FP64 masters; X-products FP64-accurate (8 exact
+//     slices, 56 bits); R-products stay on BF16 splits.
+// Penrose residuals use FP64-accurate products (exact slices, or the
+// CUDA-core FP64 kernel in the FP64 form).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/qpinv.h"
+#include "common.cuh"
+
+using namespace qp;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum { EV_TC = 0, EV_F64 = 1, EV_EW = 2 };
+enum { PM_TC = 0, PM_F64 = 1, PM_EMU = 2 };
+
+struct EvRec {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+long rup8(long x) { return (x + 7) / 8 * 8; }
+
+}  // namespace
+
+struct qpinv_ctx {
+  int device = 0;
+  qpinv_options opt;
+  std::string err = "no error";
+  std::map<std::string, DevBuf> bufs;
+  qpinv_stats stats;
+  std::vector<EvRec> pending;
+  std::vector<cudaEvent_t> pool;
+  int* d_err = nullptr;
+  double* h_pin = nullptr;  // pinned host scalars
+  cudaStream_t st = nullptr;
+  bool trace = false;
+};
+
+namespace {
+
+// ------------------------------------------------------------- utilities
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+struct QpError {
+  int code;
+  std::string msg;
+};
+
+void ck(qpinv_ctx* c, cudaError_t e, const char* what) {
+  (void)c;
+  if (e != cudaSuccess) throw QpError{QPINV_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void* buf(qpinv_ctx* c, const std::string& name, size_t bytes) {
+  DevBuf& b = c->bufs[name];
+  if (b.bytes < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw QpError{QPINV_E_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes for " + name + " failed"};
+    }
+    b.bytes = bytes;
+  }
+  return b.p;
+}
+
+// A quaternion matrix of the workspace: FP64 and/or FP32 master planes and
+// BF16 operand forms (round-to-nearest splits) for the tensor cores.
+struct QMat {
+  int rows = 0, cols = 0;
+  Planes<double> d;
+  Planes<float> f;
+  Split16 s16;
+};
+
+enum { MST_F = 1, MST_D = 2 };
+
+QMat mat(qpinv_ctx* c, const std::string& name, int rows, int cols, int masters, bool aform, bool bform,
+         int levels = 3) {
+  QMat M;
+  M.rows = rows;
+  M.cols = cols;
+  const long ps = (long)rows * cols;
+  if (masters & MST_D) {
+    M.d.ld = cols;
+    M.d.ps = ps;
+    M.d.p = (double*)buf(c, name + ".d", sizeof(double) * 4 * (size_t)ps + 64);
+  }
+  if (masters & MST_F) {
+    M.f.ld = cols;
+    M.f.ps = ps;
+    M.f.p = (float*)buf(c, name + ".f", sizeof(float) * 4 * (size_t)ps + 64);
+  }
+  M.s16.levels = levels;
+  if (aform) {
+    M.s16.lda = rup8(cols);
+    M.s16.psa = (long)rows * M.s16.lda;
+    M.s16.a = (bf16*)buf(c, name + ".a16", sizeof(bf16) * 4 * levels * (size_t)M.s16.psa + 64);
+  }
+  if (bform) {
+    M.s16.ldb = rup8(rows);
+    M.s16.psb = (long)cols * M.s16.ldb;
+    M.s16.b = (bf16*)buf(c, name + ".b16", sizeof(bf16) * 4 * levels * (size_t)M.s16.psb + 64);
+  }
+  return M;
+}
+
+Planes<const double> dview(const QMat& M) {
+  Planes<const double> p;
+  p.p = M.d.p;
+  p.ld = M.d.ld;
+  p.ps = M.d.ps;
+  return p;
+}
+Planes<const float> fview(const QMat& M) {
+  Planes<const float> p;
+  p.p = M.f.p;
+  p.ld = M.f.ld;
+  p.ps = M.f.ps;
+  return p;
+}
+
+cudaEvent_t ev_get(qpinv_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ck(c, cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+// Runs `launch` with optional event timing and counts it.
+template <typename F>
+void timed(qpinv_ctx* c, int kind, double flops, double issued, double bytes, F&& launch) {
+  EvRec r{nullptr, nullptr, kind};
+  if (c->opt.profile) {
+    r.a = ev_get(c);
+    r.b = ev_get(c);
+    ck(c, cudaEventRecord(r.a, c->st), "cudaEventRecord");
+  }
+  ck(c, launch(), "kernel launch");
+  c->stats.kernel_launches++;
+  if (kind == EV_TC) {
+    c->stats.tc_gemm_launches++;
+    c->stats.tc_gemm_flops += flops;
+    c->stats.tc_gemm_flops_issued += issued;
+  } else if (kind == EV_F64) {
+    c->stats.f64_gemm_launches++;
+    c->stats.f64_gemm_flops += flops;
+  } else {
+    c->stats.ew_launches++;
+    c->stats.ew_bytes += bytes;
+  }
+  if (c->opt.profile) {
+    ck(c, cudaEventRecord(r.b, c->st), "cudaEventRecord");
+    c->pending.push_back(r);
+  }
+}
+
+void flush_events(qpinv_ctx* c) {
+  for (EvRec& r : c->pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    if (r.kind == EV_TC) c->stats.tc_gemm_ms += ms;
+    else if (r.kind == EV_F64) c->stats.f64_gemm_ms += ms;
+    else c->stats.ew_ms += ms;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+}
+
+// Host read of `n` doubles from device (synchronises the stream).
+void read_back(qpinv_ctx* c, const double* d, int n, double* h) {
+  ck(c, cudaMemcpyAsync(c->h_pin, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st), "read back");
+  ck(c, cudaStreamSynchronize(c->st), "stream sync");
+  memcpy(h, c->h_pin, sizeof(double) * n);
+}
+
+void check_kernel_error(qpinv_ctx* c) {
+  int h = 0;
+  ck(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "read error word");
+  ck(c, cudaStreamSynchronize(c->st), "stream sync");
+  if (h != 0) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    throw QpError{QPINV_E_TIMEOUT, "tensor-core GEMM bounded wait expired (code " + std::to_string(h) + ")"};
+  }
+}
+
+// -------------------------------------------------------- solver state
+
+struct Solver {
+  qpinv_ctx* c = nullptr;
+  int m = 0, n = 0;
+  bool left = false;
+  int s = 0;              // residual side (s x s)
+  bool dbl = false;       // master type of the current phase: double (true) or float
+  int L = 3;              // BF16 split terms of tensor-core products (0: every product in FP64)
+  int xmode = PM_TC;      // mode of the X-products this iteration
+  int rmode = -1;         // mode of the R-products (-1: PM_F64 if L == 0, else PM_TC)
+  int xS = 8;             // exact slices of X-products in PM_EMU mode
+  long long gemms = 0;
+  QMat A, X[2];
+  int cur = 0;
+  double* partials = nullptr;
+  int partial_cap = 0;
+
+  // ---------------- products ----------------
+  struct Acc {
+    const void* p;
+    int kind;
+    long ld, ps;
+    const int* erow;
+    const int* ecol;
+    int shift;
+  };
+
+  Acc rprod(const QMat& P, const QMat& Q) { return prod(P, Q, rmode >= 0 ? rmode : (L == 0 ? PM_F64 : PM_TC)); }
+
+  // acc(rows x cols) = P (rows x K) * Q (K x cols) in one of three modes:
+  //   PM_TC  - tcgen05 on BF16 splits (L terms), FP32 accumulation;
+  //   PM_F64 - CUDA-core FP64 on the FP64 masters;
+  //   PM_EMU - exact-slice product on the tensor cores from the masters of the
+  //            current phase (xS slices; FP64-accurate for 8).
+  Acc prod(const QMat& P, const QMat& Q, int mode) {
+    const int M = P.rows, K = P.cols, N = Q.cols;
+    gemms++;
+    const double flops = 32.0 * M * (double)K * N;
+    if (mode == PM_EMU) return prod_emu(P, Q, xS, flops);
+    if (mode == PM_F64) {
+      Planes<double> C;
+      C.ld = N;
+      C.ps = (long)M * N;
+      C.p = (double*)buf(c, "acc64", sizeof(double) * 4 * (size_t)C.ps + 64);
+      Planes<const double> a = dview(P), b = dview(Q);
+      timed(c, EV_F64, flops, flops, 0, [&] { return launch_qgemm_f64(M, K, N, a, b, C, c->st); });
+      return Acc{C.p, ACC_F64, C.ld, C.ps, nullptr, nullptr, 0};
+    }
+    Planes<float> C;
+    C.ld = rup8(N);
+    C.ps = (long)M * C.ld;
+    C.p = (float*)buf(c, "acc32", sizeof(float) * 4 * (size_t)C.ps + 64);
+    TcGemmArgs g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.k0 = 0;
+    g.k1 = K;
+    g.A = &P.s16;
+    g.B = &Q.s16;
+    static const int pi3[6] = {2, 1, 0, 1, 0, 0}, pj3[6] = {0, 1, 2, 0, 1, 0};
+    static const int pi2[3] = {1, 0, 0}, pj2[3] = {0, 1, 0};
+    if (L >= 3) {
+      g.npairs = 6;
+      for (int t = 0; t < 6; t++) g.pair_i[t] = pi3[t], g.pair_j[t] = pj3[t];
+    } else if (L == 2) {
+      g.npairs = 3;
+      for (int t = 0; t < 3; t++) g.pair_i[t] = pi2[t], g.pair_j[t] = pj2[t];
+    } else {
+      g.npairs = 1;
+    }
+    g.C = C;
+    g.err = c->d_err;
+    timed(c, EV_TC, flops, flops * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
+    return Acc{C.p, ACC_F32, C.ld, C.ps, nullptr, nullptr, 0};
+  }
+
+  Acc prod_emu(const QMat& P, const QMat& Q, int S, double flops) {
+    const int M = P.rows, K = P.cols, N = Q.cols;
+    int* eP = (int*)buf(c, "emu.eP", sizeof(int) * (size_t)M + 64);
+    int* eQ = (int*)buf(c, "emu.eQ", sizeof(int) * (size_t)N + 64);
+    if (dbl) {
+      timed(c, EV_EW, 0, 0, 32.0 * M * K, [&] { return launch_maxexp(dview(P), M, K, 0, eP, c->st); });
+      timed(c, EV_EW, 0, 0, 32.0 * K * N, [&] { return launch_maxexp(dview(Q), K, N, 1, eQ, c->st); });
+    } else {
+      timed(c, EV_EW, 0, 0, 16.0 * M * K, [&] { return launch_maxexp_f32(fview(P), M, K, 0, eP, c->st); });
+      timed(c, EV_EW, 0, 0, 16.0 * K * N, [&] { return launch_maxexp_f32(fview(Q), K, N, 1, eQ, c->st); });
+    }
+    Split16 za, zb;
+    za.levels = zb.levels = S;
+    za.lda = rup8(K);
+    za.psa = (long)M * za.lda;
+    za.a = (bf16*)buf(c, "emu.za", sizeof(bf16) * 4 * S * (size_t)za.psa + 64);
+    zb.ldb = rup8(K);
+    zb.psb = (long)N * zb.ldb;
+    zb.b = (bf16*)buf(c, "emu.zb", sizeof(bf16) * 4 * S * (size_t)zb.psb + 64);
+    {
+      CombineArgs a = base_args(M, K, nullptr);
+      aux(a, 0, P);
+      OutSpec& o = a.out[a.nout++];
+      o.s16 = za;
+      o.exp_a = eP;
+      o.caux[0] = 1.0;
+      run(a);
+    }
+    {
+      CombineArgs a = base_args(K, N, nullptr);
+      aux(a, 0, Q);
+      OutSpec& o = a.out[a.nout++];
+      o.s16 = zb;
+      o.exp_b = eQ;
+      o.caux[0] = 1.0;
+      run(a);
+    }
+    long long* acc = (long long*)buf(c, "emu.acc", sizeof(long long) * 4 * (size_t)M * N + 64);
+    ck(c, cudaMemsetAsync(acc, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");
+    int lg = 0;
+    while ((1L << lg) < 4L * K) lg++;
+    const int shift = 61 - lg;  // |sum| < 4K in normalized units: no int64 overflow
+    for (int d = S - 1; d >= 0; d--) {
+      TcGemmArgs g;
+      g.M = M;
+      g.N = N;
+      g.K = K;
+      g.A = &za;
+      g.B = &zb;
+      g.npairs = d + 1;
+      for (int t = 0; t <= d; t++) g.pair_i[t] = t, g.pair_j[t] = d - t;
+      g.C64 = acc;
+      g.ld64 = N;
+      g.ps64 = (long)M * N;
+      g.shift = shift;
+      g.err = c->d_err;
+      // Levels whose FP32 rounding could matter are summed in K chunks small
+      // enough for every partial sum to be exact: slice digits are at most
+      // 2^7 (first) and 2^6 (others), so (d+1) pairs * 2^13 * 4 Kc <= 2^24
+      // (2^14 * 4 Kc for d = 0).  The two lowest levels are summed whole.
+      const bool exact = d <= S - 3;
+      int kc = K;
+      if (exact) {
+        const int lim = d == 0 ? 256 : 512 / (d + 1);
+        kc = lim >= 64 ? (lim / 64) * 64 : 64;
+      }
+      for (int k0 = 0; k0 < K; k0 += kc) {
+        g.k0 = k0;
+        g.k1 = k0 + kc < K ? k0 + kc : K;
+        const double part = flops * (double)(g.k1 - g.k0) / K;
+        timed(c, EV_TC, d == 0 ? part : 0.0, part * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
+      }
+    }
+    return Acc{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
+  }
+
+  // ---------------- combine helpers ----------------
+  CombineArgs base_args(int rows, int cols, const Acc* acc) {
+    CombineArgs a;
+    a.rows = rows;
+    a.cols = cols;
+    a.f64 = dbl ? 1 : 0;
+    if (acc) {
+      a.acc = acc->p;
+      a.acc_kind = acc->kind;
+      a.ld_acc = acc->ld;
+      a.ps_acc = acc->ps;
+      a.acc_erow = acc->erow;
+      a.acc_ecol = acc->ecol;
+      a.acc_shift = acc->shift;
+    }
+    return a;
+  }
+  void aux(CombineArgs& a, int t, const QMat& M) {
+    if (dbl) {
+      a.aux[t] = M.d.p;
+      a.ld_aux[t] = M.d.ld;
+      a.ps_aux[t] = M.d.ps;
+    } else {
+      a.aux[t] = M.f.p;
+      a.ld_aux[t] = M.f.ld;
+      a.ps_aux[t] = M.f.ps;
+    }
+  }
+  // Adds an output; forms: 'f' master of the phase type, 'a' A-form, 'b' B-form.
+  OutSpec& out(CombineArgs& a, const QMat& M, const char* forms, double cacc, double diag = 0.0) {
+    OutSpec& o = a.out[a.nout++];
+    o = OutSpec();
+    if (strchr(forms, 'f')) {
+      if (dbl) {
+        o.mp = M.d.p;
+        o.mld = M.d.ld;
+        o.mps = M.d.ps;
+      } else {
+        o.mp = M.f.p;
+        o.mld = M.f.ld;
+        o.mps = M.f.ps;
+      }
+    }
+    if (L > 0) {
+      o.s16.levels = L;
+      if (strchr(forms, 'a')) {
+        o.s16.a = M.s16.a;
+        o.s16.lda = M.s16.lda;
+        o.s16.psa = M.s16.psa;
+      }
+      if (strchr(forms, 'b')) {
+        o.s16.b = M.s16.b;
+        o.s16.ldb = M.s16.ldb;
+        o.s16.psb = M.s16.psb;
+      }
+    }
+    o.cacc = cacc;
+    o.diag = diag;
+    return o;
+  }
+  void run(CombineArgs& a, bool with_partials = false) {
+    int blocks = ((a.cols + 31) / 32) * ((a.rows + 31) / 32);
+    if (with_partials) {
+      if (blocks > partial_cap) {
+        partials = (double*)buf(c, "partials", sizeof(double) * 3 * (size_t)blocks + 64);
+        partial_cap = blocks;
+      }
+      a.partials = partials;
+    }
+    double bytes = 0;
+    const double el = (double)a.rows * a.cols * 4, ms = dbl ? 8 : 4;
+    if (a.acc) bytes += el * (a.acc_kind == ACC_F32 ? 4 : 8);
+    for (int t = 0; t < 4; t++)
+      if (a.aux[t]) bytes += el * ms;
+    for (int o = 0; o < a.nout; o++) {
+      if (a.out[o].mp) bytes += el * ms;
+      if (a.out[o].s16.a) bytes += el * 2 * a.out[o].s16.levels;
+      if (a.out[o].s16.b) bytes += el * 2 * a.out[o].s16.levels;
+    }
+    timed(c, EV_EW, 0, 0, bytes, [&] { return launch_combine(a, c->st, nullptr); });
+    if (with_partials) {
+      double* red = (double*)buf(c, "red", sizeof(double) * 8);
+      timed(c, EV_EW, 0, 0, 24.0 * blocks, [&] { return launch_reduce_partials(partials, blocks, 3, red, c->st); });
+    }
+  }
+
+  // ---------------- shape helpers ----------------
+  // X-products take the mode of the phase (xmode).
+  // Residual product: right A*Y (m x m), left Y*A (n x n).
+  Acc res_prod(const QMat& Y) { return left ? prod(Y, A, xmode) : prod(A, Y, xmode); }
+  // Apply a side polynomial T (s x s) to Y (n x m): right Y*T, left T*Y.
+  Acc apply(const QMat& Y, const QMat& T) { return left ? prod(T, Y, xmode) : prod(Y, T, xmode); }
+  const char* tform() const { return left ? "fa" : "fb"; }
+  QMat sq(const char* name, bool a, bool b) { return mat(c, name, s, s, MST_F | MST_D, a, b); }
+  QMat big(const char* name) { return mat(c, name, n, m, MST_F | MST_D, true, true); }
+
+  // R = I - (residual product of Y).
+  QMat residual(const QMat& Y, const char* name, const char* forms) {
+    Acc acc = res_prod(Y);
+    QMat R = sq(name, strchr(forms, 'a') != nullptr, strchr(forms, 'b') != nullptr);
+    CombineArgs a = base_args(s, s, &acc);
+    out(a, R, forms, -1.0, 1.0);
+    run(a);
+    return R;
+  }
+
+  // Xn = base + acc (master + both forms) with the stop-test partials vs X[cur].
+  void update(const QMat& base, const Acc& acc) {
+    QMat& Xn = X[cur ^ 1];
+    CombineArgs a = base_args(n, m, &acc);
+    aux(a, 0, X[cur]);
+    aux(a, 1, base);
+    OutSpec& o = out(a, Xn, "fab", 1.0);
+    o.caux[1] = 1.0;  // + base (aux 0 = X_j is only the reference of the norm)
+    run(a, true);
+  }
+
+  // ---------------- one iteration of each method ----------------
+  void step_ns() {
+    QMat R = residual(X[cur], "R", tform());
+    Acc acc = apply(X[cur], R);
+    update(X[cur], acc);
+  }
+
+  void step_qsai(double b1, double b2) {
+    QMat R = residual(X[cur], "R", "fab");
+    Acc a2 = rprod(R, R);
+    QMat R2 = sq("R2", true, true);
+    {
+      CombineArgs a = base_args(s, s, &a2);
+      out(a, R2, "fab", 1.0);
+      run(a);
+    }
+    Acc a4 = rprod(R2, R2);
+    QMat R4 = sq("R4", false, false), Fa = sq("Fa", true, false), Fb = sq("Fb", false, true);
+    {
+      CombineArgs a = base_args(s, s, &a4);
+      aux(a, 0, R2);
+      out(a, R4, "f", 1.0);
+      out(a, Fa, "fa", 1.0).caux[0] = b1;
+      out(a, Fb, "fb", 1.0).caux[0] = b2;
+      run(a);
+    }
+    Acc ab = rprod(Fa, Fb);
+    QMat q = sq("q", false, true);
+    {
+      CombineArgs a = base_args(s, s, &ab);
+      aux(a, 0, R2);
+      aux(a, 1, R4);
+      OutSpec& o = out(a, q, "fb", 1.0);
+      o.caux[0] = b1 + b2;
+      o.caux[1] = 2.0;
+      run(a);
+    }
+    Acc rq = rprod(R, q);
+    QMat t = sq("t", left, !left);
+    {
+      CombineArgs a = base_args(s, s, &rq);
+      aux(a, 0, R);
+      aux(a, 1, q);
+      OutSpec& o = out(a, t, tform(), 1.0);
+      o.caux[0] = 1.0;
+      o.caux[1] = 1.0;
+      run(a);
+    }
+    Acc xt = apply(X[cur], t);
+    update(X[cur], xt);
+  }
+
+  void step_qhpi19(const double* k) {
+    // k: a1 a2 a3 b1 b2 c1 c2 d1 d2 d3 e1 e2
+    const double c1 = k[5], c2 = k[6], d1 = k[7], d2 = k[8], d3 = k[9], e1 = k[10], e2 = k[11];
+    QMat R = residual(X[cur], "R", "fab");
+    Acc a2 = rprod(R, R);
+    QMat R2 = sq("R2", true, true), S = sq("S", true, false);
+    {
+      CombineArgs a = base_args(s, s, &a2);
+      aux(a, 0, R);
+      out(a, R2, "fab", 1.0);
+      out(a, S, "fa", 1.0).caux[0] = 1.0;
+      run(a);
+    }
+    Acc a4 = rprod(R2, R2);
+    QMat R4 = sq("R4", false, false), Fa = sq("Fa", true, false), Fb = sq("Fb", false, true);
+    {
+      CombineArgs a = base_args(s, s, &a4);
+      aux(a, 0, R2);
+      out(a, R4, "f", 1.0);
+      out(a, Fa, "fa", 1.0).caux[0] = d1;
+      out(a, Fb, "fb", 1.0).caux[0] = d2;
+      run(a);
+    }
+    Acc ab = rprod(Fa, Fb);
+    QMat u = sq("u", false, false), v = sq("v", true, false), w = sq("w", false, true);
+    {
+      CombineArgs a = base_args(s, s, &ab);
+      aux(a, 0, R2);
+      aux(a, 1, R4);
+      OutSpec& ou = out(a, u, "f", 1.0);
+      ou.caux[0] = d1 + d2;
+      ou.caux[1] = 2.0;
+      OutSpec& ov = out(a, v, "fa", 1.0);
+      ov.caux[0] = d1 + d2 + d3;
+      ov.caux[1] = 2.0;
+      OutSpec& ow = out(a, w, "fb", 1.0);
+      ow.caux[0] = d1 + d2 + e1;
+      ow.caux[1] = 2.0 + e2;
+      run(a);
+    }
+    Acc vw = rprod(v, w);
+    QMat g = sq("g", false, true);
+    {
+      CombineArgs a = base_args(s, s, &vw);
+      aux(a, 0, u);
+      aux(a, 1, R2);
+      aux(a, 2, R4);
+      OutSpec& o = out(a, g, "fb", 1.0);
+      o.caux[0] = 2.0;
+      o.caux[1] = d3 + e1 + c1;
+      o.caux[2] = e2 + c2;
+      run(a);
+    }
+    Acc sg = rprod(S, g);
+    QMat t = sq("t", left, !left);
+    {
+      CombineArgs a = base_args(s, s, &sg);
+      aux(a, 0, S);
+      out(a, t, tform(), 1.0).caux[0] = 1.0;
+      run(a);
+    }
+    Acc xt = apply(X[cur], t);
+    update(X[cur], xt);
+  }
+
+  // QRAPID correction  W + Y (I - A W)  (right) / W + (I - W A) Y (left) into Z.
+  void rapid_correct(const QMat& W, const QMat& Y, QMat& Z, bool is_final) {
+    QMat E = residual(W, "E", tform());
+    Acc acc = apply(Y, E);
+    if (is_final) {
+      update(W, acc);
+      return;
+    }
+    CombineArgs a = base_args(n, m, &acc);
+    aux(a, 0, W);
+    out(a, Z, "fab", 1.0).caux[0] = 1.0;
+    run(a);
+  }
+
+  void step_qrapid(int N) {
+    QMat R = residual(X[cur], "R", "fab");
+    Acc a2 = rprod(R, R);
+    QMat R2 = sq("R2", false, true);
+    {
+      CombineArgs a = base_args(s, s, &a2);
+      out(a, R2, "fb", 1.0);
+      run(a);
+    }
+    Acc a3 = rprod(R, R2);
+    QMat tU = sq("t", left, !left);
+    {
+      CombineArgs a = base_args(s, s, &a3);
+      aux(a, 0, R);
+      aux(a, 1, R2);
+      OutSpec& o = out(a, tU, tform(), 0.25);
+      o.caux[0] = 1.0;
+      o.caux[1] = 1.0;
+      run(a);
+    }
+    QMat Zb[3] = {big("Z0"), big("Z1"), big("Z2")};
+    Acc xt = apply(X[cur], tU);
+    {  // U = X + X tU
+      CombineArgs a = base_args(n, m, &xt);
+      aux(a, 0, X[cur]);
+      out(a, Zb[0], "fab", 1.0).caux[0] = 1.0;
+      run(a);
+    }
+    rapid_correct(Zb[0], X[cur], Zb[1], false);  // V = U + X (I - A U)
+    int y = 0, w = 1;                             // Y_0 = U, W_0 = V
+    for (int it = 1; it <= N; it++) {
+      const int z = 3 - y - w;
+      rapid_correct(Zb[w], Zb[y], Zb[z], false);
+      y = w;
+      w = z;
+    }
+    rapid_correct(Zb[w], X[cur], Zb[w], true);  // X_{j+1} = Z + X (I - A Z)
+  }
+
+  // Removes the component of X that rounding puts outside the ranges of the
+  // pseudoinverse.  For full-rank rectangular A the iteration corrects only
+  // what its residual sees: with a tall A (left form, residual I - XA) the
+  // part of X acting on range(A)^perp is invisible, with a wide A (right
+  // form) the part of X's range in null(A) is.  X (AX)^H = X X^H A^H (tall)
+  // and (XA)^H X = A^H X^H X (wide) equal A^dagger for X = A^dagger and
+  // remove such a component E to first order (it becomes O(E^2)).  FP64
+  // masters, FP64-accurate products.
+  void range_projection() {
+    const bool tall = m > n;
+    const int k = tall ? n : m;
+    QMat XH = mat(c, "XH", m, n, MST_D, false, false), AH = mat(c, "AHp", n, m, MST_D, false, false);
+    QMat G = mat(c, "G", k, k, MST_D, false, false);
+    ck(c, launch_init_x0(dview(X[cur]), n, m, 1.0, XH.d, c->st), "adjoint X");
+    ck(c, launch_init_x0(dview(A), m, n, 1.0, AH.d, c->st), "adjoint A");
+    const int L0 = L, xm0 = xmode, xs0 = xS;
+    L = 0;
+    xS = 8;
+    {
+      Acc g = tall ? prod(X[cur], XH, PM_EMU) : prod(XH, X[cur], PM_EMU);
+      CombineArgs a = base_args(k, k, &g);
+      out(a, G, "f", 1.0);
+      run(a);
+    }
+    Acc y = tall ? prod(G, AH, PM_EMU) : prod(AH, G, PM_EMU);
+    CombineArgs a = base_args(n, m, &y);
+    out(a, X[cur ^ 1], "f", 1.0);
+    run(a);
+    cur ^= 1;
+    L = L0;
+    xmode = xm0;
+    xS = xs0;
+  }
+
+  // Writes the BF16 operand forms of a matrix from the master of the phase.
+  void forms(const QMat& M, bool a, bool b) {
+    if (L == 0) return;
+    CombineArgs args = base_args(M.rows, M.cols, nullptr);
+    aux(args, 0, M);
+    OutSpec& o = out(args, M, a && b ? "ab" : (a ? "a" : "b"), 0.0);
+    o.caux[0] = 1.0;
+    run(args);
+  }
+};
+
+double hpi19_k[12];
+void init_constants() {
+  const double s93 = std::sqrt(93.0);
+  const double r = std::sqrt(27.0 - 2.0 * s93);
+  hpi19_k[0] = 5.0 / 496.0 * (31.0 + s93);    // a1
+  hpi19_k[1] = (3.0 + s93) / 8.0;             // a2
+  hpi19_k[2] = 0.5;                           // a3
+  hpi19_k[3] = 5.0 / 496.0 * (31.0 - s93);    // b1
+  hpi19_k[4] = (3.0 - s93) / 8.0;             // b2
+  hpi19_k[5] = 3.0 / 8.0;                     // c1
+  hpi19_k[6] = 321.0 / 1984.0;                // c2
+  hpi19_k[7] = 0.25 * (1.0 + r);              // d1
+  hpi19_k[8] = 0.25 * (1.0 - r);              // d2
+  hpi19_k[9] = (5.0 * s93 - 93.0) / 496.0;    // d3
+  hpi19_k[10] = -(93.0 + 5.0 * s93) / 496.0;  // e1
+  hpi19_k[11] = -s93 / 4.0;                   // e2
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copies a caller matrix (device or host planes) into a workspace FP64 master.
+void load_planes(qpinv_ctx* c, const double* const src[4], long ld, int rows, int cols, const QMat& dst) {
+  for (int p = 0; p < 4; p++) {
+    const bool dev = is_device_ptr(src[p]);
+    ck(c,
+       cudaMemcpy2DAsync(dst.d.p + p * dst.d.ps, sizeof(double) * dst.d.ld, src[p], sizeof(double) * ld,
+                         sizeof(double) * cols, rows, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),
+       "copy in");
+  }
+}
+void store_planes(qpinv_ctx* c, const QMat& src, double* const dst[4], long ld, int rows, int cols) {
+  for (int p = 0; p < 4; p++) {
+    const bool dev = is_device_ptr(dst[p]);
+    ck(c,
+       cudaMemcpy2DAsync(dst[p], sizeof(double) * ld, src.d.p + p * src.d.ps, sizeof(double) * src.d.ld,
+                         sizeof(double) * cols, rows, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
+       "copy out");
+  }
+}
+
+double fro2(qpinv_ctx* c, const Planes<const double>& P, const Planes<const double>* Q, int rows, int cols,
+            double* bad = nullptr) {
+  int blocks = 0;
+  double* part = (double*)buf(c, "fro_part", sizeof(double) * 2 * 1024 + 64);
+  double* red = (double*)buf(c, "fro_red", sizeof(double) * 4);
+  timed(c, EV_EW, 0, 0, (double)rows * cols * 32 * (Q ? 2 : 1),
+        [&] { return launch_fro2_partials(P, Q, rows, cols, part, c->st, &blocks); });
+  timed(c, EV_EW, 0, 0, 16.0 * blocks, [&] { return launch_reduce_partials(part, blocks, 2, red, c->st); });
+  double h[2];
+  read_back(c, red, 2, h);
+  if (bad) *bad = h[1];
+  return h[0];
+}
+
+double antiherm2(qpinv_ctx* c, const QMat& M) {
+  int blocks = ((M.rows + 31) / 32) * ((M.rows + 31) / 32);
+  double* part = (double*)buf(c, "ah_part", sizeof(double) * (size_t)blocks + 64);
+  double* red = (double*)buf(c, "fro_red", sizeof(double) * 4);
+  timed(c, EV_EW, 0, 0, (double)M.rows * M.rows * 64,
+        [&] { return launch_antiherm_partials(dview(M), M.rows, part, c->st, &blocks); });
+  timed(c, EV_EW, 0, 0, 8.0 * blocks, [&] { return launch_reduce_partials(part, blocks, 1, red, c->st); });
+  double h;
+  read_back(c, red, 1, &h);
+  return h;
+}
+
+// Penrose residuals (Sec. 4) for A (m x n) and X (n x m) FP64 masters, with
+// FP64-accurate products (mode PM_F64 or PM_EMU with 8 slices) and FP64 norms.
+void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, double* Er, long long* gemms) {
+  const int m = A.rows, n = A.cols;
+  Solver S;
+  S.c = c;
+  S.dbl = true;
+  S.L = 0;
+  S.xS = 8;
+  QMat AX = mat(c, "pAX", m, m, MST_D, false, false), XA = mat(c, "pXA", n, n, MST_D, false, false);
+  QMat AXA = mat(c, "pAXA", m, n, MST_D, false, false), XAX = mat(c, "pXAX", n, m, MST_D, false, false);
+  auto product = [&](const QMat& P, const QMat& Q, QMat& Out) {
+    Solver::Acc acc = S.prod(P, Q, mode);
+    CombineArgs a = S.base_args(Out.rows, Out.cols, &acc);
+    S.out(a, Out, "f", 1.0);
+    S.run(a);
+  };
+  product(A, X, AX);
+  product(X, A, XA);
+  product(AX, A, AXA);
+  product(XA, X, XAX);
+  if (gemms) *gemms += S.gemms;
+  Planes<const double> a = dview(A), x = dview(X);
+  E[0] = std::sqrt(fro2(c, dview(AXA), &a, m, n));
+  E[1] = std::sqrt(fro2(c, dview(XAX), &x, n, m));
+  E[2] = std::sqrt(antiherm2(c, AX));
+  E[3] = std::sqrt(antiherm2(c, XA));
+  const double nr[4] = {std::sqrt(fro2(c, a, nullptr, m, n)), std::sqrt(fro2(c, x, nullptr, n, m)),
+                        std::sqrt(fro2(c, dview(AX), nullptr, m, m)), std::sqrt(fro2(c, dview(XA), nullptr, n, n))};
+  for (int t = 0; t < 4; t++) Er[t] = nr[t] > 0 ? E[t] / nr[t] : E[t];
+}
+
+int fail(qpinv_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+void qpinv_default_options(qpinv_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = QPINV_PREC_MIXED;
+  o->split_level = 0;
+  o->polish_iters = 2;
+  o->alpha_mode = QPINV_ALPHA_SAFE;
+  o->alpha_user = 0.0;
+  o->qrapid_N = 5;
+  o->side = QPINV_SIDE_AUTO;
+  o->stop_rule = QPINV_STOP_REL_PLATEAU;
+  o->penrose = 1;
+  o->profile = 0;
+}
+
+static int check_opts(const qpinv_options* o) {
+  if (o->precision < 0 || o->precision > 3) return 0;
+  if (o->split_level < 0 || o->split_level > 3) return 0;
+  if (o->polish_iters < 0 || o->polish_iters > 100) return 0;
+  if (o->alpha_mode < 0 || o->alpha_mode > 4) return 0;
+  if (o->alpha_mode == QPINV_ALPHA_USER && !(o->alpha_user > 0.0 && std::isfinite(o->alpha_user))) return 0;
+  if (o->qrapid_N < 0 || o->qrapid_N > 30) return 0;
+  if (o->side < 0 || o->side > 2 || o->stop_rule < 0 || o->stop_rule > 1) return 0;
+  return 1;
+}
+
+int qpinv_init(qpinv_ctx** out, int device, const qpinv_options* opt) {
+  if (!out) return QPINV_E_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return QPINV_E_CUDA;
+  }
+  if (opt && !check_opts(opt)) return QPINV_E_INVALID;
+  qpinv_ctx* c = new qpinv_ctx();
+  c->device = device;
+  qpinv_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  memset(&c->stats, 0, sizeof(c->stats));
+  const char* tr = getenv("QPINV_TRACE");
+  c->trace = tr && tr[0] == '1';
+  DeviceGuard g(device);
+  if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_pin, sizeof(double) * 64) != cudaSuccess) {
+    cudaGetLastError();
+    qpinv_free(c);
+    return QPINV_E_NOMEM;
+  }
+  init_constants();
+  *out = c;
+  return QPINV_OK;
+}
+
+int qpinv_set_options(qpinv_ctx* c, const qpinv_options* opt) {
+  if (!c || !opt) return QPINV_E_INVALID;
+  if (!check_opts(opt)) return fail(c, QPINV_E_INVALID, "invalid options");
+  c->opt = *opt;
+  return QPINV_OK;
+}
+
+void qpinv_free(qpinv_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  flush_events(c);
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->d_err) cudaFree(c->d_err);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  delete c;
+}
+
+const char* qpinv_last_error(qpinv_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int qpinv_get_stats(qpinv_ctx* c, qpinv_stats* s) {
+  if (!c || !s) return QPINV_E_INVALID;
+  DeviceGuard g(c->device);
+  flush_events(c);
+  *s = c->stats;
+  return QPINV_OK;
+}
+
+int qpinv_reset_stats(qpinv_ctx* c) {
+  if (!c) return QPINV_E_INVALID;
+  DeviceGuard g(c->device);
+  flush_events(c);
+  memset(&c->stats, 0, sizeof(c->stats));
+  return QPINV_OK;
+}
+
+static bool planes_ok(const double* const P[4]) {
+  if (!P) return false;
+  for (int t = 0; t < 4; t++)
+    if (!P[t]) return false;
+  return true;
+}
+
+int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[4], long lda, qpinv_method method,
+                double tol, int max_iter, double* const X[4], long ldx, qpinv_result* out) {
+  if (!c) return QPINV_E_INVALID;
+  if (m <= 0 || n <= 0 || lda < n || ldx < m || !planes_ok(A) || !planes_ok((const double* const*)X) ||
+      max_iter < 1 || !(tol >= 0.0) || (int)method < 0 || (int)method > 3)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  const auto t_start = std::chrono::steady_clock::now();
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  const qpinv_options& o = c->opt;
+  qpinv_result res;
+  memset(&res, 0, sizeof(res));
+  try {
+    const bool fp64 = o.precision == QPINV_PREC_FP64;
+    // A residual forced onto the larger side has eigenvalue 1 on the
+    // complement of the range, where rounding noise grows by the method's
+    // order each step (as for rank-deficient A): such solves run with
+    // FP64-accurate products throughout.
+    const bool wrong_side = (o.side == QPINV_SIDE_RIGHT && m > n) || (o.side == QPINV_SIDE_LEFT && m < n);
+    const bool emu = o.precision == QPINV_PREC_EMU || (!fp64 && wrong_side);
+    if (!fp64 && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    Solver S;
+    S.c = c;
+    S.m = m;
+    S.n = n;
+    S.left = o.side == QPINV_SIDE_LEFT || (o.side == QPINV_SIDE_AUTO && m > n);
+    S.s = S.left ? n : m;
+    res.side = S.left ? QPINV_SIDE_LEFT : QPINV_SIDE_RIGHT;
+    S.A = mat(c, "A", m, n, MST_D | MST_F, !S.left, S.left);
+    load_planes(c, A, lda, m, n, S.A);
+    Planes<const double> a = dview(S.A);
+    double bad = 0.0;
+    const double a_f2 = fro2(c, a, nullptr, m, n, &bad);
+    if (bad > 0.0 || !std::isfinite(a_f2)) return fail(c, QPINV_E_NONFINITE, "A contains NaN or Inf");
+    // ---- norms and alpha (Thm. 1) ----
+    double* rs = (double*)buf(c, "rowsum", sizeof(double) * (size_t)(m + n) + 64);
+    double* mx = (double*)buf(c, "maxes", sizeof(double) * 4);
+    timed(c, EV_EW, 0, 0, 64.0 * m * n, [&] { return launch_abs_sums(a, m, n, rs, rs + m, c->st); });
+    timed(c, EV_EW, 0, 0, 8.0 * m, [&] { return launch_max(rs, m, mx, c->st); });
+    timed(c, EV_EW, 0, 0, 8.0 * n, [&] { return launch_max(rs + m, n, mx + 1, c->st); });
+    double hm[2];
+    read_back(c, mx, 2, hm);
+    const double norm_inf = hm[0], norm_1 = hm[1];
+    const double a2est = std::sqrt(norm_1 * norm_inf);  // >= sigma_1
+    double alpha = 0.0;
+    const int amode = o.alpha_mode == QPINV_ALPHA_LEARNED ? QPINV_ALPHA_SAFE : o.alpha_mode;
+    if (a_f2 == 0.0) {
+      alpha = 0.0;
+    } else if (amode == QPINV_ALPHA_SAFE) {
+      alpha = 1.0 / (norm_1 * norm_inf);
+    } else if (amode == QPINV_ALPHA_FRO) {
+      alpha = 1.0 / a_f2;
+    } else if (amode == QPINV_ALPHA_USER) {
+      alpha = o.alpha_user;
+    } else {  // SPECTRAL: power iteration on A^H A with FP64 matrix-vector products
+      QMat AH = mat(c, "AH", n, m, MST_D, false, false);
+      ck(c, launch_init_x0(a, m, n, 1.0, AH.d, c->st), "adjoint");
+      QMat v = mat(c, "pv", n, 1, MST_D, false, false), w = mat(c, "pw", m, 1, MST_D, false, false);
+      std::vector<double> hv(4 * (size_t)n);
+      for (int i = 0; i < 4 * n; i++) hv[i] = 1.0 / (1.0 + 0.37 * (i % 7) + 0.11 * i);
+      ck(c, cudaMemcpyAsync(v.d.p, hv.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, c->st), "copy");
+      double lam = 0.0;
+      Solver P;
+      P.c = c;
+      P.dbl = true;
+      P.L = 0;
+      for (int it = 0; it < 300; it++) {
+        const double nv = std::sqrt(fro2(c, dview(v), nullptr, n, 1));
+        CombineArgs ca = P.base_args(n, 1, nullptr);
+        P.aux(ca, 0, v);
+        P.out(ca, v, "f", 0.0).caux[0] = 1.0 / nv;
+        P.run(ca);
+        timed(c, EV_F64, 32.0 * m * n, 32.0 * m * n, 0,
+              [&] { return launch_qgemm_f64(m, n, 1, a, dview(v), w.d, c->st); });
+        timed(c, EV_F64, 32.0 * m * n, 32.0 * m * n, 0,
+              [&] { return launch_qgemm_f64(n, m, 1, dview(AH), dview(w), v.d, c->st); });
+        const double lam_new = std::sqrt(fro2(c, dview(v), nullptr, n, 1));
+        if (it > 10 && std::fabs(lam_new - lam) <= 1e-13 * lam_new) {
+          lam = lam_new;
+          break;
+        }
+        lam = lam_new;
+      }
+      alpha = 1.0 / lam;
+    }
+    res.alpha = alpha;
+    res.alpha_source = amode;
+    // ---- X_0 = alpha A^H (FP64), with the FP32 copies of A and X_0 ----
+    S.X[0] = mat(c, "X0", n, m, MST_D | MST_F, true, true);
+    S.X[1] = mat(c, "X1", n, m, MST_D | MST_F, true, true);
+    S.cur = 0;
+    ck(c, launch_init_x0(a, m, n, alpha, S.X[0].d, c->st), "init X0");
+    const int Ltc = o.split_level ? o.split_level : 3;
+    bool polish = fp64 || emu;  // these forms run in their final precision from the start
+    if (fp64 || emu) {
+      S.dbl = true;
+      S.L = 0;
+      S.xmode = S.rmode = fp64 ? PM_F64 : PM_EMU;
+      S.xS = 8;
+    } else {
+      S.dbl = false;
+      S.L = Ltc;
+      S.xmode = PM_TC;
+      ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
+      ck(c, launch_f64_to_f32(dview(S.X[0]), n, m, S.X[0].f, c->st), "X0 to fp32");
+      S.forms(S.A, !S.left, S.left);
+      S.forms(S.X[0], true, true);
+    }
+    int polish_done = 0, tc_done = 0;
+    double prev_rel = INFINITY, xnorm = std::sqrt(a_f2) * alpha;
+    res.status = QPINV_NOT_CONVERGED;
+    res.iters = 0;
+    for (int j = 0; j < max_iter; j++) {
+      if (!polish && !emu) {
+        // X-products: BF16 splits while their error, amplified by about
+        // ||A|| ||X||, stays small; exact 4-slice products beyond.
+        const double kappa_est = a2est * xnorm;
+        if (kappa_est * 1e-5 > 1e-2) {
+          S.xmode = PM_EMU;
+          S.xS = 4;
+        } else {
+          S.xmode = PM_TC;
+        }
+      }
+      switch (method) {
+        case QPINV_NS: S.step_ns(); break;
+        case QPINV_QSAI: S.step_qsai((1.0 + std::sqrt(5.0)) / 2.0, (1.0 - std::sqrt(5.0)) / 2.0); break;
+        case QPINV_QRAPID: S.step_qrapid(o.qrapid_N); break;
+        default: S.step_qhpi19(hpi19_k); break;
+      }
+      if (!fp64) check_kernel_error(c);
+      double h[3];
+      read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 3, h);
+      const double d = std::sqrt(h[0]), nx = std::sqrt(h[1]);
+      if (c->trace)
+        fprintf(stderr, "qpinv it %d %s xmode %d xS %d delta %.3e |X| %.3e rel %.3e\n", j,
+                polish ? "polish" : "tc", S.xmode, S.xS, d, nx, nx > 0 ? d / nx : d);
+      if (h[2] > 0.0 || !std::isfinite(d) || !std::isfinite(nx)) {
+        res.status = QPINV_DIVERGED;
+        break;  // X[cur] is the last finite iterate
+      }
+      const double drel = nx > 0 ? d / nx : d;
+      res.delta = d;
+      res.delta_rel = drel;
+      if (polish && !fp64 && !emu) polish_done++;
+      else if (!fp64 && !emu) tc_done++;
+      bool accept = true, stop = false;
+      const bool final_phase = polish || o.precision == QPINV_PREC_TC;  // (FP64 and EMU: polish)
+      if (o.stop_rule == QPINV_STOP_PAPER_ABS) {
+        if (d < tol && final_phase) stop = true, res.status = QPINV_CONVERGED;
+      } else {
+        if (drel <= tol && final_phase) {
+          stop = true;
+          res.status = QPINV_CONVERGED;
+        } else if (prev_rel < INFINITY && drel >= prev_rel && drel < 1e-6 && final_phase) {
+          stop = true;
+          accept = false;
+          res.status = QPINV_PLATEAU;
+        }
+      }
+      if (accept) {
+        S.cur ^= 1;
+        res.iters = j + 1;
+        xnorm = nx;
+      }
+      if (stop) break;
+      if (o.precision == QPINV_PREC_MIXED && !polish) {
+        // Leave the tensor-core phase once the step stops shrinking fast or
+        // is below the FP32 level: switch to FP64 masters and FP64-accurate
+        // X-products for the polish iterations.
+        const bool stalled = prev_rel < INFINITY && drel > 0.05 * prev_rel && drel < 1e-2;
+        if (stalled || drel < 1e-6 || (o.stop_rule == QPINV_STOP_PAPER_ABS && d < tol)) {
+          polish = true;
+          ck(c, launch_f32_to_f64(fview(S.X[S.cur]), n, m, S.X[S.cur].d, c->st), "X to fp64");
+          S.dbl = true;
+          S.xmode = PM_EMU;
+          S.xS = 8;
+          prev_rel = INFINITY;  // the plateau rule compares polish steps only with each other
+          continue;
+        }
+      } else if (o.precision == QPINV_PREC_MIXED && polish && polish_done >= o.polish_iters) {
+        res.status = (o.stop_rule == QPINV_STOP_PAPER_ABS ? d < tol : drel <= tol) ? QPINV_CONVERGED
+                                                                                   : QPINV_NOT_CONVERGED;
+        break;
+      }
+      prev_rel = drel;
+    }
+    res.tc_iters = tc_done;
+    res.polish_iters = polish_done;
+    if (!S.dbl) {
+      ck(c, launch_f32_to_f64(fview(S.X[S.cur]), n, m, S.X[S.cur].d, c->st), "X to fp64");
+      S.dbl = true;
+    }
+    if (!fp64 && !emu && m != n && res.status != QPINV_DIVERGED) S.range_projection();
+    QMat& Xf = S.X[S.cur];
+    if (o.penrose) {
+      penrose(c, S.A, Xf, fp64 ? PM_F64 : PM_EMU, res.E, res.E_rel, nullptr);
+      if (!fp64) check_kernel_error(c);
+    }
+    res.gemms = S.gemms;
+    store_planes(c, Xf, X, ldx, n, m);
+    ck(c, cudaStreamSynchronize(c->st), "stream sync");
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  res.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (out) *out = res;
+  return QPINV_OK;
+}
+
+int qpinv_qgemm(qpinv_ctx* c, void* stream, int m, int k, int n, const double* const A[4], long lda,
+                const double* const B[4], long ldb, double* const C[4], long ldc, int precision, int split_level) {
+  if (!c) return QPINV_E_INVALID;
+  if (m <= 0 || n <= 0 || k < 0 || lda < k || ldb < n || ldc < n || !planes_ok(A) || !planes_ok(B) ||
+      !planes_ok((const double* const*)C) ||
+      (precision != QPINV_PREC_FP64 && precision != QPINV_PREC_TC && precision != QPINV_PREC_EMU) ||
+      (precision == QPINV_PREC_TC && (split_level < 1 || split_level > 3)) ||
+      (precision == QPINV_PREC_EMU && (split_level < 2 || split_level > 8)))
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    if (precision != QPINV_PREC_FP64 && !tc_supported())
+      return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    const int kk = k > 0 ? k : 1;
+    QMat a = mat(c, "gA", m, kk, MST_D, precision == QPINV_PREC_TC, false);
+    QMat b = mat(c, "gB", kk, n, MST_D, false, precision == QPINV_PREC_TC);
+    QMat cc = mat(c, "gC", m, n, MST_D, false, false);
+    if (k == 0) {
+      ck(c, cudaMemsetAsync(cc.d.p, 0, sizeof(double) * 4 * cc.d.ps, c->st), "memset");
+    } else {
+      load_planes(c, A, lda, m, k, a);
+      load_planes(c, B, ldb, k, n, b);
+      Solver S;
+      S.c = c;
+      S.dbl = true;
+      S.L = precision == QPINV_PREC_TC ? split_level : 0;
+      S.xS = split_level;
+      if (precision == QPINV_PREC_TC) {
+        S.forms(a, true, false);
+        S.forms(b, false, true);
+      }
+      Solver::Acc acc = S.prod(a, b, precision == QPINV_PREC_FP64 ? PM_F64 : (precision == QPINV_PREC_TC ? PM_TC : PM_EMU));
+      S.L = 0;
+      CombineArgs args = S.base_args(m, n, &acc);
+      S.out(args, cc, "f", 1.0);
+      S.run(args);
+      if (precision != QPINV_PREC_FP64) check_kernel_error(c);
+    }
+    store_planes(c, cc, C, ldc, m, n);
+    ck(c, cudaStreamSynchronize(c->st), "stream sync");
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_penrose(qpinv_ctx* c, void* stream, int m, int n, const double* const A[4], long lda,
+                  const double* const X[4], long ldx, double* E, double* E_rel) {
+  if (!c) return QPINV_E_INVALID;
+  if (m <= 0 || n <= 0 || lda < n || ldx < m || !planes_ok(A) || !planes_ok(X) || !E || !E_rel)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    const int mode = c->opt.precision == QPINV_PREC_FP64 ? PM_F64 : PM_EMU;
+    if (mode == PM_EMU && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    QMat a = mat(c, "A", m, n, MST_D, false, false), x = mat(c, "X0", n, m, MST_D, false, false);
+    load_planes(c, A, lda, m, n, a);
+    load_planes(c, X, ldx, n, m, x);
+    penrose(c, a, x, mode, E, E_rel, nullptr);
+    if (mode == PM_EMU) check_kernel_error(c);
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, const int* n, const double* const* A,
+                        const long* lda, qpinv_method method, double tol, int max_iter, double* const* X,
+                        const long* ldx, qpinv_result* out) {
+  (void)stream; (void)batch; (void)m; (void)n; (void)A; (void)lda; (void)method; (void)tol; (void)max_iter;
+  (void)X; (void)ldx; (void)out;
+  if (!c) return QPINV_E_INVALID;
+  return fail(c, QPINV_E_UNSUPPORTED, "batched solver not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libqpinv (include/qpinv.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  The functions mirror the C entry points (qpinv_init, qpinv_solve,
+qpinv_solve_batched, qpinv_free, qpinv_qgemm, qpinv_penrose, ...) and the
+`Context` class wraps them for tensors.
+
+A quaternion matrix is a (4, rows, cols) float64 array of component planes
+(s, x, y, z): a CUDA torch tensor (device pointers) or a CPU torch tensor /
+numpy array (host pointers; the library copies through its own device
+buffers inside the call).  The library must be built (``build.py``); there is
+no fallback -- a missing library raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqpinv.so")
+
+METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3}
+PRECISION = {"fp64": 0, "mixed": 1, "tc": 2, "emu": 3}
+ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3, "learned": 4}
+SIDE = {"auto": 0, "right": 1, "left": 2}
+STOP = {"paper_abs": 0, "rel_plateau": 1}
+STATUS = {0: "converged", 1: "plateau", 2: "not_converged", 3: "diverged"}
+ERRORS = {0: "ok", -1: "invalid", -2: "cuda", -3: "nomem", -4: "nonfinite", -5: "timeout", -6: "unsupported"}
+
+
+class qpinv_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("split_level", ctypes.c_int), ("polish_iters", ctypes.c_int),
+                ("alpha_mode", ctypes.c_int), ("alpha_user", ctypes.c_double), ("qrapid_N", ctypes.c_int),
+                ("side", ctypes.c_int), ("stop_rule", ctypes.c_int), ("penrose", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class qpinv_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("tc_iters", ctypes.c_int),
+                ("polish_iters", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_source", ctypes.c_int),
+                ("side", ctypes.c_int), ("delta", ctypes.c_double), ("delta_rel", ctypes.c_double),
+                ("E", ctypes.c_double * 4), ("E_rel", ctypes.c_double * 4), ("gemms", ctypes.c_longlong),
+                ("time_ms", ctypes.c_double)]
+
+
+class qpinv_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("tc_gemm_launches", ctypes.c_longlong),
+                ("tc_gemm_ms", ctypes.c_double), ("tc_gemm_flops", ctypes.c_double),
+                ("tc_gemm_flops_issued", ctypes.c_double), ("f64_gemm_launches", ctypes.c_longlong),
+                ("f64_gemm_ms", ctypes.c_double), ("f64_gemm_flops", ctypes.c_double),
+                ("ew_launches", ctypes.c_longlong), ("ew_ms", ctypes.c_double), ("ew_bytes", ctypes.c_double)]
+
+
+PTR4 = ctypes.c_void_p * 4
+_lib = None
+
+# every symbol include/qpinv.h declares (checked by the tests)
+EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_solve", "qpinv_solve_batched",
+           "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
+           "qpinv_reset_stats")
+
+
+def lib():
+    """Loads libqpinv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqpinv.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+        L.qpinv_default_options.argtypes = [ctypes.POINTER(qpinv_options)]
+        L.qpinv_default_options.restype = None
+        L.qpinv_init.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(qpinv_options)]
+        L.qpinv_set_options.argtypes = [vp, ctypes.POINTER(qpinv_options)]
+        L.qpinv_solve.argtypes = [vp, vp, i, i, PTR4, l, i, d, i, PTR4, l, ctypes.POINTER(qpinv_result)]
+        L.qpinv_solve_batched.argtypes = [vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(vp),
+                                          ctypes.POINTER(l), i, d, i, ctypes.POINTER(vp), ctypes.POINTER(l),
+                                          ctypes.POINTER(qpinv_result)]
+        L.qpinv_free.argtypes = [vp]
+        L.qpinv_free.restype = None
+        L.qpinv_last_error.argtypes = [vp]
+        L.qpinv_last_error.restype = ctypes.c_char_p
+        L.qpinv_qgemm.argtypes = [vp, vp, i, i, i, PTR4, l, PTR4, l, PTR4, l, i, i]
+        L.qpinv_penrose.argtypes = [vp, vp, i, i, PTR4, l, PTR4, l, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.qpinv_get_stats.argtypes = [vp, ctypes.POINTER(qpinv_stats)]
+        L.qpinv_reset_stats.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- raw names
+
+def qpinv_default_options():
+    o = qpinv_options()
+    lib().qpinv_default_options(ctypes.byref(o))
+    return o
+
+
+def qpinv_init(device=0, options=None):
+    h = ctypes.c_void_p()
+    rc = lib().qpinv_init(ctypes.byref(h), int(device), ctypes.byref(options) if options is not None else None)
+    _check(None, rc, "qpinv_init")
+    return h
+
+
+def qpinv_free(ctx):
+    lib().qpinv_free(ctx)
+
+
+def qpinv_solve(ctx, stream, m, n, A, lda, method, tol, max_iter, X, ldx, result):
+    return lib().qpinv_solve(ctx, stream, m, n, A, lda, method, tol, max_iter, X, ldx, ctypes.byref(result))
+
+
+def qpinv_solve_batched(ctx, stream, batch, m, n, A, lda, method, tol, max_iter, X, ldx, results):
+    return lib().qpinv_solve_batched(ctx, stream, batch, m, n, A, lda, method, tol, max_iter, X, ldx, results)
+
+
+def _check(ctx, rc, what):
+    if rc != 0:
+        msg = lib().qpinv_last_error(ctx).decode() if ctx is not None else ""
+        raise QpinvError(rc, "%s failed: %s (%s)" % (what, ERRORS.get(rc, rc), msg))
+
+
+class QpinvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(msg)
+        self.code = code
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _planes(x):
+    """(4, r, c) float64 array/tensor -> (PTR4, ld, keepalive)."""
+    if _is_torch(x):
+        assert x.dtype.is_floating_point and x.element_size() == 8 and x.dim() == 3 and x.shape[0] == 4
+        assert x.stride(2) == 1 and x.stride(1) >= x.shape[2], "rows must be contiguous"
+        base, es = x.data_ptr(), 8
+        p = PTR4(*[base + c * x.stride(0) * es for c in range(4)])
+        return p, x.stride(1), x
+    a = np.asarray(x)
+    assert a.dtype == np.float64 and a.ndim == 3 and a.shape[0] == 4
+    if not (a.flags.c_contiguous):
+        a = np.ascontiguousarray(a)
+    base = a.ctypes.data
+    p = PTR4(*[base + c * a.strides[0] for c in range(4)])
+    return p, a.strides[1] // 8, a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Context:
+    """A libqpinv context bound to one CUDA device."""
+
+    def __init__(self, device=0, precision="mixed", split_level=0, polish_iters=2, alpha="safe",
+                 alpha_user=0.0, qrapid_N=5, side="auto", stop="rel_plateau", penrose=True, profile=False):
+        self.options = qpinv_default_options()
+        self.device = device
+        self.configure(precision=precision, split_level=split_level, polish_iters=polish_iters, alpha=alpha,
+                       alpha_user=alpha_user, qrapid_N=qrapid_N, side=side, stop=stop, penrose=penrose,
+                       profile=profile, _apply=False)
+        self.h = qpinv_init(device, self.options)
+
+    def configure(self, precision=None, split_level=None, polish_iters=None, alpha=None, alpha_user=None,
+                  qrapid_N=None, side=None, stop=None, penrose=None, profile=None, _apply=True):
+        o = self.options
+        if precision is not None: o.precision = PRECISION[precision]
+        if split_level is not None: o.split_level = int(split_level)
+        if polish_iters is not None: o.polish_iters = int(polish_iters)
+        if alpha is not None: o.alpha_mode = ALPHA[alpha]
+        if alpha_user is not None: o.alpha_user = float(alpha_user)
+        if qrapid_N is not None: o.qrapid_N = int(qrapid_N)
+        if side is not None: o.side = SIDE[side]
+        if stop is not None: o.stop_rule = STOP[stop]
+        if penrose is not None: o.penrose = int(bool(penrose))
+        if profile is not None: o.profile = int(bool(profile))
+        if _apply:
+            _check(self.h, lib().qpinv_set_options(self.h, ctypes.byref(o)), "qpinv_set_options")
+
+    def close(self):
+        if getattr(self, "h", None):
+            qpinv_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, A, method="qhpi19", tol=1e-12, max_iter=500, X=None, stream=None):
+        """Returns (X, info).  X is allocated like A (same device) unless given."""
+        m, n = A.shape[1], A.shape[2]
+        if X is None:
+            if _is_torch(A):
+                import torch
+                X = torch.empty((4, n, m), dtype=torch.float64, device=A.device)
+            else:
+                X = np.empty((4, n, m))
+        pa, lda, ka = _planes(A)
+        px, ldx, kx = _planes(X)
+        res = qpinv_result()
+        rc = qpinv_solve(self.h, _stream_handle(stream), m, n, pa, lda, METHODS[method], float(tol),
+                         int(max_iter), px, ldx, res)
+        _check(self.h, rc, "qpinv_solve")
+        if kx is not X:  # host copy made for contiguity
+            X[...] = kx
+        return X, result_dict(res)
+
+    def solve_batched(self, As, method="qhpi19", tol=1e-6, max_iter=100, Xs=None, stream=None):
+        import torch
+        b = len(As)
+        if Xs is None:
+            Xs = [torch.empty((4, a.shape[2], a.shape[1]), dtype=torch.float64, device=a.device) for a in As]
+        m = (ctypes.c_int * b)(*[a.shape[1] for a in As])
+        n = (ctypes.c_int * b)(*[a.shape[2] for a in As])
+        ap = (ctypes.c_void_p * (4 * b))()
+        xp = (ctypes.c_void_p * (4 * b))()
+        lda = (ctypes.c_long * b)()
+        ldx = (ctypes.c_long * b)()
+        for t, (a, x) in enumerate(zip(As, Xs)):
+            pa, la, _ = _planes(a)
+            px, lx, _ = _planes(x)
+            for c in range(4):
+                ap[4 * t + c] = pa[c]
+                xp[4 * t + c] = px[c]
+            lda[t], ldx[t] = la, lx
+        res = (qpinv_result * b)()
+        rc = qpinv_solve_batched(self.h, _stream_handle(stream), b, m, n, ap, lda, METHODS[method], float(tol),
+                                 int(max_iter), xp, ldx, res)
+        _check(self.h, rc, "qpinv_solve_batched")
+        return Xs, [result_dict(r) for r in res]
+
+    def qgemm(self, A, B, precision="tc", split_level=3, C=None, stream=None):
+        m, k = A.shape[1], A.shape[2]
+        n = B.shape[2]
+        if C is None:
+            if _is_torch(A):
+                import torch
+                C = torch.empty((4, m, n), dtype=torch.float64, device=A.device)
+            else:
+                C = np.empty((4, m, n))
+        pa, lda, _ka = _planes(A)
+        pb, ldb, _kb = _planes(B)
+        pc, ldc, _kc = _planes(C)
+        rc = lib().qpinv_qgemm(self.h, _stream_handle(stream), m, k, n, pa, lda, pb, ldb, pc, ldc,
+                               PRECISION[precision], int(split_level))
+        _check(self.h, rc, "qpinv_qgemm")
+        return C
+
+    def penrose(self, A, X, stream=None):
+        m, n = A.shape[1], A.shape[2]
+        pa, lda, _ka = _planes(A)
+        px, ldx, _kx = _planes(X)
+        E = (ctypes.c_double * 4)()
+        R = (ctypes.c_double * 4)()
+        rc = lib().qpinv_penrose(self.h, _stream_handle(stream), m, n, pa, lda, px, ldx, E, R)
+        _check(self.h, rc, "qpinv_penrose")
+        return list(E), list(R)
+
+    def stats(self):
+        s = qpinv_stats()
+        _check(self.h, lib().qpinv_get_stats(self.h, ctypes.byref(s)), "qpinv_get_stats")
+        return {f: getattr(s, f) for f, _ in qpinv_stats._fields_}
+
+    def reset_stats(self):
+        _check(self.h, lib().qpinv_reset_stats(self.h), "qpinv_reset_stats")
+
+
+def result_dict(r):
+    return dict(status=STATUS.get(r.status, r.status), iters=r.iters, tc_iters=r.tc_iters,
+                polish_iters=r.polish_iters, alpha=r.alpha, alpha_source=r.alpha_source,
+                side="left" if r.side == 2 else "right", delta=r.delta, delta_rel=r.delta_rel,
+                E=list(r.E), E_rel=list(r.E_rel), gemms=r.gemms, time_ms=r.time_ms)

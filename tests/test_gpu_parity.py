@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (relative Frobenius error of X against the oracle's X):
+  * FP64 products, or mixed precision with the FP64-residual polish: 1e-10;
+  * tensor-core products only (FP32-level accumulation):              1e-5.
+Quaternion GEMMs are checked against the oracle product with the error a
+BF16 split of L terms allows with FP32 tensor-core accumulation (whose error
+grows with K; K <= 1000 here): L = 1: 1e-2, L = 2: 3e-4, L = 3: 5e-5; FP64: 1e-13.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_01464_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GEMM_TOL = {1: 1e-2, 2: 3e-4, 3: 5e-5}
+
+
+@pytest.fixture(scope="module")
+def qp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_01464_gb300 import build, qpinv
+    build.build()
+    return qpinv
+
+
+@pytest.fixture()
+def ctx(qp):
+    c = qp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (7, 5, 3), (33, 65, 129), (130, 70, 257)])
+def test_qgemm_fp64_matches_oracle(ctx, m, k, n):
+    A = I.gaussian_quaternion(m, k, 1)
+    B = I.gaussian_quaternion(k, n, 2)
+    C = ctx.qgemm(dev(A), dev(B), precision="fp64").cpu().numpy()
+    assert rel(C, oracle.matmul(A, B)) <= 1e-13
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+@pytest.mark.parametrize("m,k,n", [(128, 64, 64), (200, 130, 90), (1, 1, 1), (257, 300, 129), (64, 1000, 40)])
+def test_qgemm_tc_matches_oracle(ctx, L, m, k, n):
+    A = I.gaussian_quaternion(m, k, 3)
+    B = I.gaussian_quaternion(k, n, 4)
+    C = ctx.qgemm(dev(A), dev(B), precision="tc", split_level=L).cpu().numpy()
+    assert rel(C, oracle.matmul(A, B)) <= GEMM_TOL[L]
+
+
+def test_qgemm_tc_each_sign_block(ctx):
+    """Unit quaternion matrices isolate each (A component, B component) block
+    of the real form: A = e_r * ones, B = e_s * eye; C must be e_r e_s."""
+    basis = np.eye(4)
+    for r in range(4):
+        for s in range(4):
+            A = np.zeros((4, 16, 16))
+            A[r] = 1.0
+            B = np.zeros((4, 16, 16))
+            B[s] = np.eye(16)
+            C = ctx.qgemm(dev(A), dev(B), precision="tc", split_level=1).cpu().numpy()
+            want = oracle.qmul(basis[r], basis[s])
+            assert np.allclose(C, want[:, None, None] * np.ones((1, 16, 16)), atol=0), (r, s)
+
+
+METHODS = [("ns", 5), ("qsai", 5), ("qhpi19", 5), ("qrapid", 5), ("qrapid", 0), ("qrapid", 1)]
+
+
+@pytest.mark.parametrize("method,N", METHODS)
+@pytest.mark.parametrize("precision,tol_x", [("fp64", 1e-10), ("mixed", 1e-10), ("emu", 1e-10), ("tc", 1e-5)])
+def test_solve_dense_gaussian_64x48(ctx, method, N, precision, tol_x):
+    A = I.dense_gaussian(64, 48, seed=0)
+    ctx.configure(precision=precision, qrapid_N=N)
+    X, info = ctx.solve(dev(A), method, tol=1e-12, max_iter=200)
+    Xo, oinfo = oracle.solve(A, method, tol=1e-12, max_iter=200, N=N)
+    assert info["status"] in ("converged", "plateau", "not_converged"), info
+    assert rel(X.cpu().numpy(), Xo) <= tol_x, (rel(X.cpu().numpy(), Xo), info)
+    if precision != "tc":
+        assert info["E_rel"][0] <= 1e-12, info
+    assert info["side"] == "left"  # 64 x 48 is tall: residual on the 48 side
+
+
+@pytest.mark.parametrize("method", ["ns", "qsai", "qhpi19", "qrapid"])
+@pytest.mark.parametrize("shape,side", [((40, 96), "auto"), ((96, 40), "auto"), ((96, 40), "right"),
+                                        ((40, 96), "left"), ((70, 70), "left")])
+def test_solve_sides_and_shapes(ctx, method, shape, side):
+    m, n = shape
+    A = I.gaussian_quaternion(m, n, 7)
+    ctx.configure(precision="mixed", side=side, qrapid_N=2)
+    X, info = ctx.solve(dev(A), method, tol=1e-13, max_iter=200)
+    Xo, _ = oracle.solve(A, method, tol=1e-13, max_iter=200, N=2)
+    assert rel(X.cpu().numpy(), Xo) <= 1e-10, info
+
+
+@pytest.mark.parametrize("method", ["ns", "qsai", "qhpi19", "qrapid"])
+@pytest.mark.parametrize("precision", ["emu", "fp64"])
+def test_solve_rank_deficient(ctx, method, precision):
+    """Rank-deficient input: null-space rounding noise grows by the method's
+    order per step -- about kappa^2 over a solve -- so these run with
+    FP64-accurate products throughout, and X is accurate to about
+    kappa^2 * eps (kappa = 1e3 here); the FP64 oracle agrees to the same level."""
+    A, QL, s, QR = I.rank_deficient(80, 60, 20, 1e-3, seed_l=4, seed_r=5)
+    ctx.configure(precision=precision, qrapid_N=3)
+    X, info = ctx.solve(dev(A), method, tol=1e-13, max_iter=300)
+    want = oracle.pinv_from_svd(QL, s, QR)
+    assert info["status"] in ("converged", "plateau"), info
+    assert rel(X.cpu().numpy(), want) <= 1e-8, (rel(X.cpu().numpy(), want), info)
+    Xo, _ = oracle.solve(A, method, tol=1e-13, max_iter=300, N=3)
+    assert rel(Xo, want) <= 1e-8
+    assert info["E_rel"][0] <= 1e-12
+
+
+def test_example1_iteration_counts_and_values(ctx):
+    from tests.test_oracle_pins import load_example1
+    A, P, vals = load_example1()
+    ctx.configure(precision="fp64", alpha="spectral", stop="paper_abs")
+    for method, N in [("qsai", 5), ("qhpi19", 5), ("qrapid", 1)]:
+        ctx.configure(qrapid_N=N)
+        X, info = ctx.solve(dev(A), method, tol=1e-10, max_iter=100)
+        assert abs(info["alpha"] - vals["alpha"]) <= 0.5e-9
+        assert info["iters"] == vals[("iters", method)], (method, info)
+        assert np.max(np.abs(X.cpu().numpy() - P)) <= 0.5e-4 + 1e-12
+        assert max(info["E"]) <= vals["Emax"]
+
+
+def test_nonfinite_input_rejected(ctx, qp):
+    A = I.gaussian_quaternion(10, 8, 1)
+    A[2, 3, 4] = np.nan
+    with pytest.raises(qp.QpinvError) as e:
+        ctx.solve(dev(A), "qhpi19")
+    assert e.value.code == -4
+
+
+def test_max_iter_one_not_converged(ctx):
+    A = I.gaussian_quaternion(20, 12, 2)
+    X, info = ctx.solve(dev(A), "ns", tol=1e-14, max_iter=1)
+    assert info["status"] == "not_converged" and info["iters"] == 1
+    Xo, _ = oracle.solve(A, "ns", tol=1e-14, max_iter=1)
+    ctx.configure(precision="fp64")
+    X, info = ctx.solve(dev(A), "ns", tol=1e-14, max_iter=1)
+    assert rel(X.cpu().numpy(), Xo) <= 1e-13
+
+
+def test_divergent_alpha_detected(ctx):
+    A = I.gaussian_quaternion(16, 12, 5)
+    smax = oracle.sigma_max(A)
+    ctx.configure(precision="fp64", alpha="user", alpha_user=3.0 / smax ** 2)
+    X, info = ctx.solve(dev(A), "qhpi19", tol=1e-14, max_iter=60)
+    assert info["status"] == "diverged"
+    assert np.all(np.isfinite(X.cpu().numpy()))
+
+
+def test_host_pointers_match_device(ctx):
+    A = I.gaussian_quaternion(50, 30, 11)
+    Xd, _ = ctx.solve(dev(A), "qsai", tol=1e-12)
+    Xh, _ = ctx.solve(A.copy(), "qsai", tol=1e-12)
+    assert isinstance(Xh, np.ndarray)
+    assert np.array_equal(Xd.cpu().numpy(), Xh)
+
+
+def test_penrose_matches_oracle(ctx):
+    A = I.gaussian_quaternion(30, 20, 12)
+    Xo, _ = oracle.solve(A, "qhpi19", tol=1e-6, max_iter=3)
+    E, R = ctx.penrose(dev(A), dev(Xo))
+    Eo, Ro = oracle.penrose(A, Xo)
+    assert np.allclose(E, Eo, rtol=1e-8, atol=1e-14)
+    assert np.allclose(R, Ro, rtol=1e-8, atol=1e-14)
+
+
+def test_spectral_alpha_matches_oracle(ctx):
+    A = I.gaussian_quaternion(40, 25, 13)
+    ctx.configure(alpha="spectral")
+    _, info = ctx.solve(dev(A), "qhpi19", tol=1e-12)
+    assert abs(info["alpha"] - oracle.alpha(A, "spectral")) <= 1e-9 * info["alpha"]
+
+
+def test_gemm_counts_per_iteration(ctx):
+    A = I.gaussian_quaternion(24, 24, 14)
+    ctx.configure(precision="tc", penrose=False, stop="paper_abs")
+    for method, N, per in [("ns", 0, 2), ("qsai", 0, 6), ("qhpi19", 0, 7), ("qrapid", 2, 12)]:
+        ctx.configure(qrapid_N=N)
+        _, info = ctx.solve(dev(A), method, tol=0.0, max_iter=3)
+        assert info["gemms"] == 3 * per, (method, info)
+
+
+EMU_TOL = {2: 1e-3, 4: 1e-7, 6: 1e-11, 8: 1e-14}
+
+
+@pytest.mark.parametrize("S", [2, 4, 6, 8])
+@pytest.mark.parametrize("m,k,n", [(130, 300, 257), (64, 1000, 40), (1, 1, 1), (200, 64, 90)])
+def test_qgemm_exact_slices_match_oracle(ctx, S, m, k, n):
+    """Exact-slice products: S slices of 7 bits per operand; 8 slices give an
+    FP64-level product (the oracle's own rounding is the reference)."""
+    A = I.gaussian_quaternion(m, k, 5)
+    B = I.gaussian_quaternion(k, n, 6)
+    C = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=S).cpu().numpy()
+    assert rel(C, oracle.matmul(A, B)) <= EMU_TOL[S], rel(C, oracle.matmul(A, B))
+
+
+def test_qgemm_exact_slices_wide_dynamic_range(ctx):
+    """Rows and columns spanning 2^-40 .. 2^40: per-row/column power-of-two
+    scaling keeps every entry FP64-accurate relative to its row/column scale."""
+    rng = np.random.default_rng(3)
+    A = I.gaussian_quaternion(96, 128, 7) * np.exp2(rng.integers(-40, 40, size=(1, 96, 1)))
+    B = I.gaussian_quaternion(128, 80, 8) * np.exp2(rng.integers(-40, 40, size=(1, 1, 80)))
+    C = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=8).cpu().numpy()
+    Co = oracle.matmul(A, B)
+    scale = np.abs(A).max(axis=(0, 2))[:, None] * np.abs(B).max(axis=(0, 1))[None, :] * 128
+    assert np.max(np.abs(C - Co) / scale[None]) <= 1e-15
+
+
+@pytest.mark.parametrize("method", ["qhpi19", "qsai", "ns"])
+def test_solve_logspaced_kappa_1e6(ctx, method):
+    """Square A = U diag(sigma) V^H with sigma log-spaced 1..1e-6 (the large
+    workload's structure at n = 256): mixed precision must reach the FP64
+    level: E1/||A|| <= 1e-10 and X within 1e-8 of the exact V Sigma^-1 U^H."""
+    A, U, s, V = I.logspaced_square(256, 1e-6, seed_u=1, seed_v=2)
+    X, info = ctx.solve(dev(A), method, tol=1e-12, max_iter=200)
+    want = oracle.pinv_from_svd(U, s, V)
+    assert info["E_rel"][0] <= 1e-10, info
+    assert rel(X.cpu().numpy(), want) <= 1e-8, (rel(X.cpu().numpy(), want), info)
+    Eo, Ro = oracle.penrose(A, X.cpu().numpy())
+    assert Ro[0] <= 1e-10  # the oracle's own FP64 evaluation of E1 agrees with the bound

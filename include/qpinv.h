@@ -49,6 +49,10 @@ extern "C" {
 #define QPINV_E_NONFINITE (-4)    /* A contains NaN or Inf */
 #define QPINV_E_TIMEOUT (-5)      /* a device-side bounded wait expired (kernel aborted cleanly) */
 #define QPINV_E_UNSUPPORTED (-6)  /* option combination not available on this device */
+#define QPINV_E_NOALLOC_LIMIT (-7) /* qpinv_qgemm_noalloc: a dimension exceeds QPINV_NOALLOC_MAX_DIM */
+
+/* Largest m, k and n accepted by qpinv_qgemm_noalloc. */
+#define QPINV_NOALLOC_MAX_DIM 256
 
 /* ---- solver outcome (qpinv_result.status) ----------------------------- */
 #define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
@@ -192,6 +196,30 @@ int qpinv_qgemm(qpinv_ctx* ctx, void* stream, int m, int k, int n, const double*
  * E_rel = E / (||A||_F, ||X||_F, ||AX||_F, ||XA||_F).  E, E_rel: host arrays of 4. */
 int qpinv_penrose(qpinv_ctx* ctx, void* stream, int m, int n, const double* const A[4], long lda,
                   const double* const X[4], long ldx, double* E, double* E_rel);
+
+/* Allocation-free quaternion GEMM (the paper has no counterpart: this is a
+ * deployment convenience).  Computes C = A B like qpinv_qgemm with
+ * QPINV_PREC_TC and `split_level` = 1..3 BF16 terms, for callers that may not
+ * allocate device memory when they need the product -- code inside a memory
+ * pool or arena that forbids new cudaMalloc calls, loops that must not touch
+ * the allocator after start-up, or callers without a qpinv context (a
+ * context allocates its workspace on first use).  All its scratch lives in a
+ * fixed array of about 4 MiB that every GPU loading the library holds until
+ * the process exits; it calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   - A (m x k), B (k x n), C (m x n): four FP64 planes each, DEVICE pointers
+ *     only, row-major with leading dimensions lda >= k, ldb >= n, ldc >= n;
+ *     1 <= m, k, n <= QPINV_NOALLOC_MAX_DIM, else QPINV_E_NOALLOC_LIMIT;
+ *     host pointers give QPINV_E_INVALID.  C must not alias A or B.
+ *   - Runs on the caller's current device and on `stream`; returns after the
+ *     product is complete (it reads back the kernel's error word).
+ *   - The first call on each device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - Every call shares the one array: calls whose work may overlap on the GPU
+ *     (other streams, unsynchronised host threads) race and must be
+ *     serialised by the caller. */
+int qpinv_qgemm_noalloc(void* stream, int m, int k, int n, const double* const A[4], long lda,
+                        const double* const B[4], long ldb, double* const C[4], long ldc, int split_level);
 
 /* Kernel counters and (with profile = 1) CUDA-event timings since the last reset. */
 int qpinv_get_stats(qpinv_ctx* ctx, qpinv_stats* stats);

@@ -25,7 +25,9 @@ ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3, "learned": 4}
 SIDE = {"auto": 0, "right": 1, "left": 2}
 STOP = {"paper_abs": 0, "rel_plateau": 1}
 STATUS = {0: "converged", 1: "plateau", 2: "not_converged", 3: "diverged"}
-ERRORS = {0: "ok", -1: "invalid", -2: "cuda", -3: "nomem", -4: "nonfinite", -5: "timeout", -6: "unsupported"}
+ERRORS = {0: "ok", -1: "invalid", -2: "cuda", -3: "nomem", -4: "nonfinite", -5: "timeout", -6: "unsupported",
+          -7: "noalloc_limit"}
+NOALLOC_MAX_DIM = 256
 
 
 class qpinv_options(ctypes.Structure):
@@ -57,7 +59,7 @@ _lib = None
 # every symbol include/qpinv.h declares (checked by the tests)
 EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_solve", "qpinv_solve_batched",
            "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
-           "qpinv_reset_stats")
+           "qpinv_reset_stats", "qpinv_qgemm_noalloc")
 
 
 def lib():
@@ -84,6 +86,7 @@ def lib():
         L.qpinv_penrose.argtypes = [vp, vp, i, i, PTR4, l, PTR4, l, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.qpinv_get_stats.argtypes = [vp, ctypes.POINTER(qpinv_stats)]
         L.qpinv_reset_stats.argtypes = [vp]
+        L.qpinv_qgemm_noalloc.argtypes = [vp, i, i, i, PTR4, l, PTR4, l, PTR4, l, i]
         _lib = L
     return _lib
 
@@ -113,6 +116,17 @@ def qpinv_solve(ctx, stream, m, n, A, lda, method, tol, max_iter, X, ldx, result
 
 def qpinv_solve_batched(ctx, stream, batch, m, n, A, lda, method, tol, max_iter, X, ldx, results):
     return lib().qpinv_solve_batched(ctx, stream, batch, m, n, A, lda, method, tol, max_iter, X, ldx, results)
+
+
+def qpinv_qgemm_noalloc(A, B, C, split_level=3, stream=None):
+    """C = A B through the allocation-free entry point (CUDA tensors of
+    shape (4, m, k), (4, k, n), (4, m, n), float64).  Returns the C-ABI code."""
+    m, k = A.shape[1], A.shape[2]
+    n = B.shape[2]
+    pa, lda, _ka = _planes(A)
+    pb, ldb, _kb = _planes(B)
+    pc, ldc, _kc = _planes(C)
+    return lib().qpinv_qgemm_noalloc(_stream_handle(stream), m, k, n, pa, lda, pb, ldb, pc, ldc, int(split_level))
 
 
 def _check(ctx, rc, what):

@@ -154,10 +154,31 @@ def run_reference(args, rank):
     return 0
 
 
+def kernel_qgemm(args, torch, qpinv):
+    """Times the tcgen05 quaternion GEMM alone on seeded n x n operands."""
+    from paper_2605_01464_gb300 import inputs
+    n = args.n
+    A = torch.from_numpy(inputs.gaussian_quaternion(n, n, 21)).cuda()
+    B = torch.from_numpy(inputs.gaussian_quaternion(n, n, 22)).cuda()
+    ctx = qpinv.Context(0, profile=True)
+    for _ in range(args.warmup):
+        ctx.qgemm(A, B, precision="tc", split_level=args.split)
+    ctx.reset_stats()
+    for _ in range(args.steps):
+        ctx.qgemm(A, B, precision="tc", split_level=args.split)
+    st = ctx.stats()
+    ms = st["tc_gemm_ms"] / max(st["tc_gemm_launches"], 1)
+    print(json.dumps({"kernel": "k_qgemm_tc", "n": n, "split": args.split, "ms_per_launch": ms,
+                      "tflops_algorithmic": st["tc_gemm_flops"] / st["tc_gemm_launches"] / ms / 1e9,
+                      "tflops_issued": st["tc_gemm_flops_issued"] / st["tc_gemm_launches"] / ms / 1e9}))
+    return 0
+
+
 def workload_config(args):
     return {"workload": "square %dx%d quaternion A = U diag(sigma) V^H, Haar U and V, sigma log-spaced 1..1e-6; "
-                        "%s, mixed precision (BF16x6 tensor cores, %d FP64-residual polish iterations), "
-                        "safe fixed alpha, rel. tol %g, FP64 Penrose residuals" %
+                        "%s, mixed precision (BF16-split tensor-core products with FP32 accumulation; exact-slice "
+                        "tensor-core X-products once ||A|| ||X|| > 1e3; %d polish iterations with FP64 masters and "
+                        "FP64-accurate X-products), safe fixed alpha, rel. tol %g, FP64-accurate Penrose residuals" %
                         (args.n, args.n, args.method.upper(), args.polish, args.tol),
             "m": args.n, "n": args.n, "method": args.method, "precision": "mixed",
             "l2": "inputs exceed L2 (A alone is 134 MB of FP64 planes; no flush)"}
@@ -175,6 +196,11 @@ def main():
     ap.add_argument("--polish", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["qgemm"],
+                    help="time only the tensor-core quaternion GEMM (n x n x n) for kernel profiling")
+    ap.add_argument("--split", type=int, default=1, help="BF16 terms of --kernel qgemm (1..3)")
+    ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
+                    help="device that builds the synthetic input (cpu under profilers)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -191,12 +217,14 @@ def main():
 
     libbuild.build()
     torch.cuda.set_device(local)
+    if args.kernel == "qgemm":
+        return kernel_qgemm(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    A_host = make_workload(args.n, "cuda:%d" % local)
+    A_host = make_workload(args.n, "cuda:%d" % local if args.gen_device == "cuda" else "cpu")
     A = torch.from_numpy(A_host).cuda()
     stream = torch.cuda.current_stream()
     ctx = qpinv.Context(local, precision="mixed", polish_iters=args.polish, profile=True)
@@ -261,7 +289,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x6-split f32-acc + f64 residuals", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16-split/f32-acc + exact-slice f64", "data": "synthetic",
         "config": workload_config(args),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved / bf16_sust, "traffic": None,

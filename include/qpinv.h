@@ -95,7 +95,9 @@ enum { QPINV_STOP_PAPER_ABS = 0,  /* ||X_{j+1} - X_j||_F < tol (Algorithms 1-3) 
 
 typedef struct {
   int precision;     /* QPINV_PREC_FP64, _MIXED, _TC or _EMU; default MIXED */
-  int split_level;   /* tensor-core operand terms: 1 = bf16, 2 = bf16x3, 3 = bf16x6; 0 = automatic (default) */
+  int split_level;   /* BF16 terms of the tensor-core R-products (polynomials in R): 1 = bf16,
+                        2 = bf16x3, 3 = bf16x6; 0 = automatic (2).  X-products use 3 terms
+                        or exact slices (see QPINV_PREC_MIXED) */
   int polish_iters;  /* MIXED: iterations with an FP64 residual at the end (default 2) */
   int alpha_mode;    /* QPINV_ALPHA_*, default SAFE */
   double alpha_user; /* used with QPINV_ALPHA_USER */

@@ -120,6 +120,7 @@ struct TcGemmArgs {
   const Split16* B = nullptr;  // uses the B-form
   int npairs = 0;
   int pair_i[16] = {0}, pair_j[16] = {0};
+  int pair_acc[16] = {0};  // TMEM accumulator of each pair (1 only with C64: the two are summed)
   Planes<float> C;  // FP32 output
   int* err = nullptr;  // device error word (bounded-wait expiry)
 };

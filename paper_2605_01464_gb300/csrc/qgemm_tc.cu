@@ -38,11 +38,11 @@ constexpr int A_PLANE_BYTES = BM * BK * 2;
 constexpr int B_PLANE_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 4 * (A_PLANE_BYTES + B_PLANE_BYTES);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int TMEM_COLS = 4 * BN;  // power of two >= 32
+constexpr int ACC_COLS = 4 * BN;  // TMEM columns of one accumulator (four output components)
 constexpr int THREADS = 192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
-static_assert(TMEM_COLS == 256, "TMEM allocation must be a power of two");
+static_assert(ACC_COLS == 256, "TMEM allocations must be powers of two (256 or 512 columns)");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -140,6 +140,9 @@ struct KParams {
   int kb0, kb1;  // K blocks [kb0, kb1) of BK elements
   int npairs;
   int pi[16], pj[16];
+  int pacc[16];   // accumulator (0 or 1) of each pair
+  int pfirst[16]; // 1 if the pair is the first of its accumulator
+  int nacc;       // 1 or 2 accumulators (2 only with int64 output)
   Planes<float> C;
   long long* C64;  // non-null: int64 fixed-point accumulation
   long ld64, ps64;
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nunits = (P.kb1 - P.kb0) * P.npairs;
+  const uint32_t tmem_cols = P.nacc == 2 ? 2 * ACC_COLS : ACC_COLS;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -210,6 +214,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_after();
         uint8_t* st = smem + (size_t)s * STAGE_BYTES;
         const uint32_t a_base = smem_u32(st), b_base = smem_u32(st + 4 * A_PLANE_BYTES);
+        const int pr = u % P.npairs;
+        const uint32_t dacc = tmem + (uint32_t)(P.pacc[pr] * ACC_COLS);
+        const bool fresh = u < P.npairs && P.pfirst[pr];  // first K block of this accumulator
 #pragma unroll
         for (int kk = 0; kk < BK / 16; kk++) {
 #pragma unroll
@@ -221,8 +228,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
                                (r == 3 && (c == 0 || c == 1));
               const uint64_t bd = smem_desc(b_base + bp * B_PLANE_BYTES + kk * 32);
-              const uint32_t acc = (u > 0 || kk > 0 || r > 0) ? 1u : 0u;
-              mma_bf16(tmem + c * BN, ad, bd, neg ? IDESC_NEG_A : IDESC, acc);
+              const uint32_t acc = (!fresh || kk > 0 || r > 0) ? 1u : 0u;
+              mma_bf16(dacc + c * BN, ad, bd, neg ? IDESC_NEG_A : IDESC, acc);
             }
           }
         }
@@ -246,17 +253,22 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int c = 0; c < 4; c++) {
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ch++) {
-          float v[32];
+          float v[32], v2[32];
           if (nunits > 0) {
             tmem_ld32(tbase + c * BN + ch * 32, v);
+            if (P.nacc == 2) tmem_ld32(tbase + ACC_COLS + c * BN + ch * 32, v2);
           } else {
 #pragma unroll
-            for (int t = 0; t < 32; t++) v[t] = 0.f;
+            for (int t = 0; t < 32; t++) v[t] = v2[t] = 0.f;
           }
           if (row < P.M && P.C64) {
             long long* dst = P.C64 + c * P.ps64 + (long)row * P.ld64 + n0 + ch * 32;
             const int ncol = min(32, P.N - (n0 + ch * 32));
-            for (int t = 0; t < ncol; t++) dst[t] += __float2ll_rn(v[t] * P.scale);
+            if (P.nacc == 2) {
+              for (int t = 0; t < ncol; t++) dst[t] += __float2ll_rn(v[t] * P.scale) + __float2ll_rn(v2[t] * P.scale);
+            } else {
+              for (int t = 0; t < ncol; t++) dst[t] += __float2ll_rn(v[t] * P.scale);
+            }
           } else if (row < P.M) {
             float* dst = P.C.p + c * P.C.ps + (long)row * P.C.ld + n0 + ch * 32;
             const int ncol = min(32, P.N - (n0 + ch * 32));
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
   }
 }
 
@@ -335,9 +347,14 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   if ((a.A->lda % 8) || (a.A->psa % 8) || (a.B->ldb % 8) || (a.B->psb % 8)) return cudaErrorInvalidValue;
   if ((a.k0 % BK) != 0 || (a.k1 != a.K && (a.k1 % BK) != 0) || a.k0 < 0 || a.k1 > a.K || a.k0 > a.k1)
     return cudaErrorInvalidValue;
-  for (int p = 0; p < a.npairs; p++)
-    if (a.pair_i[p] < 0 || a.pair_i[p] >= a.A->levels || a.pair_j[p] < 0 || a.pair_j[p] >= a.B->levels)
+  int nacc = 1;
+  for (int p = 0; p < a.npairs; p++) {
+    if (a.pair_i[p] < 0 || a.pair_i[p] >= a.A->levels || a.pair_j[p] < 0 || a.pair_j[p] >= a.B->levels ||
+        a.pair_acc[p] < 0 || a.pair_acc[p] > 1)
       return cudaErrorInvalidValue;
+    if (a.pair_acc[p] == 1) nacc = 2;
+  }
+  if (nacc == 2 && !a.C64) return cudaErrorInvalidValue;  // two accumulators only sum into int64
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM)) return cudaErrorInvalidValue;
   if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, BN)) return cudaErrorInvalidValue;
@@ -353,10 +370,18 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   P.kb0 = a.k0 / BK;
   P.kb1 = (a.k1 + BK - 1) / BK;
   P.npairs = a.npairs;
+  bool seen[2] = {false, false};
   for (int p = 0; p < 16; p++) {
     P.pi[p] = p < a.npairs ? a.pair_i[p] : 0;
     P.pj[p] = p < a.npairs ? a.pair_j[p] : 0;
+    P.pacc[p] = p < a.npairs ? a.pair_acc[p] : 0;
+    P.pfirst[p] = 0;
+    if (p < a.npairs && !seen[P.pacc[p]]) {
+      P.pfirst[p] = 1;
+      seen[P.pacc[p]] = true;
+    }
   }
+  P.nacc = nacc;
   P.C = a.C;
   P.C64 = a.C64;
   P.ld64 = a.ld64;

@@ -31,6 +31,7 @@
 //     slices, 56 bits); R-products stay on BF16 splits.
 // Penrose residuals use FP64-accurate products (exact slices, or the
 // CUDA-core FP64 kernel in the FP64 form).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -252,7 +253,10 @@ struct Solver {
   bool left = false;
   int s = 0;              // residual side (s x s)
   bool dbl = false;       // master type of the current phase: double (true) or float
-  int L = 3;              // BF16 split terms of tensor-core products (0: every product in FP64)
+  int L = 3;              // BF16 split terms written for tensor-core operands (0: every product in FP64)
+  int Lr = 2;             // BF16 split terms of tensor-core R-products
+  int Lx = 3;             // BF16 split terms of tensor-core X-products
+  int Lcur = 3;           // split terms of the product being issued
   int xmode = PM_TC;      // mode of the X-products this iteration
   int rmode = -1;         // mode of the R-products (-1: PM_F64 if L == 0, else PM_TC)
   int xS = 8;             // exact slices of X-products in PM_EMU mode
@@ -272,7 +276,10 @@ struct Solver {
     int shift;
   };
 
-  Acc rprod(const QMat& P, const QMat& Q) { return prod(P, Q, rmode >= 0 ? rmode : (L == 0 ? PM_F64 : PM_TC)); }
+  Acc rprod(const QMat& P, const QMat& Q) {
+    Lcur = Lr;
+    return prod(P, Q, rmode >= 0 ? rmode : (L == 0 ? PM_F64 : PM_TC));
+  }
 
   // acc(rows x cols) = P (rows x K) * Q (K x cols) in one of three modes:
   //   PM_TC  - tcgen05 on BF16 splits (L terms), FP32 accumulation;
@@ -307,10 +314,10 @@ struct Solver {
     g.B = &Q.s16;
     static const int pi3[6] = {2, 1, 0, 1, 0, 0}, pj3[6] = {0, 1, 2, 0, 1, 0};
     static const int pi2[3] = {1, 0, 0}, pj2[3] = {0, 1, 0};
-    if (L >= 3) {
+    if (Lcur >= 3) {
       g.npairs = 6;
       for (int t = 0; t < 6; t++) g.pair_i[t] = pi3[t], g.pair_j[t] = pj3[t];
-    } else if (L == 2) {
+    } else if (Lcur == 2) {
       g.npairs = 3;
       for (int t = 0; t < 3; t++) g.pair_i[t] = pi2[t], g.pair_j[t] = pj2[t];
     } else {
@@ -364,35 +371,50 @@ struct Solver {
     int lg = 0;
     while ((1L << lg) < 4L * K) lg++;
     const int shift = 61 - lg;  // |sum| < 4K in normalized units: no int64 overflow
-    for (int d = S - 1; d >= 0; d--) {
+    // Levels d = s + t are launched two at a time (two TMEM accumulators
+    // summed by the epilogue), lowest first.  Levels whose FP32 rounding
+    // could matter are summed in K chunks small enough for every partial sum
+    // to be exact: balanced digits are at most 2^7 (slice 0) and 2^6, so one
+    // level-d product term is at most 2^14 (d = 0) or 2^12 (d + 3) over the
+    // pairs (2^13 for (0, d) and (d, 0), 2^12 for the rest); with 4 Kc terms
+    // per output this stays <= 2^24 for Kc <= 256 (d = 0) and 2^10 / (d + 3).
+    // The two lowest levels are summed over the whole K.
+    auto chunk = [&](int d) {
+      if (d > S - 3) return K;
+      const int lim = d == 0 ? 256 : 1024 / (d + 3);
+      return lim >= 64 ? (lim / 64) * 64 : 64;
+    };
+    for (int hi = S - 1; hi >= 0; hi -= 2) {
+      const int lo = hi - 1;  // second level of the launch (-1: none)
       TcGemmArgs g;
       g.M = M;
       g.N = N;
       g.K = K;
       g.A = &za;
       g.B = &zb;
-      g.npairs = d + 1;
-      for (int t = 0; t <= d; t++) g.pair_i[t] = t, g.pair_j[t] = d - t;
+      g.npairs = 0;
+      for (int t = 0; t <= hi; t++, g.npairs++) {
+        g.pair_i[g.npairs] = t;
+        g.pair_j[g.npairs] = hi - t;
+        g.pair_acc[g.npairs] = 0;
+      }
+      if (lo >= 0)
+        for (int t = 0; t <= lo; t++, g.npairs++) {
+          g.pair_i[g.npairs] = t;
+          g.pair_j[g.npairs] = lo - t;
+          g.pair_acc[g.npairs] = 1;
+        }
       g.C64 = acc;
       g.ld64 = N;
       g.ps64 = (long)M * N;
       g.shift = shift;
       g.err = c->d_err;
-      // Levels whose FP32 rounding could matter are summed in K chunks small
-      // enough for every partial sum to be exact: slice digits are at most
-      // 2^7 (first) and 2^6 (others), so (d+1) pairs * 2^13 * 4 Kc <= 2^24
-      // (2^14 * 4 Kc for d = 0).  The two lowest levels are summed whole.
-      const bool exact = d <= S - 3;
-      int kc = K;
-      if (exact) {
-        const int lim = d == 0 ? 256 : 512 / (d + 1);
-        kc = lim >= 64 ? (lim / 64) * 64 : 64;
-      }
+      const int kc = lo >= 0 ? std::min(chunk(hi), chunk(lo)) : chunk(hi);
       for (int k0 = 0; k0 < K; k0 += kc) {
         g.k0 = k0;
         g.k1 = k0 + kc < K ? k0 + kc : K;
         const double part = flops * (double)(g.k1 - g.k0) / K;
-        timed(c, EV_TC, d == 0 ? part : 0.0, part * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
+        timed(c, EV_TC, (lo == 0 || hi == 0) ? part : 0.0, part * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
       }
     }
     return Acc{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
@@ -487,9 +509,15 @@ struct Solver {
   // ---------------- shape helpers ----------------
   // X-products take the mode of the phase (xmode).
   // Residual product: right A*Y (m x m), left Y*A (n x n).
-  Acc res_prod(const QMat& Y) { return left ? prod(Y, A, xmode) : prod(A, Y, xmode); }
+  Acc res_prod(const QMat& Y) {
+    Lcur = Lx;
+    return left ? prod(Y, A, xmode) : prod(A, Y, xmode);
+  }
   // Apply a side polynomial T (s x s) to Y (n x m): right Y*T, left T*Y.
-  Acc apply(const QMat& Y, const QMat& T) { return left ? prod(T, Y, xmode) : prod(Y, T, xmode); }
+  Acc apply(const QMat& Y, const QMat& T) {
+    Lcur = Lx;
+    return left ? prod(T, Y, xmode) : prod(Y, T, xmode);
+  }
   const char* tform() const { return left ? "fa" : "fb"; }
   QMat sq(const char* name, bool a, bool b) { return mat(c, name, s, s, MST_F | MST_D, a, b); }
   QMat big(const char* name) { return mat(c, name, n, m, MST_F | MST_D, true, true); }
@@ -806,30 +834,46 @@ double antiherm2(qpinv_ctx* c, const QMat& M) {
 // Penrose residuals (Sec. 4) for A (m x n) and X (n x m) FP64 masters, with
 // FP64-accurate products (mode PM_F64 or PM_EMU with 8 slices) and FP64 norms.
 void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, double* Er, long long* gemms) {
+  // E1 = ||AXA - A|| = ||(AX - I) A||, E2 = ||XAX - X|| = ||(XA - I) X||,
+  // E3 = ||(AX)^H - AX|| = ||Rr^H - Rr|| (Rr = AX - I), E4 likewise with XA.
+  // Every product is FP64-accurate: AX - I is not small when A is
+  // rectangular or rank deficient (it is -1 on the complement of the range).
   const int m = A.rows, n = A.cols;
   Solver S;
   S.c = c;
   S.dbl = true;
   S.L = 0;
-  S.xS = 8;
-  QMat AX = mat(c, "pAX", m, m, MST_D, false, false), XA = mat(c, "pXA", n, n, MST_D, false, false);
-  QMat AXA = mat(c, "pAXA", m, n, MST_D, false, false), XAX = mat(c, "pXAX", n, m, MST_D, false, false);
-  auto product = [&](const QMat& P, const QMat& Q, QMat& Out) {
+  QMat Rr = mat(c, "pRr", m, m, MST_D, false, false), Rl = mat(c, "pRl", n, n, MST_D, false, false);
+  QMat E1m = mat(c, "pE1", m, n, MST_D, false, false), E2m = mat(c, "pE2", n, m, MST_D, false, false);
+  auto product = [&](const QMat& P, const QMat& Q, QMat& Out, int slices, double diag) {
+    S.xS = slices;
     Solver::Acc acc = S.prod(P, Q, mode);
     CombineArgs a = S.base_args(Out.rows, Out.cols, &acc);
-    S.out(a, Out, "f", 1.0);
+    S.out(a, Out, "f", 1.0, diag);
     S.run(a);
   };
-  product(A, X, AX);
-  product(X, A, XA);
-  product(AX, A, AXA);
-  product(XA, X, XAX);
+  product(A, X, Rr, 8, -1.0);
+  product(X, A, Rl, 8, -1.0);
+  product(Rr, A, E1m, 8, 0.0);
+  product(Rl, X, E2m, 8, 0.0);
   if (gemms) *gemms += S.gemms;
   Planes<const double> a = dview(A), x = dview(X);
-  E[0] = std::sqrt(fro2(c, dview(AXA), &a, m, n));
-  E[1] = std::sqrt(fro2(c, dview(XAX), &x, n, m));
-  E[2] = std::sqrt(antiherm2(c, AX));
-  E[3] = std::sqrt(antiherm2(c, XA));
+  E[0] = std::sqrt(fro2(c, dview(E1m), nullptr, m, n));
+  E[1] = std::sqrt(fro2(c, dview(E2m), nullptr, n, m));
+  E[2] = std::sqrt(antiherm2(c, Rr));
+  E[3] = std::sqrt(antiherm2(c, Rl));
+  // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from AX = Rr + I instead
+  QMat AX = mat(c, "pAX", m, m, MST_D, false, false), XA = mat(c, "pXA", n, n, MST_D, false, false);
+  {
+    CombineArgs t = S.base_args(m, m, nullptr);
+    S.aux(t, 0, Rr);
+    S.out(t, AX, "f", 0.0, 1.0).caux[0] = 1.0;
+    S.run(t);
+    CombineArgs u = S.base_args(n, n, nullptr);
+    S.aux(u, 0, Rl);
+    S.out(u, XA, "f", 0.0, 1.0).caux[0] = 1.0;
+    S.run(u);
+  }
   const double nr[4] = {std::sqrt(fro2(c, a, nullptr, m, n)), std::sqrt(fro2(c, x, nullptr, n, m)),
                         std::sqrt(fro2(c, dview(AX), nullptr, m, m)), std::sqrt(fro2(c, dview(XA), nullptr, n, n))};
   for (int t = 0; t < 4; t++) Er[t] = nr[t] > 0 ? E[t] / nr[t] : E[t];
@@ -1036,7 +1080,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     S.X[1] = mat(c, "X1", n, m, MST_D | MST_F, true, true);
     S.cur = 0;
     ck(c, launch_init_x0(a, m, n, alpha, S.X[0].d, c->st), "init X0");
-    const int Ltc = o.split_level ? o.split_level : 3;
+    const int Lr = o.split_level ? o.split_level : 2;
     bool polish = fp64 || emu;  // these forms run in their final precision from the start
     if (fp64 || emu) {
       S.dbl = true;
@@ -1045,7 +1089,9 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       S.xS = 8;
     } else {
       S.dbl = false;
-      S.L = Ltc;
+      S.L = 3;
+      S.Lr = Lr;
+      S.Lx = 3;
       S.xmode = PM_TC;
       ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
       ck(c, launch_f64_to_f32(dview(S.X[0]), n, m, S.X[0].f, c->st), "X0 to fp32");
@@ -1182,6 +1228,7 @@ int qpinv_qgemm(qpinv_ctx* c, void* stream, int m, int k, int n, const double* c
       S.c = c;
       S.dbl = true;
       S.L = precision == QPINV_PREC_TC ? split_level : 0;
+      S.Lcur = split_level;
       S.xS = split_level;
       if (precision == QPINV_PREC_TC) {
         S.forms(a, true, false);

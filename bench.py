@@ -174,6 +174,36 @@ def kernel_qgemm(args, torch, qpinv):
     return 0
 
 
+def bench_batched(args, torch, qpinv):
+    """4096 pure-quaternion blocks (m, n ~ U[16, 256], rank ~ U[4, min(m, n)])
+    solved by qpinv_solve_batched in one persistent launch per step."""
+    from paper_2605_01464_gb300 import inputs
+    mats = inputs.pure_quaternion_batch(4096, seed=3)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs = [torch.empty((4, a.shape[2], a.shape[1]), dtype=torch.float64, device="cuda") for a in As]
+    ctx = qpinv.Context(0)
+    for _ in range(args.warmup):
+        ctx.solve_batched(As, args.method, tol=args.tol, max_iter=200, Xs=Xs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            _, infos = ctx.solve_batched(As, args.method, tol=args.tol, max_iter=200, Xs=Xs)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    e1 = [i["E_rel"][0] for i in infos]
+    its = [i["iters"] for i in infos]
+    print(json.dumps({"metric": "batched pinv solves/s", "value": 4096 * args.steps / dt, "unit": "solves/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                      "higher_is_better": True, "dtype": "df32 (double-FP32)", "data": "synthetic",
+                      "config": {"workload": "4096 pure-quaternion blocks, m, n ~ U[16,256], rank ~ U[4,min(m,n)], "
+                                             "seed 3, %s, rel. tol %g, one persistent launch" % (args.method, args.tol)},
+                      "result": {"max_E1_rel": max(e1), "median_iters": sorted(its)[len(its) // 2],
+                                 "statuses": sorted(set(i["status"] for i in infos))},
+                      "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def workload_config(args):
     return {"workload": "square %dx%d quaternion A = U diag(sigma) V^H, Haar U and V, sigma log-spaced 1..1e-6; "
                         "%s, mixed precision (BF16-split tensor-core products with FP32 accumulation; exact-slice "
@@ -199,6 +229,8 @@ def main():
     ap.add_argument("--kernel", default=None, choices=["qgemm"],
                     help="time only the tensor-core quaternion GEMM (n x n x n) for kernel profiling")
     ap.add_argument("--split", type=int, default=1, help="BF16 terms of --kernel qgemm (1..3)")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched"],
+                    help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
     args = ap.parse_args()
@@ -219,6 +251,8 @@ def main():
     torch.cuda.set_device(local)
     if args.kernel == "qgemm":
         return kernel_qgemm(args, torch, qpinv)
+    if args.workload == "batched":
+        return bench_batched(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -59,6 +59,7 @@ extern "C" {
 #define QPINV_PLATEAU 1       /* relative step stopped decreasing below 1e-6; X is the iterate before that step */
 #define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
 #define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
+#define QPINV_NONFINITE_INPUT 4 /* qpinv_solve_batched: this A holds NaN/Inf; its X is left untouched */
 
 /* ---- methods ----------------------------------------------------------- */
 typedef enum {
@@ -163,14 +164,21 @@ int qpinv_solve(qpinv_ctx* ctx, void* stream, int m, int n, const double* const 
                 qpinv_method method, double tol, int max_iter, double* const X[4], long ldx,
                 qpinv_result* out);
 
-/* Batched solve of `batch` independent matrices of uneven shapes.  m[b],
- * n[b] (host arrays): shape of matrix b, each in [1, 256]; A[4*b + c] and
- * X[4*b + c] (host arrays of device pointers): plane c of matrix b, with
+/* Batched solve of `batch` independent matrices of uneven shapes (CUR
+ * intersection blocks and the like; the paper solves them one by one).
+ * m[b], n[b] (host arrays): shape of matrix b, each in [1, 256]; A[4*b + c]
+ * and X[4*b + c] (host arrays of DEVICE pointers): plane c of matrix b, with
  * leading dimensions lda[b] >= n[b] and ldx[b] >= m[b].  All matrices are
- * solved in one persistent kernel launch with FP32 arithmetic (tensor-core
- * products where the tile pays); out[b] (host array, may be NULL) receives
- * each outcome (E1..E4 are computed in FP64).  Matrices are independent: a
- * failure of one does not affect the others. */
+ * solved in ONE persistent kernel launch: every CTA takes matrices from a
+ * work counter (largest first) and runs alpha, X_0 = alpha A^H, the method
+ * (residual on the smaller side), the stop rule of the context's options and
+ * E1..E4 for each, in double-FP32 arithmetic (an unevaluated sum of two
+ * floats, ~2^-46: small blocks are often rank deficient, and null-space
+ * noise grows by ~kappa^2 over a solve).  Options used: stop_rule, qrapid_N,
+ * alpha_mode (SAFE, FRO or USER; SPECTRAL and LEARNED run as SAFE).
+ * out[b] (host array, may be NULL) receives each outcome; tc_iters and
+ * polish_iters are 0; time_ms is the whole call.  Matrices are independent:
+ * a non-finite A gives QPINV_NONFINITE_INPUT for that matrix only. */
 int qpinv_solve_batched(qpinv_ctx* ctx, void* stream, int batch, const int* m, const int* n,
                         const double* const* A, const long* lda, qpinv_method method, double tol,
                         int max_iter, double* const* X, const long* ldx, qpinv_result* out);

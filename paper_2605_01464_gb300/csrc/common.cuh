@@ -127,4 +127,24 @@ struct TcGemmArgs {
 cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);
 bool tc_supported();
 
+// Batched solver (batched.cu).
+struct BatchResultHost {
+  int status, iters, side, gemms;
+  double alpha, delta, delta_rel;
+  double E[4], E_rel[4];
+};
+}  // namespace qp
+#include <vector>
+namespace qp {
+cudaError_t run_batched(int batch, const int* m, const int* n, const double* const* A, const long* lda,
+                        double* const* X, const long* ldx, int method, double tol, int max_iter, int qrapid_N,
+                        int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, void* ws,
+                        size_t ws_bytes, int slots, void* dev_items, void* dev_order, void* dev_results,
+                        int* dev_counter, std::vector<BatchResultHost>& out, cudaStream_t st);
+size_t batched_slot_bytes();
+size_t batched_item_bytes();
+size_t batched_result_bytes();
+int batched_max_dim();
+int batched_slots_per_sm();
+
 }  // namespace qp

@@ -1275,10 +1275,66 @@ int qpinv_penrose(qpinv_ctx* c, void* stream, int m, int n, const double* const 
 int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, const int* n, const double* const* A,
                         const long* lda, qpinv_method method, double tol, int max_iter, double* const* X,
                         const long* ldx, qpinv_result* out) {
-  (void)stream; (void)batch; (void)m; (void)n; (void)A; (void)lda; (void)method; (void)tol; (void)max_iter;
-  (void)X; (void)ldx; (void)out;
   if (!c) return QPINV_E_INVALID;
-  return fail(c, QPINV_E_UNSUPPORTED, "batched solver not built yet");
+  if (batch < 1 || !m || !n || !A || !X || !lda || !ldx || max_iter < 1 || !(tol >= 0.0) || (int)method < 0 ||
+      (int)method > 3)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  const int maxd = batched_max_dim();
+  for (int b = 0; b < batch; b++) {
+    if (m[b] < 1 || n[b] < 1 || m[b] > maxd || n[b] > maxd || lda[b] < n[b] || ldx[b] < m[b])
+      return fail(c, QPINV_E_INVALID, "batched matrix " + std::to_string(b) + ": shape outside [1, 256] or bad ld");
+    for (int q = 0; q < 4; q++)
+      if (!A[4 * b + q] || !X[4 * b + q] || !is_device_ptr(A[4 * b + q]) || !is_device_ptr(X[4 * b + q]))
+        return fail(c, QPINV_E_INVALID, "batched matrix " + std::to_string(b) + ": planes must be device pointers");
+  }
+  const auto t_start = std::chrono::steady_clock::now();
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    int nsm = 0;
+    ck(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
+    int slots = nsm * batched_slots_per_sm();
+    if (slots > batch) slots = batch;
+    void* ws = buf(c, "batch.ws", batched_slot_bytes() * (size_t)slots);
+    void* items = buf(c, "batch.items", batched_item_bytes() * (size_t)batch + 64);
+    void* order = buf(c, "batch.order", sizeof(int) * (size_t)batch + 64);
+    void* results = buf(c, "batch.results", batched_result_bytes() * (size_t)batch + 64);
+    int* counter = (int*)buf(c, "batch.counter", 64);
+    std::vector<BatchResultHost> res;
+    const int amode = c->opt.alpha_mode == QPINV_ALPHA_USER ? QPINV_ALPHA_USER
+                      : c->opt.alpha_mode == QPINV_ALPHA_FRO ? QPINV_ALPHA_FRO
+                                                              : QPINV_ALPHA_SAFE;
+    timed(c, EV_EW, 0, 0, 0, [&] {
+      return run_batched(batch, m, n, A, lda, X, ldx, (int)method, tol, max_iter, c->opt.qrapid_N,
+                         c->opt.stop_rule, amode, c->opt.alpha_user, hpi19_k, ws, batched_slot_bytes() * slots,
+                         slots, items, order, results, counter, res, c->st);
+    });
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (out) {
+      for (int b = 0; b < batch; b++) {
+        qpinv_result& r = out[b];
+        memset(&r, 0, sizeof(r));
+        r.status = res[b].status < 0 ? QPINV_NONFINITE_INPUT : res[b].status;
+        r.iters = res[b].iters;
+        r.alpha = res[b].alpha;
+        r.alpha_source = amode;
+        r.side = res[b].side;
+        r.delta = res[b].delta;
+        r.delta_rel = res[b].delta_rel;
+        for (int q = 0; q < 4; q++) {
+          r.E[q] = res[b].E[q];
+          r.E_rel[q] = res[b].E_rel[q];
+        }
+        r.gemms = res[b].gemms;
+        r.time_ms = ms;
+      }
+    }
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
 }
 
 }  // extern "C"

@@ -24,7 +24,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "tc": 2, "emu": 3}
 ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3, "learned": 4}
 SIDE = {"auto": 0, "right": 1, "left": 2}
 STOP = {"paper_abs": 0, "rel_plateau": 1}
-STATUS = {0: "converged", 1: "plateau", 2: "not_converged", 3: "diverged"}
+STATUS = {0: "converged", 1: "plateau", 2: "not_converged", 3: "diverged", 4: "nonfinite_input"}
 ERRORS = {0: "ok", -1: "invalid", -2: "cuda", -3: "nomem", -4: "nonfinite", -5: "timeout", -6: "unsupported",
           -7: "noalloc_limit"}
 NOALLOC_MAX_DIM = 256

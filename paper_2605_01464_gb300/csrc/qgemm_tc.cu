@@ -32,13 +32,31 @@ namespace {
 
 constexpr int BM = 128;  // output rows per CTA = TMEM lanes
 constexpr int BN = 64;   // quaternion output columns per CTA (per component)
-constexpr int BK = 64;   // BF16 K elements per stage: one 128-byte swizzle row
-constexpr int STAGES = 2;
-constexpr int A_PLANE_BYTES = BM * BK * 2;
-constexpr int B_PLANE_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = 4 * (A_PLANE_BYTES + B_PLANE_BYTES);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int ACC_COLS = 4 * BN;  // TMEM columns of one accumulator (four output components)
+constexpr int GROUP_M = 16;       // CTA rasterization: 16 row tiles per group share B tiles in L2
+
+// Stage shape.  BK BF16 K-elements per stage = one swizzle row of 2*BK bytes.
+//   Wide: BK = 32 (64-byte swizzle), 48 KB per stage, two CTAs per SM, so one
+//         CTA's epilogue overlaps the other's main loop (one accumulator).
+//   Deep: BK = 64 (128-byte swizzle), 96 KB per stage, one CTA per SM (two
+//         accumulators take all 512 TMEM columns).
+template <int BK_, int SWB_, int MINB_>
+struct Cfg {
+  static constexpr int BK = BK_;
+  static constexpr int SWB = SWB_;
+  static constexpr int MINB = MINB_;
+  static constexpr int STAGES = 2;
+  static constexpr int A_PLANE = BM * BK * 2;
+  static constexpr int B_PLANE = BN * BK * 2;
+  static constexpr int STAGE = 4 * (A_PLANE + B_PLANE);
+  static constexpr int SMEM = STAGES * STAGE + 1024;
+  static constexpr unsigned long long LAYOUT = SWB == 128 ? 2ull : 4ull;  // descriptor swizzle code
+  static constexpr unsigned SBO = 8 * SWB;                               // bytes between 8-row groups
+};
+using CfgWide = Cfg<32, 64, 2>;
+using CfgDeep = Cfg<64, 128, 1>;
+static_assert(CfgWide::SMEM * 2 <= 227 * 1024, "two wide CTAs per SM");
+static_assert(CfgDeep::SMEM * 2 > 228 * 1024, "one deep CTA per SM");
 constexpr int THREADS = 192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
@@ -93,10 +111,11 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor: K-major, swizzled rows of 2*BK bytes, 8-row groups SBO bytes apart.
+template <class C>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(C::SBO >> 4) << 32) |
+         ((uint64_t)1 << 46) | (C::LAYOUT << 61);
 }
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -137,6 +156,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 struct KParams {
   int M, N;
+  int Mt, Nt;    // tile counts
   int kb0, kb1;  // K blocks [kb0, kb1) of BK elements
   int npairs;
   int pi[16], pj[16];
@@ -150,8 +170,11 @@ struct KParams {
   int* err;
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <class C>
+__global__ void __launch_bounds__(THREADS, C::MINB)
     k_qgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KParams P) {
+  constexpr int BK = C::BK, STAGES = C::STAGES, A_PLANE_BYTES = C::A_PLANE, B_PLANE_BYTES = C::B_PLANE,
+                STAGE_BYTES = C::STAGE;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc;
   __shared__ uint32_t tmem_slot;
@@ -159,7 +182,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // grouped rasterization: consecutive CTAs walk GROUP_M row tiles, then the next column tile
+  const int per_group = GROUP_M * P.Nt, group = blockIdx.x / per_group, local = blockIdx.x % per_group;
+  const int gm = min(GROUP_M, P.Mt - group * GROUP_M);
+  const int m0 = (group * GROUP_M + local % gm) * BM, n0 = (local / gm) * BN;
   const int nunits = (P.kb1 - P.kb0) * P.npairs;
   const uint32_t tmem_cols = P.nacc == 2 ? 2 * ACC_COLS : ACC_COLS;
 
@@ -221,13 +247,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kk = 0; kk < BK / 16; kk++) {
 #pragma unroll
           for (int r = 0; r < 4; r++) {
-            const uint64_t ad = smem_desc(a_base + r * A_PLANE_BYTES + kk * 32);
+            const uint64_t ad = smem_desc<C>(a_base + r * A_PLANE_BYTES + kk * 32);
 #pragma unroll
             for (int c = 0; c < 4; c++) {
               const int bp = r ^ c;
               const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
                                (r == 3 && (c == 0 || c == 1));
-              const uint64_t bd = smem_desc(b_base + bp * B_PLANE_BYTES + kk * 32);
+              const uint64_t bd = smem_desc<C>(b_base + bp * B_PLANE_BYTES + kk * 32);
               const uint32_t acc = (!fresh || kk > 0 || r > 0) ? 1u : 0u;
               mma_bf16(dacc + c * BN, ad, bd, neg ? IDESC_NEG_A : IDESC, acc);
             }
@@ -317,18 +343,41 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 3-D map over [planes][rows][K] BF16 with a box of (BK, box_rows, 1).
-bool make_map(CUtensorMap* map, const bf16* base, int K, int rows, int planes, long ld, long ps, int box_rows) {
+// 3-D map over [planes][rows][K] BF16 with a box of (bk, box_rows, 1) and a 2*bk-byte swizzle.
+bool make_map(CUtensorMap* map, const bf16* base, int K, int rows, int planes, long ld, long ps, int box_rows,
+              int bk) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ps * 2};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+template <class C>
+cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
+  constexpr int BK = C::BK;
+  if ((a.k0 % BK) != 0 || (a.k1 != a.K && (a.k1 % BK) != 0) || a.k0 < 0 || a.k1 > a.K || a.k0 > a.k1)
+    return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM, BK)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, BN, BK)) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_qgemm_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  P.kb0 = a.k0 / BK;
+  P.kb1 = (a.k1 + BK - 1) / BK;
+  P.Mt = (a.M + BM - 1) / BM;
+  P.Nt = (a.N + BN - 1) / BN;
+  k_qgemm_tc<C><<<P.Mt * P.Nt, THREADS, C::SMEM, st>>>(mA, mB, P);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -345,8 +394,6 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
   if (a.npairs < 1 || a.npairs > 16 || !a.A || !a.B || !a.A->a || !a.B->b) return cudaErrorInvalidValue;
   if ((a.A->lda % 8) || (a.A->psa % 8) || (a.B->ldb % 8) || (a.B->psb % 8)) return cudaErrorInvalidValue;
-  if ((a.k0 % BK) != 0 || (a.k1 != a.K && (a.k1 % BK) != 0) || a.k0 < 0 || a.k1 > a.K || a.k0 > a.k1)
-    return cudaErrorInvalidValue;
   int nacc = 1;
   for (int p = 0; p < a.npairs; p++) {
     if (a.pair_i[p] < 0 || a.pair_i[p] >= a.A->levels || a.pair_j[p] < 0 || a.pair_j[p] >= a.B->levels ||
@@ -355,20 +402,9 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
     if (a.pair_acc[p] == 1) nacc = 2;
   }
   if (nacc == 2 && !a.C64) return cudaErrorInvalidValue;  // two accumulators only sum into int64
-  CUtensorMap mA, mB;
-  if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, BN)) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_qgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   KParams P;
   P.M = a.M;
   P.N = a.N;
-  P.kb0 = a.k0 / BK;
-  P.kb1 = (a.k1 + BK - 1) / BK;
   P.npairs = a.npairs;
   bool seen[2] = {false, false};
   for (int p = 0; p < 16; p++) {
@@ -388,9 +424,7 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   P.ps64 = a.ps64;
   P.scale = ldexpf(1.0f, a.shift);
   P.err = a.err;
-  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
-  k_qgemm_tc<<<grid, THREADS, SMEM_BYTES, st>>>(mA, mB, P);
-  return cudaGetLastError();
+  return nacc == 2 ? launch_cfg<CfgDeep>(a, P, st) : launch_cfg<CfgWide>(a, P, st);
 }
 
 }  // namespace qp

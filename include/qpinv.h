@@ -56,7 +56,7 @@ extern "C" {
 
 /* ---- solver outcome (qpinv_result.status) ----------------------------- */
 #define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
-#define QPINV_PLATEAU 1       /* relative step stopped decreasing below 1e-6; X is the iterate before that step */
+#define QPINV_PLATEAU 1       /* relative step stopped decreasing after falling below 1e-3 (rounding floor); X is the iterate before that step */
 #define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
 #define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
 #define QPINV_NONFINITE_INPUT 4 /* qpinv_solve_batched: this A holds NaN/Inf; its X is left untouched */
@@ -76,12 +76,14 @@ enum {
                            polish iterations whose residual R = I - A X and update X t are
                            FP64-accurate (QPINV_PREC_EMU products) */
   QPINV_PREC_TC = 2,    /* tensor-core products only (FP32-level output) */
-  QPINV_PREC_EMU = 3    /* every product FP64-accurate on the tensor cores: exact 7-bit slices
+  QPINV_PREC_EMU = 3,   /* every product FP64-accurate on the tensor cores: exact 7-bit slices
                            per operand (power-of-two row and column scaling; 8 slices in a
                            solve, `split_level` = 2..8 in qpinv_qgemm), K-chunked so every FP32
                            partial sum is exact, accumulated in 64-bit fixed point.  Use it for
                            rank-deficient A, whose null-space rounding noise the iteration
                            multiplies by its order each step */
+  QPINV_PREC_DF32 = 4   /* reported only (qpinv_result.precision of batched solves): double-FP32
+                           arithmetic on the CUDA cores */
 };
 enum { QPINV_ALPHA_SAFE = 0,     /* 1 / (||A||_1 ||A||_inf), entry moduli; always < 2/sigma_1^2 */
        QPINV_ALPHA_SPECTRAL = 1, /* 1 / sigma_1^2 (Algorithms 1-3), sigma_1 by power iteration */
@@ -119,6 +121,10 @@ typedef struct {
   double alpha;      /* scaling used in X_0 = alpha A^H */
   int alpha_source;  /* QPINV_ALPHA_* actually used */
   int side;          /* QPINV_SIDE_RIGHT or QPINV_SIDE_LEFT actually used */
+  int precision;     /* precision that produced X: a MIXED solve with penrose = 1 that diverges or
+                        whose E_rel[0] exceeds 1e-6 (typically rank-deficient A) is repeated in
+                        QPINV_PREC_EMU and reports EMU here, gemms then counting both attempts;
+                        batched solves report QPINV_PREC_DF32 */
   double delta;      /* ||X_{j+1} - X_j||_F of the last computed step */
   double delta_rel;  /* delta / ||X_{j+1}||_F */
   double E[4];       /* Sec. 4: ||AXA-A||_F, ||XAX-X||_F, ||(AX)^H-AX||_F, ||(XA)^H-XA||_F */
@@ -188,6 +194,43 @@ void qpinv_free(qpinv_ctx* ctx);
 
 /* Message for the last error on this context (never NULL). */
 const char* qpinv_last_error(qpinv_ctx* ctx);
+
+/* ---- learned initial scaling (the benchmark spec's learned initializer) ----
+ * A 32 -> 64 -> 64 -> 1 tanh network maps 32 cheap sketched features of A to
+ * y = log(alpha * theta_1), where theta_1 <= sigma_1^2 is the top Ritz value
+ * of a 16-step Lanczos run on A^H A; labels are the optimum of Thm. 1's
+ * contraction factor max|1 - alpha sigma_i^2|, alpha* = 2/(sigma_1^2 +
+ * sigma_r^2).  With QPINV_ALPHA_LEARNED, qpinv_solve uses the prediction only
+ * if alpha * theta_1 * 1.05 < 2 (Thm. 1's condition alpha < 2/sigma_1^2 with a
+ * margin for theta_1); otherwise, or while the network is untrained, it uses
+ * QPINV_ALPHA_SAFE (reported in qpinv_result.alpha_source). */
+#define QPINV_ALPHA_NFEAT 32
+#define QPINV_ALPHA_NWEIGHTS 6401 /* W1 64x32, b1, W2 64x64, b2, w3 64, b3, input mean 32, input sd 32 */
+#define QPINV_ALPHA_NTRAIN 6337   /* trainable parameters: the block up to and including b3 */
+
+/* Features of A (planes as in qpinv_solve): feat (host, 32 floats); theta1
+ * (host, may be NULL) receives the Lanczos estimate of sigma_1^2. */
+int qpinv_alpha_features(qpinv_ctx* ctx, void* stream, int m, int n, const double* const A[4], long lda,
+                         float* feat, double* theta1);
+
+/* Trains the context's network from scratch on the GPU (own forward,
+ * backward and Adam kernels): `count` samples, feat (host, count x 32 floats,
+ * row-major), label (host, count floats of y = log(alpha * theta_1)),
+ * minibatches of `batch`, `epochs` passes in a seeded shuffled order, learning
+ * rate lr.  loss (host, may be NULL) receives the final mean squared error. */
+int qpinv_alpha_train(qpinv_ctx* ctx, void* stream, int count, const float* feat, const float* label, int epochs,
+                      int batch, float lr, unsigned long long seed, double* loss);
+
+/* Network output y for one feature vector (host, 32 floats). */
+int qpinv_alpha_predict(qpinv_ctx* ctx, void* stream, const float* feat, double* y);
+
+/* Gradient of the mean squared error over `count` samples with respect to
+ * the QPINV_ALPHA_NTRAIN trainable parameters (host out), and the loss. */
+int qpinv_alpha_gradient(qpinv_ctx* ctx, void* stream, int count, const float* feat, const float* label,
+                         float* grad, double* loss);
+
+/* Reads (set = 0) or loads (set = 1) the QPINV_ALPHA_NWEIGHTS weight block (host). */
+int qpinv_alpha_weights(qpinv_ctx* ctx, float* w, int count, int set);
 
 /* ---- building blocks, exposed for tests and measurement ---------------- */
 

@@ -21,7 +21,9 @@
  *  - The stop rule of Algs. 1-3 is absolute (||X_{j+1}-X_j||_F < tol); a
  *    relative rule with plateau detection is offered as an option because the
  *    absolute rule is scale dependent and, for rank-deficient input, rounding
- *    noise in the null-space part of X grows by p(1) per extra iteration.
+ *    noise in the null-space part of X grows by p(1) per extra iteration:
+ *    PLATEAU = the relative step stopped decreasing after it had fallen below
+ *    1e-3, i.e. the rounding floor was reached; X_j is returned.
  *  - Side: the paper's residual is R = I_m - A X (right form).  The left form
  *    R' = I_n - X A with X_{j+1} = p(R') X gives the same iterates in exact
  *    arithmetic (X (AX)^k = (XA)^k X); it is offered for tall inputs.
@@ -494,7 +496,7 @@ void qo_solve(int m, int n, const double *A, int method, int N, int alpha_mode,
       if (d < tol) { res->status = 0; res->iters = j + 1; break; }
     } else {
       if (drel <= tol) { qm_free(&x); x = xn; res->status = 0; res->iters = j + 1; break; }
-      if (j > 0 && drel >= prev_rel && drel < 1e-6) {
+      if (j > 0 && prev_rel < 1e-3 && drel >= prev_rel) {
         /* no progress: keep X_j, the iterate before the non-decreasing step */
         res->status = 1; res->iters = j;
         qm_free(&xn);

@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(TPB, 2) k_batched(BatchParams P) {
         } else if (drel <= P.tol) {
           stop = true;
           res.status = QPINV_CONVERGED;
-        } else if (prev < INFINITY && drel >= prev && drel < 1e-6) {
+        } else if (prev < 1e-3 && drel >= prev) {
           stop = true;
           accept = false;
           res.status = QPINV_PLATEAU;

@@ -142,6 +142,18 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
                         size_t ws_bytes, int slots, void* dev_items, void* dev_order, void* dev_results,
                         int* dev_counter, std::vector<BatchResultHost>& out, cudaStream_t st);
 size_t batched_slot_bytes();
+// Learned alpha (alpha.cu).
+int alpha_nweights();
+int alpha_ntrain();
+cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fro2, double norm1, double norminf,
+                           float* scratch, double* dscratch, double* pin, cudaStream_t st, float* feat,
+                           double* theta1_out);
+void alpha_init_weights(float* W, unsigned long long seed);
+size_t alpha_scratch_floats(int B);
+cudaError_t alpha_forward(const float* dW, const float* dX, int B, float* scratch, float* dy_out, cudaStream_t st);
+cudaError_t alpha_gradient(const float* dW, const float* dX, const float* dT, int B, float* scratch, float* dG,
+                           double* dloss, cudaStream_t st);
+cudaError_t alpha_adam(float* dW, const float* dG, float* dM1, float* dM2, int t, float lr, cudaStream_t st);
 size_t batched_item_bytes();
 size_t batched_result_bytes();
 int batched_max_dim();

@@ -77,6 +77,7 @@ struct qpinv_ctx {
   double* h_pin = nullptr;  // pinned host scalars
   cudaStream_t st = nullptr;
   bool trace = false;
+  std::vector<float> alpha_w;  // learned-alpha network (empty: untrained)
 };
 
 namespace {
@@ -884,6 +885,32 @@ int fail(qpinv_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
+// Learned-alpha features of an m x n matrix whose FP32 master is A.f.
+void features_of(qpinv_ctx* c, const QMat& A, double fro2, double n1, double ninf, float* feat, double* theta1) {
+  const int m = A.rows, n = A.cols;
+  float* sc = (float*)buf(c, "alpha.lanczos", sizeof(float) * 4 * (3 * (size_t)n + m) + 256);
+  double* ds = (double*)buf(c, "alpha.dot", sizeof(double) * 4);
+  ck(c, alpha_features(fview(A), m, n, fro2, n1, ninf, sc, ds, c->h_pin, c->st, feat, theta1), "alpha features");
+  c->stats.kernel_launches += 16 * 6;
+}
+
+// Network prediction y = log(alpha * theta_1) for one feature vector.
+double predict_one(qpinv_ctx* c, const float* feat) {
+  const int NW = alpha_nweights();
+  float* dW = (float*)buf(c, "alpha.W", sizeof(float) * NW);
+  float* dX = (float*)buf(c, "alpha.x1", sizeof(float) * 32);
+  float* sc = (float*)buf(c, "alpha.s1", sizeof(float) * alpha_scratch_floats(1) + 64);
+  float* dy = (float*)buf(c, "alpha.y1", sizeof(float) * 4);
+  ck(c, cudaMemcpyAsync(dW, c->alpha_w.data(), sizeof(float) * NW, cudaMemcpyHostToDevice, c->st), "weights");
+  ck(c, cudaMemcpyAsync(dX, feat, sizeof(float) * 32, cudaMemcpyHostToDevice, c->st), "features");
+  timed(c, EV_EW, 0, 0, 0, [&] { return alpha_forward(dW, dX, 1, sc, dy, c->st); });
+  float y = 0.f;
+  ck(c, cudaMemcpyAsync(c->h_pin, dy, sizeof(float), cudaMemcpyDeviceToHost, c->st), "read");
+  ck(c, cudaStreamSynchronize(c->st), "sync");
+  memcpy(&y, c->h_pin, sizeof(float));
+  return (double)y;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1007,8 +1034,15 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     // order each step (as for rank-deficient A): such solves run with
     // FP64-accurate products throughout.
     const bool wrong_side = (o.side == QPINV_SIDE_RIGHT && m > n) || (o.side == QPINV_SIDE_LEFT && m < n);
-    const bool emu = o.precision == QPINV_PREC_EMU || (!fp64 && wrong_side);
+    bool emu = o.precision == QPINV_PREC_EMU || (!fp64 && wrong_side);
     if (!fp64 && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    long long gemms_before = 0;
+    // A MIXED solve whose result fails the Penrose check is repeated with
+    // FP64-accurate products: rank-deficient A (and A beyond the tensor-core
+    // phase's conditioning reach) amplifies BF16 rounding in the complement of
+    // the range by the method's order every step.
+    for (int attempt = 0;; attempt++) {
+    res.precision = fp64 ? QPINV_PREC_FP64 : emu ? QPINV_PREC_EMU : o.precision;
     Solver S;
     S.c = c;
     S.m = m;
@@ -1033,8 +1067,28 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     const double norm_inf = hm[0], norm_1 = hm[1];
     const double a2est = std::sqrt(norm_1 * norm_inf);  // >= sigma_1
     double alpha = 0.0;
-    const int amode = o.alpha_mode == QPINV_ALPHA_LEARNED ? QPINV_ALPHA_SAFE : o.alpha_mode;
-    if (a_f2 == 0.0) {
+    int amode = o.alpha_mode;
+    if (amode == QPINV_ALPHA_LEARNED) {
+      // Network prediction, accepted only if it passes Thm. 1's contraction
+      // condition alpha sigma_1^2 < 2 with a 5% margin for the Lanczos
+      // estimate theta_1 <= sigma_1^2; otherwise the safe alpha is used.
+      amode = QPINV_ALPHA_SAFE;
+      if (!c->alpha_w.empty() && a_f2 > 0.0) {
+        ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
+        float feat[32];
+        double theta1 = 0.0;
+        features_of(c, S.A, a_f2, norm_1, norm_inf, feat, &theta1);
+        const double y = predict_one(c, feat);
+        const double al = std::exp(y) / theta1;
+        if (std::isfinite(al) && al > 0.0 && al * theta1 * 1.05 < 2.0) {
+          alpha = al;
+          amode = QPINV_ALPHA_LEARNED;
+        }
+      }
+    }
+    if (amode == QPINV_ALPHA_LEARNED) {
+      // alpha set above
+    } else if (a_f2 == 0.0) {
       alpha = 0.0;
     } else if (amode == QPINV_ALPHA_SAFE) {
       alpha = 1.0 / (norm_1 * norm_inf);
@@ -1144,7 +1198,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         if (drel <= tol && final_phase) {
           stop = true;
           res.status = QPINV_CONVERGED;
-        } else if (prev_rel < INFINITY && drel >= prev_rel && drel < 1e-6 && final_phase) {
+        } else if (prev_rel < 1e-3 && drel >= prev_rel && final_phase) {
           stop = true;
           accept = false;
           res.status = QPINV_PLATEAU;
@@ -1189,8 +1243,18 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       penrose(c, S.A, Xf, fp64 ? PM_F64 : PM_EMU, res.E, res.E_rel, nullptr);
       if (!fp64) check_kernel_error(c);
     }
-    res.gemms = S.gemms;
+    res.gemms = gemms_before + S.gemms;
+    if (c->trace)
+      fprintf(stderr, "qpinv: attempt %d precision %d status %d iters %d E1_rel %.3e\n", attempt, res.precision,
+              res.status, res.iters, res.E_rel[0]);
+    if (attempt == 0 && o.precision == QPINV_PREC_MIXED && !emu && o.penrose && !(res.E_rel[0] <= 1e-6)) {
+      gemms_before = res.gemms;
+      emu = true;
+      continue;
+    }
     store_planes(c, Xf, X, ldx, n, m);
+    break;
+    }
     ck(c, cudaStreamSynchronize(c->st), "stream sync");
   } catch (const QpError& e) {
     cudaGetLastError();
@@ -1320,6 +1384,7 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
         r.alpha = res[b].alpha;
         r.alpha_source = amode;
         r.side = res[b].side;
+        r.precision = QPINV_PREC_DF32;
         r.delta = res[b].delta;
         r.delta_rel = res[b].delta_rel;
         for (int q = 0; q < 4; q++) {
@@ -1330,6 +1395,164 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
         r.time_ms = ms;
       }
     }
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_alpha_features(qpinv_ctx* c, void* stream, int m, int n, const double* const A[4], long lda, float* feat,
+                         double* theta1) {
+  if (!c) return QPINV_E_INVALID;
+  if (m <= 0 || n <= 0 || lda < n || !planes_ok(A) || !feat) return fail(c, QPINV_E_INVALID, "invalid argument");
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    QMat a = mat(c, "A", m, n, MST_D | MST_F, false, false);
+    load_planes(c, A, lda, m, n, a);
+    Planes<const double> av = dview(a);
+    double bad = 0.0;
+    const double f2 = fro2(c, av, nullptr, m, n, &bad);
+    if (bad > 0.0) return fail(c, QPINV_E_NONFINITE, "A contains NaN or Inf");
+    double* rs = (double*)buf(c, "rowsum", sizeof(double) * (size_t)(m + n) + 64);
+    double* mx = (double*)buf(c, "maxes", sizeof(double) * 4);
+    ck(c, launch_abs_sums(av, m, n, rs, rs + m, c->st), "abs sums");
+    ck(c, launch_max(rs, m, mx, c->st), "max");
+    ck(c, launch_max(rs + m, n, mx + 1, c->st), "max");
+    double hm[2];
+    read_back(c, mx, 2, hm);
+    ck(c, launch_f64_to_f32(av, m, n, a.f, c->st), "A to fp32");
+    double t1 = 0.0;
+    features_of(c, a, f2, hm[1], hm[0], feat, &t1);
+    if (theta1) *theta1 = t1;
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_alpha_weights(qpinv_ctx* c, float* w, int count, int set) {
+  if (!c || !w || count != alpha_nweights()) return c ? fail(c, QPINV_E_INVALID, "weight count mismatch") : QPINV_E_INVALID;
+  if (set) {
+    c->alpha_w.assign(w, w + count);
+  } else {
+    if (c->alpha_w.empty()) return fail(c, QPINV_E_INVALID, "the network is untrained");
+    memcpy(w, c->alpha_w.data(), sizeof(float) * count);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_alpha_gradient(qpinv_ctx* c, void* stream, int count, const float* feat, const float* label, float* grad,
+                         double* loss) {
+  if (!c || count < 1 || !feat || !label || !grad || c->alpha_w.empty())
+    return c ? fail(c, QPINV_E_INVALID, "invalid argument or untrained network") : QPINV_E_INVALID;
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    const int NW = alpha_nweights(), NT = alpha_ntrain();
+    float* dW = (float*)buf(c, "alpha.W", sizeof(float) * NW);
+    float* dX = (float*)buf(c, "alpha.X", sizeof(float) * 32 * (size_t)count);
+    float* dT = (float*)buf(c, "alpha.T", sizeof(float) * (size_t)count);
+    float* dG = (float*)buf(c, "alpha.G", sizeof(float) * NT);
+    float* sc = (float*)buf(c, "alpha.sc", sizeof(float) * alpha_scratch_floats(count) + 64);
+    double* dl = (double*)buf(c, "alpha.loss", sizeof(double) * 2);
+    ck(c, cudaMemcpyAsync(dW, c->alpha_w.data(), sizeof(float) * NW, cudaMemcpyHostToDevice, c->st), "copy");
+    ck(c, cudaMemcpyAsync(dX, feat, sizeof(float) * 32 * count, cudaMemcpyHostToDevice, c->st), "copy");
+    ck(c, cudaMemcpyAsync(dT, label, sizeof(float) * count, cudaMemcpyHostToDevice, c->st), "copy");
+    timed(c, EV_EW, 0, 0, 0, [&] { return alpha_gradient(dW, dX, dT, count, sc, dG, dl, c->st); });
+    ck(c, cudaMemcpyAsync(grad, dG, sizeof(float) * NT, cudaMemcpyDeviceToHost, c->st), "copy");
+    double hl = 0.0;
+    read_back(c, dl, 1, &hl);
+    if (loss) *loss = hl;
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_alpha_train(qpinv_ctx* c, void* stream, int count, const float* feat, const float* label, int epochs,
+                      int batch, float lr, unsigned long long seed, double* loss) {
+  if (!c || count < 2 || !feat || !label || epochs < 1 || batch < 1 || !(lr > 0.f))
+    return c ? fail(c, QPINV_E_INVALID, "invalid argument") : QPINV_E_INVALID;
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    const int NW = alpha_nweights(), NT = alpha_ntrain();
+    std::vector<float> W(NW);
+    alpha_init_weights(W.data(), seed);
+    // input standardisation from the training set (mu, sd stored with the weights)
+    for (int j = 0; j < 32; j++) {
+      double mu = 0, v = 0;
+      for (int i = 0; i < count; i++) mu += feat[(size_t)i * 32 + j];
+      mu /= count;
+      for (int i = 0; i < count; i++) v += (feat[(size_t)i * 32 + j] - mu) * (feat[(size_t)i * 32 + j] - mu);
+      W[NW - 64 + j] = (float)mu;
+      W[NW - 32 + j] = (float)std::max(std::sqrt(v / count), 1e-3);
+    }
+    if (batch > count) batch = count;
+    float* dW = (float*)buf(c, "alpha.W", sizeof(float) * NW);
+    float* dX = (float*)buf(c, "alpha.X", sizeof(float) * 32 * (size_t)count);
+    float* dT = (float*)buf(c, "alpha.T", sizeof(float) * (size_t)count);
+    float* dG = (float*)buf(c, "alpha.G", sizeof(float) * NT);
+    float* dM1 = (float*)buf(c, "alpha.M1", sizeof(float) * NT);
+    float* dM2 = (float*)buf(c, "alpha.M2", sizeof(float) * NT);
+    float* sc = (float*)buf(c, "alpha.sc", sizeof(float) * alpha_scratch_floats(std::max(batch, count)) + 64);
+    double* dl = (double*)buf(c, "alpha.loss", sizeof(double) * 2);
+    ck(c, cudaMemcpyAsync(dW, W.data(), sizeof(float) * NW, cudaMemcpyHostToDevice, c->st), "copy");
+    ck(c, cudaMemsetAsync(dM1, 0, sizeof(float) * NT, c->st), "memset");
+    ck(c, cudaMemsetAsync(dM2, 0, sizeof(float) * NT, c->st), "memset");
+    std::vector<int> perm(count);
+    for (int i = 0; i < count; i++) perm[i] = i;
+    std::vector<float> px((size_t)count * 32), pt(count);
+    unsigned long long st = seed * 0x9E3779B97F4A7C15ull + 1;
+    int step = 0;
+    for (int ep = 0; ep < epochs; ep++) {
+      for (int i = count - 1; i > 0; i--) {  // Fisher-Yates with splitmix64
+        st += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        std::swap(perm[i], perm[(int)(z % (unsigned long long)(i + 1))]);
+      }
+      for (int i = 0; i < count; i++) {
+        memcpy(&px[(size_t)i * 32], &feat[(size_t)perm[i] * 32], sizeof(float) * 32);
+        pt[i] = label[perm[i]];
+      }
+      ck(c, cudaMemcpyAsync(dX, px.data(), sizeof(float) * 32 * count, cudaMemcpyHostToDevice, c->st), "copy");
+      ck(c, cudaMemcpyAsync(dT, pt.data(), sizeof(float) * count, cudaMemcpyHostToDevice, c->st), "copy");
+      for (int b0 = 0; b0 + batch <= count; b0 += batch) {
+        step++;
+        timed(c, EV_EW, 0, 0, 0,
+              [&] { return alpha_gradient(dW, dX + (size_t)b0 * 32, dT + b0, batch, sc, dG, dl, c->st); });
+        timed(c, EV_EW, 0, 0, 0, [&] { return alpha_adam(dW, dG, dM1, dM2, step, lr, c->st); });
+      }
+      ck(c, cudaStreamSynchronize(c->st), "sync");  // host buffers px, pt are reused next epoch
+    }
+    timed(c, EV_EW, 0, 0, 0, [&] { return alpha_gradient(dW, dX, dT, count, sc, dG, dl, c->st); });
+    double hl = 0.0;
+    read_back(c, dl, 1, &hl);
+    if (loss) *loss = hl;
+    ck(c, cudaMemcpyAsync(W.data(), dW, sizeof(float) * NW, cudaMemcpyDeviceToHost, c->st), "copy");
+    ck(c, cudaStreamSynchronize(c->st), "sync");
+    c->alpha_w = W;
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
+int qpinv_alpha_predict(qpinv_ctx* c, void* stream, const float* feat, double* y) {
+  if (!c || !feat || !y || c->alpha_w.empty())
+    return c ? fail(c, QPINV_E_INVALID, "invalid argument or untrained network") : QPINV_E_INVALID;
+  DeviceGuard g(c->device);
+  c->st = (cudaStream_t)stream;
+  try {
+    *y = predict_one(c, feat);
   } catch (const QpError& e) {
     cudaGetLastError();
     return fail(c, e.code, e.msg);

@@ -1,0 +1,93 @@
+"""Dataset, labels and evaluation for the learned initial scaling alpha.
+
+The network itself (features, forward, backward, Adam) runs in libqpinv's
+kernels; this module only builds training matrices with known spectra from
+the seeded generators, computes labels, and drives the C ABI.
+
+Families (the workloads' generators at smaller sizes):
+  dense      -- Gaussian quaternion m x n (spectrum from LAPACK on the
+                complex representation, used for the label only);
+  logspaced  -- U diag(sigma) V^H, sigma log-spaced from 1 to 10^-u;
+  geometric  -- rank r < min(m, n), sigma geometric from 1 to 10^-u;
+  clustered  -- sigma drawn around 2-4 cluster centres (held-out mix).
+Label: y = log(alpha* theta_1), alpha* = 2 / (sigma_1^2 + sigma_r^2) the
+minimiser of Thm. 1's max |1 - alpha sigma_i^2|, theta_1 the features'
+Lanczos estimate of sigma_1^2 (so alpha = exp(y) / theta_1), scaled down by
+1.1 so that most predictions clear the solver's contraction check.
+"""
+import math
+
+import numpy as np
+
+from . import inputs
+
+MARGIN = 1.1
+TRAIN_FAMILIES = ("dense", "logspaced", "geometric")
+HELDOUT_FAMILIES = ("logspaced", "geometric", "clustered")
+
+
+def _spectrum(family, r, rng):
+    u = rng.uniform(1.0, 8.0)
+    if family == "logspaced":
+        return np.logspace(0.0, -u, r)
+    if family == "geometric":
+        return np.geomspace(1.0, 10.0 ** -u, r)
+    centres = 10.0 ** -rng.uniform(0.0, u, size=rng.integers(2, 5))
+    centres[0] = 1.0
+    s = centres[rng.integers(0, len(centres), size=r)] * np.exp(rng.normal(0.0, 0.05, size=r))
+    return np.sort(s)[::-1] / s.max()
+
+
+def sample_matrix(family, m, n, seed, device="cpu"):
+    """(A planes (4, m, n), nonzero singular values descending)."""
+    rng = np.random.default_rng(seed)
+    if family == "dense":
+        A = inputs.gaussian_quaternion(m, n, seed)
+        sv = np.linalg.svd(inputs.chi(A), compute_uv=False)[::2]
+        return A, sv
+    k = min(m, n)
+    r = k if family != "geometric" else int(rng.integers(max(1, k // 4), max(2, k // 2) + 1))
+    sigma = _spectrum(family, r, rng) * 10.0 ** rng.uniform(-2, 2)
+    U = inputs.orthonormal_columns(m, r, 2 * seed + 1, device)
+    V = inputs.orthonormal_columns(n, r, 2 * seed + 2, device)
+    return inputs.with_spectrum(U, sigma, V, device), sigma
+
+
+def optimal_alpha(sigma):
+    s = np.asarray(sigma, dtype=np.float64)
+    s = s[s > 0]
+    return 2.0 / (s.max() ** 2 + s.min() ** 2)
+
+
+def make_dataset(ctx, count, lo, hi, seed, families=TRAIN_FAMILIES, device="cpu", to_device=None):
+    """Features (count x 32), labels (count) and per-sample (family, m, n, theta_1)."""
+    rng = np.random.default_rng(seed)
+    feats, labels, meta = [], [], []
+    for t in range(count):
+        fam = families[t % len(families)]
+        m = int(rng.integers(lo, hi + 1))
+        n = int(rng.integers(lo, hi + 1)) if rng.uniform() < 0.5 else m
+        A, sigma = sample_matrix(fam, m, n, seed * 100003 + t, device)
+        Ad = to_device(A) if to_device else A
+        f, theta1 = ctx.alpha_features(Ad)
+        feats.append(f)
+        labels.append(math.log(optimal_alpha(sigma) * theta1 / MARGIN))
+        meta.append((fam, m, n, theta1))
+    return np.array(feats, dtype=np.float32), np.array(labels, dtype=np.float32), meta
+
+
+def compare_iterations(ctx, mats, method="qhpi19", tol=1e-12, to_device=None):
+    """Solves every matrix with the safe and the learned alpha; returns a list
+    of (iters_safe, iters_learned, E1rel_safe, E1rel_learned, alpha_source,
+    precision_safe, precision_learned)."""
+    out = []
+    for A in mats:
+        Ad = to_device(A) if to_device else A
+        ctx.configure(alpha="safe")
+        _, s = ctx.solve(Ad, method, tol=tol)
+        ctx.configure(alpha="learned")
+        _, l = ctx.solve(Ad, method, tol=tol)
+        out.append((s["iters"], l["iters"], s["E_rel"][0], l["E_rel"][0], l["alpha_source"], s["precision"],
+                    l["precision"]))
+    ctx.configure(alpha="safe")
+    return out

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libqpinv.so")
 
 METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3}
 PRECISION = {"fp64": 0, "mixed": 1, "tc": 2, "emu": 3}
+PRECISION_NAME = {0: "fp64", 1: "mixed", 2: "tc", 3: "emu", 4: "df32"}
 ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3, "learned": 4}
 SIDE = {"auto": 0, "right": 1, "left": 2}
 STOP = {"paper_abs": 0, "rel_plateau": 1}
@@ -40,9 +41,9 @@ class qpinv_options(ctypes.Structure):
 class qpinv_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("tc_iters", ctypes.c_int),
                 ("polish_iters", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_source", ctypes.c_int),
-                ("side", ctypes.c_int), ("delta", ctypes.c_double), ("delta_rel", ctypes.c_double),
-                ("E", ctypes.c_double * 4), ("E_rel", ctypes.c_double * 4), ("gemms", ctypes.c_longlong),
-                ("time_ms", ctypes.c_double)]
+                ("side", ctypes.c_int), ("precision", ctypes.c_int), ("delta", ctypes.c_double),
+                ("delta_rel", ctypes.c_double), ("E", ctypes.c_double * 4), ("E_rel", ctypes.c_double * 4),
+                ("gemms", ctypes.c_longlong), ("time_ms", ctypes.c_double)]
 
 
 class qpinv_stats(ctypes.Structure):
@@ -59,7 +60,9 @@ _lib = None
 # every symbol include/qpinv.h declares (checked by the tests)
 EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_solve", "qpinv_solve_batched",
            "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
-           "qpinv_reset_stats", "qpinv_qgemm_noalloc")
+           "qpinv_reset_stats", "qpinv_qgemm_noalloc", "qpinv_alpha_features", "qpinv_alpha_train",
+           "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights")
+ALPHA_NFEAT, ALPHA_NWEIGHTS, ALPHA_NTRAIN = 32, 6401, 6337
 
 
 def lib():
@@ -87,6 +90,13 @@ def lib():
         L.qpinv_get_stats.argtypes = [vp, ctypes.POINTER(qpinv_stats)]
         L.qpinv_reset_stats.argtypes = [vp]
         L.qpinv_qgemm_noalloc.argtypes = [vp, i, i, i, PTR4, l, PTR4, l, PTR4, l, i]
+        fp = ctypes.POINTER(ctypes.c_float)
+        dp = ctypes.POINTER(d)
+        L.qpinv_alpha_features.argtypes = [vp, vp, i, i, PTR4, l, fp, dp]
+        L.qpinv_alpha_train.argtypes = [vp, vp, i, fp, fp, i, i, ctypes.c_float, ctypes.c_ulonglong, dp]
+        L.qpinv_alpha_predict.argtypes = [vp, vp, fp, dp]
+        L.qpinv_alpha_gradient.argtypes = [vp, vp, i, fp, fp, fp, dp]
+        L.qpinv_alpha_weights.argtypes = [vp, fp, i, i]
         _lib = L
     return _lib
 
@@ -162,6 +172,10 @@ def _planes(x):
     base = a.ctypes.data
     p = PTR4(*[base + c * a.strides[0] for c in range(4)])
     return p, a.strides[1] // 8, a
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
 def _stream_handle(stream):
@@ -281,6 +295,54 @@ class Context:
         _check(self.h, rc, "qpinv_penrose")
         return list(E), list(R)
 
+    # ---- learned alpha ----
+    def alpha_features(self, A, stream=None):
+        """(features[32] float32, theta_1) of A."""
+        m, n = A.shape[1], A.shape[2]
+        pa, lda, _ka = _planes(A)
+        f = np.zeros(ALPHA_NFEAT, dtype=np.float32)
+        t1 = ctypes.c_double()
+        rc = lib().qpinv_alpha_features(self.h, _stream_handle(stream), m, n, pa, lda, _fptr(f), ctypes.byref(t1))
+        _check(self.h, rc, "qpinv_alpha_features")
+        return f, t1.value
+
+    def alpha_train(self, feats, labels, epochs=200, batch=128, lr=1e-3, seed=0, stream=None):
+        X = np.ascontiguousarray(feats, dtype=np.float32)
+        T = np.ascontiguousarray(labels, dtype=np.float32)
+        assert X.ndim == 2 and X.shape[1] == ALPHA_NFEAT and T.shape == (X.shape[0],)
+        loss = ctypes.c_double()
+        rc = lib().qpinv_alpha_train(self.h, _stream_handle(stream), X.shape[0], _fptr(X), _fptr(T), int(epochs),
+                                     int(batch), float(lr), int(seed), ctypes.byref(loss))
+        _check(self.h, rc, "qpinv_alpha_train")
+        return loss.value
+
+    def alpha_predict(self, feat, stream=None):
+        f = np.ascontiguousarray(feat, dtype=np.float32)
+        y = ctypes.c_double()
+        _check(self.h, lib().qpinv_alpha_predict(self.h, _stream_handle(stream), _fptr(f), ctypes.byref(y)),
+               "qpinv_alpha_predict")
+        return y.value
+
+    def alpha_gradient(self, feats, labels, stream=None):
+        X = np.ascontiguousarray(feats, dtype=np.float32)
+        T = np.ascontiguousarray(labels, dtype=np.float32)
+        g = np.zeros(ALPHA_NTRAIN, dtype=np.float32)
+        loss = ctypes.c_double()
+        rc = lib().qpinv_alpha_gradient(self.h, _stream_handle(stream), X.shape[0], _fptr(X), _fptr(T), _fptr(g),
+                                        ctypes.byref(loss))
+        _check(self.h, rc, "qpinv_alpha_gradient")
+        return g, loss.value
+
+    def alpha_weights(self, w=None):
+        """Returns the weight block, or loads `w` (QPINV_ALPHA_NWEIGHTS floats)."""
+        if w is None:
+            out = np.zeros(ALPHA_NWEIGHTS, dtype=np.float32)
+            _check(self.h, lib().qpinv_alpha_weights(self.h, _fptr(out), ALPHA_NWEIGHTS, 0), "qpinv_alpha_weights")
+            return out
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(self.h, lib().qpinv_alpha_weights(self.h, _fptr(w), ALPHA_NWEIGHTS, 1), "qpinv_alpha_weights")
+        return w
+
     def stats(self):
         s = qpinv_stats()
         _check(self.h, lib().qpinv_get_stats(self.h, ctypes.byref(s)), "qpinv_get_stats")
@@ -293,5 +355,6 @@ class Context:
 def result_dict(r):
     return dict(status=STATUS.get(r.status, r.status), iters=r.iters, tc_iters=r.tc_iters,
                 polish_iters=r.polish_iters, alpha=r.alpha, alpha_source=r.alpha_source,
-                side="left" if r.side == 2 else "right", delta=r.delta, delta_rel=r.delta_rel,
+                side="left" if r.side == 2 else "right", precision=PRECISION_NAME.get(r.precision, r.precision),
+                delta=r.delta, delta_rel=r.delta_rel,
                 E=list(r.E), E_rel=list(r.E_rel), gemms=r.gemms, time_ms=r.time_ms)

@@ -1,0 +1,98 @@
+"""Learned initial scaling on the GPU: features against numpy definitions
+(complete Lanczos = the spectrum of A^H A), the training gradient of the
+library's kernels against the FP64 oracle network, training on generator
+families, and the gain over the safe alpha on held-out matrices at equal
+accuracy (E1/||A|| within 10x of the safe-alpha solve's, or <= 1e-10)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2605_01464_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_01464_gb300 import build, qpinv
+    build.build()
+    return qpinv
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_gradient_matches_fp64_oracle(qp):
+    ctx = qp.Context(0)
+    rng = np.random.default_rng(7)
+    w = rng.normal(0, 0.3, mlp.NWEIGHTS).astype(np.float32)
+    w[mlp.OFF_MU:mlp.OFF_SD] = rng.normal(0, 1, mlp.NF)
+    w[mlp.OFF_SD:] = rng.uniform(0.5, 2.0, mlp.NF)
+    ctx.alpha_weights(w)
+    X = rng.normal(size=(64, mlp.NF)).astype(np.float32)
+    T = rng.normal(size=64).astype(np.float32)
+    g, loss = ctx.alpha_gradient(X, T)
+    go = mlp.gradient(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    assert abs(loss - mlp.loss(w.astype(np.float64), X, T)) <= 1e-5 * loss
+    ctx.close()
+
+
+def test_features_match_definitions(qp):
+    ctx = qp.Context(0)
+    A = I.gaussian_quaternion(12, 9, 3)
+    f, theta1 = ctx.alpha_features(cuda(A))
+    C = I.chi(A)
+    sv2 = np.sort(np.linalg.svd(C, compute_uv=False)[::2] ** 2)[::-1]  # quaternion singular values squared
+    mod = np.sqrt((A ** 2).sum(axis=0))
+    n1, ninf, fro2 = mod.sum(axis=0).max(), mod.sum(axis=1).max(), (A ** 2).sum()
+    assert abs(theta1 - sv2[0]) <= 1e-5 * sv2[0]  # 9 Lanczos steps on a 9 x 9 A^H A: exact
+    want = [np.log(12), np.log(9), np.log(fro2 / sv2[0]), 0.5 * np.log(fro2), np.log(n1), np.log(ninf),
+            np.log(sv2[0]), np.log(sv2[0] / (n1 * ninf))]
+    assert np.allclose(f[:8], want, rtol=1e-4, atol=1e-4)
+    assert np.allclose(f[8:17], sv2 / sv2[0], rtol=1e-3, atol=1e-5)
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def trained(qp):
+    from paper_2605_01464_gb300 import learned_alpha as LA
+    ctx = qp.Context(0)
+    feats, labels, meta = LA.make_dataset(ctx, 360, 16, 64, seed=11, to_device=cuda)
+    loss = ctx.alpha_train(feats, labels, epochs=300, batch=60, lr=3e-3, seed=5)
+    yield ctx, LA, feats, labels, loss
+    ctx.close()
+
+
+def test_training_fits_and_generalises(trained):
+    # Labels are log(alpha* theta_1 / 1.1), mostly near log(2 / 1.1) (sigma_r << sigma_1);
+    # the fit is judged in absolute log-alpha error and against the safe rule,
+    # whose log(alpha theta_1) is feature 7.
+    ctx, LA, feats, labels, loss = trained
+    assert loss < 1e-3, loss
+    f2, l2, _ = LA.make_dataset(ctx, 60, 16, 64, seed=12, to_device=cuda)
+    pred = np.array([ctx.alpha_predict(f) for f in f2])
+    err = np.abs(pred - l2)
+    assert np.sqrt(np.mean(err ** 2)) < 0.05, err  # alpha within about 5% of the label
+    assert np.mean(err) < 0.25 * np.mean(np.abs(f2[:, 7] - l2))
+
+
+@pytest.mark.parametrize("method", ["qhpi19", "ns"])
+def test_learned_alpha_saves_iterations(trained, method):
+    ctx, LA, *_ = trained
+    mats = [LA.sample_matrix(fam, m, m + d, 900 + k)[0]
+            for k, (fam, m, d) in enumerate([("logspaced", 96, 0), ("geometric", 80, 16), ("clustered", 64, 32),
+                                              ("logspaced", 120, -20), ("clustered", 100, 0), ("geometric", 72, 0)])]
+    rows = LA.compare_iterations(ctx, mats, method, tol=1e-12, to_device=cuda)
+    safe = sum(r[0] for r in rows)
+    learned = sum(r[1] for r in rows)
+    assert learned < safe, rows
+    # Equal accuracy: rank-deficient families (kappa up to 1e8 here) fail MIXED's
+    # Penrose check and are repeated in EMU, whose E1 floor is about eps * kappa.
+    assert all(r[3] <= max(1e-10, 10.0 * r[2]) and r[2] <= 1e-7 for r in rows), rows
+    assert all(r[5] == r[6] for r in rows), rows
+    assert sum(r[4] == 4 for r in rows) >= len(rows) // 2, rows  # prediction accepted (QPINV_ALPHA_LEARNED)

@@ -31,7 +31,7 @@ METRIC = "pinv solves/s & quaternion-GEMM TFLOP/s (% TC peak) to rel. Penrose re
 # sample extrapolates to: iterations x 7 products + 4 Penrose products.  The
 # iteration count is the one the GPU arm reports for this workload
 # ("iters" in its JSON line).
-WORKLOAD_ITERS = 13
+WORKLOAD_ITERS = 16
 
 
 def peaks():
@@ -161,16 +161,26 @@ def kernel_qgemm(args, torch, qpinv):
     A = torch.from_numpy(inputs.gaussian_quaternion(n, n, 21)).cuda()
     B = torch.from_numpy(inputs.gaussian_quaternion(n, n, 22)).cuda()
     ctx = qpinv.Context(0, profile=True)
+    prec = args.gemm_precision
     for _ in range(args.warmup):
-        ctx.qgemm(A, B, precision="tc", split_level=args.split)
+        ctx.qgemm(A, B, precision=prec, split_level=args.split)
     ctx.reset_stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx.qgemm(A, B, precision="tc", split_level=args.split)
+        ctx.qgemm(A, B, precision=prec, split_level=args.split)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.steps
     st = ctx.stats()
-    ms = st["tc_gemm_ms"] / max(st["tc_gemm_launches"], 1)
-    print(json.dumps({"kernel": "k_qgemm_tc", "n": n, "split": args.split, "ms_per_launch": ms,
-                      "tflops_algorithmic": st["tc_gemm_flops"] / st["tc_gemm_launches"] / ms / 1e9,
-                      "tflops_issued": st["tc_gemm_flops_issued"] / st["tc_gemm_launches"] / ms / 1e9}))
+    launches = max(st["tc_gemm_launches"], 1)
+    ms = st["tc_gemm_ms"] / launches
+    print(json.dumps({"kernel": "k_qgemm_tc", "n": n, "precision": prec, "split": args.split,
+                      "launches_per_product": launches / args.steps, "ms_per_launch": ms,
+                      "gemm_ms_per_product": st["tc_gemm_ms"] / args.steps,
+                      "all_kernels_ms_per_product": (st["tc_gemm_ms"] + st["ew_ms"]) / args.steps,
+                      "wall_ms_per_product": wall * 1e3,
+                      "tflops_algorithmic": st["tc_gemm_flops"] / st["tc_gemm_ms"] / 1e9,
+                      "tflops_issued": st["tc_gemm_flops_issued"] / st["tc_gemm_ms"] / 1e9}))
     return 0
 
 
@@ -204,6 +214,121 @@ def bench_batched(args, torch, qpinv):
     return 0
 
 
+def _timed_solve(ctx, torch, A, method, tol):
+    """One solve on the current stream, timed with CUDA events."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, info = ctx.solve(A, method, tol=tol, max_iter=500, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), info
+
+
+def bench_rankdef(args, torch, qpinv):
+    """Rank-2048 8192 x 4096 A = QL diag(sigma) QR^H, sigma geometric 1..1e-4
+    (seeds 4, 5): QHPI19 and Newton-Schulz with FP64-accurate tensor-core
+    products (EMU) and the plateau stop; one step = one QHPI19 solve."""
+    from paper_2605_01464_gb300 import inputs
+    dev = "cuda" if args.gen_device == "cuda" else "cpu"
+    A = torch.from_numpy(inputs.rank_deficient(8192, 4096, 2048, 1e-4, 4, 5, device=dev)[0]).cuda()
+    ctx = qpinv.Context(0, precision="emu", profile=True)
+    out = {}
+    with ClockSampler(0) as clk:
+        for method in ("qhpi19", "ns"):
+            for _ in range(args.warmup):
+                _timed_solve(ctx, torch, A, method, args.tol)
+            ctx.reset_stats()
+            times, info = [], None
+            for _ in range(args.steps if method == "qhpi19" else 1):
+                ms, info = _timed_solve(ctx, torch, A, method, args.tol)
+                times.append(ms)
+            st = ctx.stats()
+            out[method] = {"ms_per_solve": statistics.mean(times), "iters": info["iters"], "status": info["status"],
+                           "E_rel": info["E_rel"], "gemms": info["gemms"], "gpu_launches": st["kernel_launches"],
+                           "tc_gemm_ms": st["tc_gemm_ms"], "tc_gemm_flops_issued": st["tc_gemm_flops_issued"],
+                           "tc_gemm_flops": st["tc_gemm_flops"]}
+    q = out["qhpi19"]
+    bf16_burst, bf16_sust, hbm, src = peaks()
+    issued = q["tc_gemm_flops_issued"] / q["tc_gemm_ms"] / 1e9
+    alg = q["tc_gemm_flops"] / q["tc_gemm_ms"] / 1e9
+    print(json.dumps({
+        "metric": "rank-deficient pinv solves/s to rel. Penrose res (FP64 floor)", "value": 1e3 / q["ms_per_solve"],
+        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q["ms_per_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "exact-slice bf16 (FP64-accurate)",
+        "data": "synthetic",
+        "config": {"workload": "8192x4096 quaternion, rank 2048, A = QL diag(sigma) QR^H, sigma geometric 1..1e-4, "
+                               "orthonormal factors from Gaussian quaternion matrices (seeds 4, 5); left residual "
+                               "(4096 side); EMU precision; rel. tol %g with plateau stop" % args.tol,
+                   "l2": "inputs exceed L2"},
+        "roofline": {"bound": "tensor", "achieved": alg, "achieved_issued": issued, "peak": bf16_sust,
+                     "unit": "TFLOP/s", "frac": alg / bf16_sust, "frac_issued": issued / bf16_sust, "traffic": None,
+                     "kernel": "k_qgemm_tc (exact-slice passes)",
+                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src},
+        "result": out, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
+def bench_learned(args, torch, qpinv):
+    """Learned initial scaling: train the MLP on generator families at sizes
+    32..256, then solve held-out full-rank 1024^2 and 2048 x 1024 matrices
+    (log-uniform / geometric / clustered spectra, kappa <= 1e5) with the safe
+    and the learned alpha (MIXED), and one with the plain FP64 form."""
+    import numpy as np
+
+    from paper_2605_01464_gb300 import learned_alpha as LA
+
+    def cuda(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    ctx = qpinv.Context(0)
+    t0 = time.perf_counter()
+    feats, labels, _ = LA.make_dataset(ctx, args.train_count, 32, 256, seed=11, device="cuda", to_device=cuda)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = ctx.alpha_train(feats, labels, epochs=300, batch=100, lr=3e-3, seed=5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = []
+    shapes = [(1024, 1024), (2048, 1024)]
+    with ClockSampler(0) as clk:
+        for k, fam in enumerate(("logspaced", "geometric", "clustered")):
+            for (m, n) in shapes:
+                A = cuda(LA.heldout_matrix(fam, m, n, 700 + 10 * k + m // 1024, device="cuda")[0])
+                res = {}
+                for mode in ("safe", "learned"):
+                    ctx.configure(alpha=mode)
+                    _timed_solve(ctx, torch, A, "qhpi19", args.tol)  # warm-up
+                    ms, info = _timed_solve(ctx, torch, A, "qhpi19", args.tol)
+                    res[mode] = {"ms": ms, "iters": info["iters"], "E1_rel": info["E_rel"][0],
+                                 "alpha_source": info["alpha_source"], "precision": info["precision"]}
+                rows.append({"family": fam, "m": m, "n": n, **res})
+        ctx.configure(alpha="safe")
+        A = cuda(LA.heldout_matrix("logspaced", 1024, 1024, 700, device="cuda")[0])
+        ctx.configure(precision="fp64")
+        ms64, info64 = _timed_solve(ctx, torch, A, "qhpi19", args.tol)
+        ctx.configure(precision="mixed", alpha="learned")
+        msl, infol = _timed_solve(ctx, torch, A, "qhpi19", args.tol)
+        ctx.configure(alpha="safe")
+    safe_ms = sum(r["safe"]["ms"] for r in rows)
+    learned_ms = sum(r["learned"]["ms"] for r in rows)
+    print(json.dumps({
+        "metric": "held-out solve time, safe alpha / learned alpha (QHPI19, mixed, equal accuracy)",
+        "value": safe_ms / learned_ms, "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "dtype": "bf16-split/f32-acc + exact-slice f64", "data": "synthetic",
+        "config": {"workload": "MLP 32-64-64-1 trained on %d generator-family matrices (32..256); held-out "
+                               "1024^2 and 2048x1024, kappa = 10^U[1,5]" % args.train_count},
+        "training": {"samples": args.train_count, "final_loss": loss, "data_s": t_data, "train_s": t_train},
+        "iters": {"safe": sum(r["safe"]["iters"] for r in rows), "learned": sum(r["learned"]["iters"] for r in rows)},
+        "rows": rows,
+        "vs_fp64_fixed_alpha": {"matrix": "logspaced 1024^2 (seed 700)", "fp64_safe_ms": ms64,
+                                "fp64_E1_rel": info64["E_rel"][0], "mixed_learned_ms": msl,
+                                "mixed_learned_E1_rel": infol["E_rel"][0], "speedup": ms64 / msl},
+        "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def workload_config(args):
     return {"workload": "square %dx%d quaternion A = U diag(sigma) V^H, Haar U and V, sigma log-spaced 1..1e-6; "
                         "%s, mixed precision (BF16-split tensor-core products with FP32 accumulation; exact-slice "
@@ -228,9 +353,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default=None, choices=["qgemm"],
                     help="time only the tensor-core quaternion GEMM (n x n x n) for kernel profiling")
-    ap.add_argument("--split", type=int, default=1, help="BF16 terms of --kernel qgemm (1..3)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched"],
-                    help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step")
+    ap.add_argument("--split", type=int, default=1,
+                    help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
+    ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "rankdef", "learned"],
+                    help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "
+                         "rankdef: rank-2048 8192x4096 (QHPI19 and NS, EMU); learned: learned-alpha training "
+                         "and held-out evaluation")
+    ap.add_argument("--train-count", type=int, default=1500, help="--workload learned: training matrices")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
     args = ap.parse_args()
@@ -253,6 +383,10 @@ def main():
         return kernel_qgemm(args, torch, qpinv)
     if args.workload == "batched":
         return bench_batched(args, torch, qpinv)
+    if args.workload == "rankdef":
+        return bench_rankdef(args, torch, qpinv)
+    if args.workload == "learned":
+        return bench_learned(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -17,6 +17,9 @@
 
 namespace qp {
 
+// kernels launched by this thread through the launch_* functions below
+extern thread_local long long g_kernel_launches;
+
 typedef __nv_bfloat16 bf16;
 
 // Row-major plane set: element (c, i, j) at p[c * ps + i * ld + j].
@@ -84,20 +87,24 @@ namespace qp {
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_out);
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int nvals, double* out,
                                    cudaStream_t st);
+// colsum needs `scratch` of COL_SCRATCH(n) doubles
 cudaError_t launch_abs_sums(const Planes<const double>& A, int m, int n, double* rowsum,
-                            double* colsum, cudaStream_t st);
+                            double* colsum, double* scratch, cudaStream_t st);
 cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st);
+// scratch entries of a column reduction over `cols` columns
+inline long COL_SCRATCH(long cols) { return 64 * cols; }
 cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m,
                                  int n, double* partials, cudaStream_t st, int* blocks_out);
 cudaError_t launch_antiherm_partials(const Planes<const double>& M, int n, double* partials,
                                      cudaStream_t st, int* blocks_out);
 cudaError_t launch_init_x0(const Planes<const double>& A, int m, int n, double alpha, const Planes<double>& X,
                            cudaStream_t st);
-cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e,
+// by_col needs `scratch` of COL_SCRATCH(cols) ints
+cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e, int* scratch,
                               cudaStream_t st);
 cudaError_t launch_f64_to_f32(const Planes<const double>& src, int rows, int cols, const Planes<float>& dst,
                               cudaStream_t st);
-cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e,
+cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e, int* scratch,
                           cudaStream_t st);
 cudaError_t launch_f32_to_f64(const Planes<const float>& src, int rows, int cols,
                               const Planes<double>& dst, cudaStream_t st);
@@ -125,6 +132,26 @@ struct TcGemmArgs {
   int* err = nullptr;  // device error word (bounded-wait expiry)
 };
 cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);
+
+// FP64-accurate product from S exact slices per operand in one launch
+// (qgemm_emu.cu): C64 += sum over levels d < S of the level-d slice products,
+// in 64-bit fixed point (value * 2^shift).  kc[d] = K chunk of level d
+// (multiple of 32, or >= K), short enough that every FP32 partial sum of the
+// level is exact.  emu_fused_ok(K, S) says whether K is small enough for the
+// kernel's int32 per-level sums.
+struct EmuGemmArgs {
+  int M = 0, N = 0, K = 0;
+  const Split16* A = nullptr;  // A-form slices (levels >= S)
+  const Split16* B = nullptr;  // B-form slices (levels >= S)
+  int S = 0;
+  int kc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long* C64 = nullptr;
+  long ld64 = 0, ps64 = 0;
+  int shift = 0;
+  int* err = nullptr;
+};
+bool emu_fused_ok(int K, int S);
+cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st);
 bool tc_supported();
 
 // Batched solver (batched.cu).

@@ -10,9 +10,13 @@
 // extraction use integer operations on the bit patterns.  Reductions are
 // deterministic: each block writes partial sums and one block adds them in a
 // fixed order.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace qp {
+
+thread_local long long g_kernel_launches = 0;
 
 namespace {
 
@@ -208,18 +212,39 @@ __global__ void k_row_abs_sums(Planes<const double> A, int m, int n, double* row
   if (lane == 0) rowsum[warp] = s;
 }
 
-__global__ void k_col_abs_sums(Planes<const double> A, int m, int n, double* colsum) {
+// Column reductions: blocks of 32 columns x one row chunk (a warp reads 32
+// consecutive entries of a row) write one partial per (chunk, column); the
+// finishing kernel combines the partials in chunk order, so the result does
+// not depend on scheduling.
+constexpr int CR_COLS = 32, CR_ROWS = 8, CR_MAX_CHUNKS = 64;
+
+__global__ void k_col_abs_part(Planes<const double> A, int m, int n, int chunk_rows, double* part) {
+  __shared__ double sh[CR_ROWS][CR_COLS];
+  const int j = blockIdx.x * CR_COLS + threadIdx.x;
+  const int r0 = blockIdx.y * chunk_rows, r1 = min(m, r0 + chunk_rows);
+  double s = 0.0;
+  if (j < n)
+    for (int i = r0 + threadIdx.y; i < r1; i += CR_ROWS) {
+      double q = 0.0;
+      for (int c = 0; c < 4; c++) {
+        const double x = A.p[c * A.ps + (long)i * A.ld + j];
+        q += x * x;
+      }
+      s += sqrt(q);
+    }
+  sh[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    for (int t = 1; t < CR_ROWS; t++) s += sh[t][threadIdx.x];
+    part[(long)blockIdx.y * n + j] = s;
+  }
+}
+
+__global__ void k_col_abs_finish(const double* part, int chunks, int n, double* colsum) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double s = 0.0;
-  for (int i = 0; i < m; i++) {
-    double q = 0.0;
-    for (int c = 0; c < 4; c++) {
-      const double x = A.p[c * A.ps + (long)i * A.ld + j];
-      q += x * x;
-    }
-    s += sqrt(q);
-  }
+  for (int ch = 0; ch < chunks; ch++) s += part[(long)ch * n + j];
   colsum[j] = s;
 }
 
@@ -324,13 +349,37 @@ __global__ void k_row_maxexp(Planes<const T> A, int rows, int cols, int* e) {
 }
 
 template <typename T>
-__global__ void k_col_maxexp(Planes<const T> A, int rows, int cols, int* e) {
+__global__ void k_col_maxexp_part(Planes<const T> A, int rows, int cols, int chunk_rows, int* part) {
+  __shared__ int sh[CR_ROWS][CR_COLS];
+  const int j = blockIdx.x * CR_COLS + threadIdx.x;
+  const int r0 = blockIdx.y * chunk_rows, r1 = min(rows, r0 + chunk_rows);
+  int mx = -100000;
+  if (j < cols)
+    for (int i = r0 + threadIdx.y; i < r1; i += CR_ROWS)
+      for (int c = 0; c < 4; c++) mx = max(mx, exp_of(A.p[c * A.ps + (long)i * A.ld + j]));
+  sh[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < cols) {
+    for (int t = 1; t < CR_ROWS; t++) mx = max(mx, sh[t][threadIdx.x]);
+    part[(long)blockIdx.y * cols + j] = mx;
+  }
+}
+
+__global__ void k_col_maxexp_finish(const int* part, int chunks, int cols, int* e) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= cols) return;
   int mx = -100000;
-  for (int i = 0; i < rows; i++)
-    for (int c = 0; c < 4; c++) mx = max(mx, exp_of(A.p[c * A.ps + (long)i * A.ld + j]));
+  for (int ch = 0; ch < chunks; ch++) mx = max(mx, part[(long)ch * cols + j]);
   e[j] = mx == -100000 ? 0 : mx;
+}
+
+// Row chunks of a column reduction: about four blocks per SM of a 152-SM
+// part in total, at least 64 rows per chunk.
+static int col_chunks(int rows, int cols) {
+  const int colblocks = (cols + CR_COLS - 1) / CR_COLS;
+  int ch = (608 + colblocks - 1) / colblocks;
+  ch = std::min(ch, (rows + 63) / 64);
+  return std::max(1, std::min(ch, CR_MAX_CHUNKS));
 }
 
 __global__ void k_f32_to_f64(Planes<const float> S, int rows, int cols, Planes<double> D) {
@@ -366,24 +415,33 @@ cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_ou
     k_combine<double><<<grid, TILE * TROWS, 0, st>>>(a);
   else
     k_combine<float><<<grid, TILE * TROWS, 0, st>>>(a);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int nvals, double* out,
                                    cudaStream_t st) {
   k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, nvals, out);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_abs_sums(const Planes<const double>& A, int m, int n, double* rowsum, double* colsum,
-                            cudaStream_t st) {
+                            double* scratch, cudaStream_t st) {
   k_row_abs_sums<<<(m + 7) / 8, 256, 0, st>>>(A, m, n, rowsum);
-  k_col_abs_sums<<<(n + 127) / 128, 128, 0, st>>>(A, m, n, colsum);
+  ++g_kernel_launches;
+  const int ch = col_chunks(m, n), chunk_rows = (m + ch - 1) / ch;
+  k_col_abs_part<<<dim3((n + CR_COLS - 1) / CR_COLS, ch), dim3(CR_COLS, CR_ROWS), 0, st>>>(A, m, n, chunk_rows,
+                                                                                         scratch);
+  ++g_kernel_launches;
+  k_col_abs_finish<<<(n + 255) / 256, 256, 0, st>>>(scratch, ch, n, colsum);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st) {
   k_max<<<1, 256, 0, st>>>(v, n, out);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -396,6 +454,7 @@ cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<con
   *blocks_out = blocks;
   Planes<const double> Bz = B ? *B : Planes<const double>();
   k_fro2<<<blocks, 256, 0, st>>>(A, Bz, B ? 1 : 0, m, n, partials);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -404,6 +463,7 @@ cudaError_t launch_antiherm_partials(const Planes<const double>& M, int n, doubl
   dim3 grid((n + TILE - 1) / TILE, (n + TILE - 1) / TILE);
   *blocks_out = grid.x * grid.y;
   k_antiherm<<<grid, TILE * TROWS, 0, st>>>(M, n, partials);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -411,36 +471,51 @@ cudaError_t launch_init_x0(const Planes<const double>& A, int m, int n, double a
                            cudaStream_t st) {
   dim3 grid((n + TILE - 1) / TILE, (m + TILE - 1) / TILE);
   k_init_x0<<<grid, TILE * TROWS, 0, st>>>(A, m, n, alpha, X);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e,
+cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int by_col, int* e, int* scratch,
                           cudaStream_t st) {
-  if (by_col)
-    k_col_maxexp<double><<<(cols + 127) / 128, 128, 0, st>>>(A, rows, cols, e);
-  else
+  if (by_col) {
+    const int ch = col_chunks(rows, cols), chunk_rows = (rows + ch - 1) / ch;
+    k_col_maxexp_part<double><<<dim3((cols + CR_COLS - 1) / CR_COLS, ch), dim3(CR_COLS, CR_ROWS), 0, st>>>(
+        A, rows, cols, chunk_rows, scratch);
+    k_col_maxexp_finish<<<(cols + 255) / 256, 256, 0, st>>>(scratch, ch, cols, e);
+    g_kernel_launches += 2;
+  } else {
     k_row_maxexp<double><<<(rows + 7) / 8, 256, 0, st>>>(A, rows, cols, e);
+    ++g_kernel_launches;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e,
+cudaError_t launch_maxexp_f32(const Planes<const float>& A, int rows, int cols, int by_col, int* e, int* scratch,
                               cudaStream_t st) {
-  if (by_col)
-    k_col_maxexp<float><<<(cols + 127) / 128, 128, 0, st>>>(A, rows, cols, e);
-  else
+  if (by_col) {
+    const int ch = col_chunks(rows, cols), chunk_rows = (rows + ch - 1) / ch;
+    k_col_maxexp_part<float><<<dim3((cols + CR_COLS - 1) / CR_COLS, ch), dim3(CR_COLS, CR_ROWS), 0, st>>>(
+        A, rows, cols, chunk_rows, scratch);
+    k_col_maxexp_finish<<<(cols + 255) / 256, 256, 0, st>>>(scratch, ch, cols, e);
+    g_kernel_launches += 2;
+  } else {
     k_row_maxexp<float><<<(rows + 7) / 8, 256, 0, st>>>(A, rows, cols, e);
+    ++g_kernel_launches;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_f32_to_f64(const Planes<const float>& src, int rows, int cols, const Planes<double>& dst,
                               cudaStream_t st) {
   k_f32_to_f64<<<grid_for((long)rows * cols), 256, 0, st>>>(src, rows, cols, dst);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_f64_to_f32(const Planes<const double>& src, int rows, int cols, const Planes<float>& dst,
                               cudaStream_t st) {
   k_f64_to_f32<<<grid_for((long)rows * cols), 256, 0, st>>>(src, rows, cols, dst);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -1,0 +1,296 @@
+// qgemm_emu.cu -- FP64-accurate quaternion GEMM from exact BF16 slices in ONE
+// tensor-core launch.
+//
+// Operands arrive as S exact slices per entry (row / column power-of-two
+// scaling, balanced 7-bit digits; see slice_store in elementwise.cu), so
+// A B = sum over slice pairs (s, t) of A_s B_t, and level d = s + t carries
+// the weight 2^-7(d+2).  Levels 0..S-1 are formed.  Every FP32 partial sum of
+// a level is an exact integer (in units of the level) as long as the K range
+// it spans is short enough (host-chosen chunk per level); the two lowest
+// levels run over the whole K.
+//
+// One CTA owns a 128 x 64 quaternion output tile and walks all (level,
+// K-chunk) work items: the MMA warp accumulates a chunk into an FP32 TMEM
+// buffer (columns 0..255); the epilogue warps convert it exactly to int32 and
+// add it into an int32 TMEM accumulator of the level (columns 256..511), then
+// release the buffer for the next chunk.  At the end of a level the int32 sum
+// is shifted to the common 64-bit fixed point and added to the global int64
+// accumulator through a shared-memory transpose (coalesced rows).  Global
+// traffic per product is S read-modify-writes of the accumulator instead of
+// one per chunk, and there is a single launch per product.
+//
+// int32 range: a level-d sum is bounded by 4K 2^12 (d + 3) (2^14 for d = 0)
+// level units; launch_qgemm_emu refuses K beyond what keeps this below 2^31.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace qp {
+namespace {
+
+constexpr int EBM = 128, EBN = 64, EBK = 32, ESWB = 64;
+constexpr int ESTAGES = 4;
+constexpr int EA_PLANE = EBM * EBK * 2;                    // 8 KB
+constexpr int EB_PLANE = EBN * EBK * 2;                    // 4 KB
+constexpr int ESTAGE = 4 * (EA_PLANE + EB_PLANE);          // 48 KB
+constexpr int ESTAGING = 4 * 32 * 33 * 8;                  // epilogue transpose, 4 warps
+constexpr int ESMEM = ESTAGES * ESTAGE + ESTAGING + 1024;  // + alignment slack
+constexpr int ETHREADS = 192;
+constexpr int EGROUP_M = 16;
+static_assert(ESMEM <= 227 * 1024, "shared memory per CTA");
+
+constexpr uint32_t EIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EBN >> 3) << 17) |
+                            ((uint32_t)(EBM >> 4) << 24);
+constexpr uint32_t EIDESC_NEG_A = EIDESC | (1u << 13);
+
+struct EParams {
+  int M, N, K, S;
+  int Mt, Nt;
+  int kc[8];  // K chunk of each level (elements; multiple of EBK, or >= K); work items
+              // run level S-1 first, each level's chunks in K order
+  long long* C64;
+  long ld64, ps64;
+  int shift;  // int64 fixed point: value * 2^shift
+  int* err;
+};
+
+__global__ void __launch_bounds__(ETHREADS, 1)
+    k_qgemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_full[ESTAGES], bar_empty[ESTAGES], bar_acc_full, bar_acc_empty;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_group = EGROUP_M * P.Nt, group = blockIdx.x / per_group, local = blockIdx.x % per_group;
+  const int gm = min(EGROUP_M, P.Mt - group * EGROUP_M);
+  const int m0 = (group * EGROUP_M + local % gm) * EBM, n0 = (local / gm) * EBN;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < ESTAGES; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc_full), 1);
+    mbar_init(smem_u32(&bar_acc_empty), 4);  // one arrival per epilogue warp
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  int issued = 0;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int u = 0;
+      bool ok = true;
+      for (int d = P.S - 1; d >= 0 && ok; d--) {
+        for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d]) {
+          const int kb0 = k0 / EBK, kb1 = (min(P.K, k0 + P.kc[d]) + EBK - 1) / EBK;
+          for (int kb = kb0; kb < kb1 && ok; kb++) {
+            for (int s = 0; s <= d; s++, u++) {
+              const int st = u % ESTAGES;
+              if (u >= ESTAGES &&
+                  !mbar_wait(smem_u32(&bar_empty[st]), ((u / ESTAGES) - 1) & 1, &abort_flag, P.err, 11)) {
+                ok = false;
+                break;
+              }
+              const uint32_t fb = smem_u32(&bar_full[st]);
+              mbar_expect_tx(fb, ESTAGE);
+              uint8_t* sp = smem + (size_t)st * ESTAGE;
+              for (int c = 0; c < 4; c++)
+                tma_load_3d(smem_u32(sp + c * EA_PLANE), &tmA, kb * EBK, m0, s * 4 + c, fb);
+              for (int c = 0; c < 4; c++)
+                tma_load_3d(smem_u32(sp + 4 * EA_PLANE + c * EB_PLANE), &tmB, kb * EBK, n0, (d - s) * 4 + c, fb);
+              issued = u + 1;
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int u = 0, w = 0;
+      bool ok = true;
+      for (int d = P.S - 1; d >= 0 && ok; d--) {
+        for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
+          // the FP32 buffer is free once the epilogue has read chunk w - 1
+          if (w > 0 && !mbar_wait(smem_u32(&bar_acc_empty), (w - 1) & 1, &abort_flag, P.err, 12)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const int kb0 = k0 / EBK, kb1 = (min(P.K, k0 + P.kc[d]) + EBK - 1) / EBK;
+          bool first = true;
+          for (int kb = kb0; kb < kb1 && ok; kb++) {
+            for (int s = 0; s <= d; s++, u++) {
+              const int st = u % ESTAGES;
+              if (!mbar_wait(smem_u32(&bar_full[st]), (u / ESTAGES) & 1, &abort_flag, P.err, 13)) {
+                ok = false;
+                break;
+              }
+              fence_after();
+              uint8_t* sp = smem + (size_t)st * ESTAGE;
+              const uint32_t a_base = smem_u32(sp), b_base = smem_u32(sp + 4 * EA_PLANE);
+#pragma unroll
+              for (int kk = 0; kk < EBK / 16; kk++) {
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                  const uint64_t ad = smem_desc_sw<ESWB>(a_base + r * EA_PLANE + kk * 32);
+#pragma unroll
+                  for (int c = 0; c < 4; c++) {
+                    const int bp = r ^ c;
+                    const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
+                                     (r == 3 && (c == 0 || c == 1));
+                    const uint64_t bd = smem_desc_sw<ESWB>(b_base + bp * EB_PLANE + kk * 32);
+                    const uint32_t acc = (!first || kk > 0 || r > 0) ? 1u : 0u;
+                    mma_bf16(tmem + c * EBN, ad, bd, neg ? EIDESC_NEG_A : EIDESC, acc);
+                  }
+                }
+              }
+              first = false;
+              mma_commit(smem_u32(&bar_empty[st]));
+            }
+          }
+          if (ok) mma_commit(smem_u32(&bar_acc_full));
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: exact FP32 -> int32 per chunk, int64 per level ----------------
+    const int quarter = warp & 3;
+    const int row0 = m0 + quarter * 32;
+    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
+    long long* st64 = reinterpret_cast<long long*>(smem + ESTAGES * ESTAGE) + (warp - 2) * (32 * 33);
+    const int nrow = min(32, P.M - row0);
+    int w = 0;
+    bool ok = true;
+    for (int d = P.S - 1; d >= 0 && ok; d--) {
+      const float scale = ldexpf(1.0f, 7 * (d + 2));  // level unit -> integer (a power of two: exact)
+      const int sh = P.shift - 7 * (d + 2);
+      for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
+        int have = 1;
+        if (lane == 0) have = mbar_wait(smem_u32(&bar_acc_full), w & 1, &abort_flag, P.err, 14) ? 1 : 0;
+        have = __shfl_sync(0xffffffffu, have, 0);
+        if (!have) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const bool first = k0 == 0;
+#pragma unroll 1
+        for (int p = 0; p < 8; p++) {
+          uint32_t f[32], a[32];
+          tmem_ld32u(tb + p * 32, f);
+          if (!first) tmem_ld32u(tb + 256 + p * 32, a);
+          tmem_wait_ld();
+#pragma unroll
+          for (int t = 0; t < 32; t++) {
+            const int x = __float2int_rn(__uint_as_float(f[t]) * scale);
+            a[t] = first ? (uint32_t)x : (uint32_t)((int)a[t] + x);
+          }
+          tmem_st32u(tb + 256 + p * 32, a);
+        }
+        // every FP32 value of the chunk is in registers: release the buffer
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));
+        tmem_wait_st();
+        const bool last = k0 + P.kc[d] >= P.K;
+        if (!last) continue;
+        // level done: int64 += int32 * 2^sh (rounded shift when sh < 0)
+#pragma unroll 1
+        for (int p = 0; p < 8; p++) {
+          uint32_t a[32];
+          tmem_ld32u(tb + 256 + p * 32, a);
+          tmem_wait_ld();
+#pragma unroll
+          for (int t = 0; t < 32; t++) {
+            const long long x = (long long)(int)a[t];
+            st64[lane * 33 + t] = sh >= 0 ? (x << sh) : ((x + (1LL << (-sh - 1))) >> (-sh));
+          }
+          __syncwarp();
+          const int c = p >> 1, col = n0 + (p & 1) * 32 + lane;
+          if (col < P.N) {
+            long long* dst = P.C64 + c * P.ps64 + (long)row0 * P.ld64 + col;
+            rmw_rows64(dst, P.ld64, nrow, st64 + lane);
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && abort_flag) {
+    for (int u = (issued > ESTAGES ? issued - ESTAGES : 0); u < issued; u++)
+      (void)mbar_wait(smem_u32(&bar_full[u % ESTAGES]), (u / ESTAGES) & 1, &abort_flag, nullptr, 0);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+}  // namespace
+
+bool emu_fused_ok(int K, int S) {
+  if (S < 1 || S > 8 || K < 1) return false;
+  const double lvl0 = 4.0 * K * 16384.0, lvlhi = 4.0 * K * 4096.0 * (S + 2);
+  return lvl0 < 2147483648.0 && lvlhi < 2147483648.0;
+}
+
+cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaSuccess;
+  if (!a.A || !a.B || !a.A->a || !a.B->b || !a.C64 || !emu_fused_ok(a.K, a.S)) return cudaErrorInvalidValue;
+  if (a.A->levels < a.S || a.B->levels < a.S) return cudaErrorInvalidValue;
+  if ((a.A->lda % 8) || (a.A->psa % 8) || (a.B->ldb % 8) || (a.B->psb % 8)) return cudaErrorInvalidValue;
+  EParams P;
+  P.M = a.M;
+  P.N = a.N;
+  P.K = a.K;
+  P.S = a.S;
+  for (int d = 0; d < 8; d++) {
+    const int kc = d < a.S ? a.kc[d] : a.K;
+    if (kc < a.K && (kc <= 0 || kc % EBK)) return cudaErrorInvalidValue;
+    P.kc[d] = kc < a.K ? kc : a.K;
+  }
+  P.C64 = a.C64;
+  P.ld64 = a.ld64;
+  P.ps64 = a.ps64;
+  P.shift = a.shift;
+  P.err = a.err;
+  P.Mt = (a.M + EBM - 1) / EBM;
+  P.Nt = (a.N + EBN - 1) / EBN;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, EBM, EBK)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, EBN, EBK)) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_qgemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, ESMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_qgemm_emu<<<P.Mt * P.Nt, ETHREADS, ESMEM, st>>>(mA, mB, P);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace qp

@@ -89,6 +89,7 @@ cudaError_t launch_qgemm_f64(int M, int K, int N, const Planes<const double>& A,
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   k_qgemm_f64<<<grid, 256, 0, st>>>(M, K, N, A, B, C);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace qp {
 namespace {
@@ -50,109 +51,19 @@ struct Cfg {
   static constexpr int B_PLANE = BN * BK * 2;
   static constexpr int STAGE = 4 * (A_PLANE + B_PLANE);
   static constexpr int SMEM = STAGES * STAGE + 1024;
-  static constexpr unsigned long long LAYOUT = SWB == 128 ? 2ull : 4ull;  // descriptor swizzle code
-  static constexpr unsigned SBO = 8 * SWB;                               // bytes between 8-row groups
 };
 using CfgWide = Cfg<32, 64, 2>;
 using CfgDeep = Cfg<64, 128, 1>;
 static_assert(CfgWide::SMEM * 2 <= 227 * 1024, "two wide CTAs per SM");
 static_assert(CfgDeep::SMEM * 2 > 228 * 1024, "one deep CTA per SM");
 constexpr int THREADS = 192;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 static_assert(ACC_COLS == 256, "TMEM allocations must be powers of two (256 or 512 columns)");
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false if the abort flag is raised or WAIT_NS elapses (then
-// raises the flag and records `code` in *err).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err, int code) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtime();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (*abort_flag) return false;
-      if (gtime() - t0 > WAIT_NS) {
-        *abort_flag = 1;
-        if (err) atomicCAS(err, 0, code);
-        return false;
-      }
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major, swizzled rows of 2*BK bytes, 8-row groups SBO bytes apart.
-template <class C>
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(C::SBO >> 4) << 32) |
-         ((uint64_t)1 << 46) | (C::LAYOUT << 61);
-}
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int t = 0; t < 32; t++) v[t] = __uint_as_float(r[t]);
-}
 
 struct KParams {
   int M, N;
@@ -247,13 +158,13 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
         for (int kk = 0; kk < BK / 16; kk++) {
 #pragma unroll
           for (int r = 0; r < 4; r++) {
-            const uint64_t ad = smem_desc<C>(a_base + r * A_PLANE_BYTES + kk * 32);
+            const uint64_t ad = smem_desc_sw<C::SWB>(a_base + r * A_PLANE_BYTES + kk * 32);
 #pragma unroll
             for (int c = 0; c < 4; c++) {
               const int bp = r ^ c;
               const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
                                (r == 3 && (c == 0 || c == 1));
-              const uint64_t bd = smem_desc<C>(b_base + bp * B_PLANE_BYTES + kk * 32);
+              const uint64_t bd = smem_desc_sw<C::SWB>(b_base + bp * B_PLANE_BYTES + kk * 32);
               const uint32_t acc = (!fresh || kk > 0 || r > 0) ? 1u : 0u;
               mma_bf16(dacc + c * BN, ad, bd, neg ? IDESC_NEG_A : IDESC, acc);
             }
@@ -264,9 +175,14 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
       }
     }
   } else {
-    // ---------------- epilogue: TMEM -> FP32 global ----------------
+    // ---------------- epilogue: TMEM -> global ----------------
+    // Each warp owns 32 accumulator rows (its TMEM lane quarter).  A 32 x 32
+    // block read from TMEM (one row per thread) is transposed through shared
+    // memory -- the pipeline stages are idle once the last MMA has completed --
+    // so that every global access of the warp covers 32 consecutive columns
+    // of one row.
     const int quarter = warp & 3;
-    const int row = m0 + quarter * 32 + lane;
+    const int row0 = m0 + quarter * 32;
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
     int have = 1;
     if (nunits > 0) {
@@ -275,6 +191,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
       fence_after();
     }
     if (have) {
+      long long* st64 = reinterpret_cast<long long*>(smem) + (warp - 2) * (32 * 33);
+      float* st32 = reinterpret_cast<float*>(st64);
 #pragma unroll 1
       for (int c = 0; c < 4; c++) {
 #pragma unroll 1
@@ -287,25 +205,32 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
 #pragma unroll
             for (int t = 0; t < 32; t++) v[t] = v2[t] = 0.f;
           }
-          if (row < P.M && P.C64) {
-            long long* dst = P.C64 + c * P.ps64 + (long)row * P.ld64 + n0 + ch * 32;
-            const int ncol = min(32, P.N - (n0 + ch * 32));
+          const int col = n0 + ch * 32 + lane;
+          const int nrow = min(32, P.M - row0);
+          if (P.C64) {
             if (P.nacc == 2) {
-              for (int t = 0; t < ncol; t++) dst[t] += __float2ll_rn(v[t] * P.scale) + __float2ll_rn(v2[t] * P.scale);
-            } else {
-              for (int t = 0; t < ncol; t++) dst[t] += __float2ll_rn(v[t] * P.scale);
-            }
-          } else if (row < P.M) {
-            float* dst = P.C.p + c * P.C.ps + (long)row * P.C.ld + n0 + ch * 32;
-            const int ncol = min(32, P.N - (n0 + ch * 32));
-            if (ncol == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-              for (int t = 0; t < 32; t += 4)
-                *reinterpret_cast<float4*>(dst + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+              for (int t = 0; t < 32; t++)
+                st64[lane * 33 + t] = __float2ll_rn(v[t] * P.scale) + __float2ll_rn(v2[t] * P.scale);
             } else {
-              for (int t = 0; t < ncol; t++) dst[t] = v[t];
+#pragma unroll
+              for (int t = 0; t < 32; t++) st64[lane * 33 + t] = __float2ll_rn(v[t] * P.scale);
+            }
+            __syncwarp();
+            if (col < P.N) {
+              long long* dst = P.C64 + c * P.ps64 + (long)row0 * P.ld64 + col;
+              rmw_rows64(dst, P.ld64, nrow, st64 + lane);
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t < 32; t++) st32[lane * 33 + t] = v[t];
+            __syncwarp();
+            if (col < P.N) {
+              float* dst = P.C.p + c * P.C.ps + (long)row0 * P.C.ld + col;
+              store_rows32(dst, P.C.ld, nrow, st32 + lane);
             }
           }
+          __syncwarp();
         }
       }
     }
@@ -324,38 +249,6 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
   }
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
-// 3-D map over [planes][rows][K] BF16 with a box of (bk, box_rows, 1) and a 2*bk-byte swizzle.
-bool make_map(CUtensorMap* map, const bf16* base, int K, int rows, int planes, long ld, long ps, int box_rows,
-              int bk) {
-  EncodeTiledFn enc = get_encode();
-  if (!enc) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ps * 2};
-  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
 }
 
 template <class C>
@@ -377,6 +270,7 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
   P.Mt = (a.M + BM - 1) / BM;
   P.Nt = (a.N + BN - 1) / BN;
   k_qgemm_tc<C><<<P.Mt * P.Nt, THREADS, C::SMEM, st>>>(mA, mB, P);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

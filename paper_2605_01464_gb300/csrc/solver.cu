@@ -196,8 +196,9 @@ void timed(qpinv_ctx* c, int kind, double flops, double issued, double bytes, F&
     r.b = ev_get(c);
     ck(c, cudaEventRecord(r.a, c->st), "cudaEventRecord");
   }
+  const long long before = g_kernel_launches;
   ck(c, launch(), "kernel launch");
-  c->stats.kernel_launches++;
+  c->stats.kernel_launches += g_kernel_launches - before;
   if (kind == EV_TC) {
     c->stats.tc_gemm_launches++;
     c->stats.tc_gemm_flops += flops;
@@ -334,12 +335,13 @@ struct Solver {
     const int M = P.rows, K = P.cols, N = Q.cols;
     int* eP = (int*)buf(c, "emu.eP", sizeof(int) * (size_t)M + 64);
     int* eQ = (int*)buf(c, "emu.eQ", sizeof(int) * (size_t)N + 64);
+    int* eS = (int*)buf(c, "emu.eS", sizeof(int) * (size_t)COL_SCRATCH(N) + 64);
     if (dbl) {
-      timed(c, EV_EW, 0, 0, 32.0 * M * K, [&] { return launch_maxexp(dview(P), M, K, 0, eP, c->st); });
-      timed(c, EV_EW, 0, 0, 32.0 * K * N, [&] { return launch_maxexp(dview(Q), K, N, 1, eQ, c->st); });
+      timed(c, EV_EW, 0, 0, 32.0 * M * K, [&] { return launch_maxexp(dview(P), M, K, 0, eP, nullptr, c->st); });
+      timed(c, EV_EW, 0, 0, 32.0 * K * N, [&] { return launch_maxexp(dview(Q), K, N, 1, eQ, eS, c->st); });
     } else {
-      timed(c, EV_EW, 0, 0, 16.0 * M * K, [&] { return launch_maxexp_f32(fview(P), M, K, 0, eP, c->st); });
-      timed(c, EV_EW, 0, 0, 16.0 * K * N, [&] { return launch_maxexp_f32(fview(Q), K, N, 1, eQ, c->st); });
+      timed(c, EV_EW, 0, 0, 16.0 * M * K, [&] { return launch_maxexp_f32(fview(P), M, K, 0, eP, nullptr, c->st); });
+      timed(c, EV_EW, 0, 0, 16.0 * K * N, [&] { return launch_maxexp_f32(fview(Q), K, N, 1, eQ, eS, c->st); });
     }
     Split16 za, zb;
     za.levels = zb.levels = S;
@@ -385,6 +387,31 @@ struct Solver {
       const int lim = d == 0 ? 256 : 1024 / (d + 3);
       return lim >= 64 ? (lim / 64) * 64 : 64;
     };
+    if (emu_fused_ok(K, S)) {
+      // all levels and chunks in one launch, int32 level sums in TMEM
+      EmuGemmArgs g;
+      g.M = M;
+      g.N = N;
+      g.K = K;
+      g.A = &za;
+      g.B = &zb;
+      g.S = S;
+      for (int d = 0; d < S; d++) {
+        if (d > S - 3) {
+          g.kc[d] = K;
+        } else {
+          const int lim = d == 0 ? 256 : 1024 / (d + 3);
+          g.kc[d] = (lim / 32) * 32;
+        }
+      }
+      g.C64 = acc;
+      g.ld64 = N;
+      g.ps64 = (long)M * N;
+      g.shift = shift;
+      g.err = c->d_err;
+      timed(c, EV_TC, flops, flops * S * (S + 1) / 2, 0, [&] { return launch_qgemm_emu(g, c->st); });
+      return Acc{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
+    }
     for (int hi = S - 1; hi >= 0; hi -= 2) {
       const int lo = hi - 1;  // second level of the launch (-1: none)
       TcGemmArgs g;
@@ -1059,7 +1086,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     // ---- norms and alpha (Thm. 1) ----
     double* rs = (double*)buf(c, "rowsum", sizeof(double) * (size_t)(m + n) + 64);
     double* mx = (double*)buf(c, "maxes", sizeof(double) * 4);
-    timed(c, EV_EW, 0, 0, 64.0 * m * n, [&] { return launch_abs_sums(a, m, n, rs, rs + m, c->st); });
+    timed(c, EV_EW, 0, 0, 64.0 * m * n, [&] { return launch_abs_sums(a, m, n, rs, rs + m, (double*)buf(c, "colpart", sizeof(double) * (size_t)COL_SCRATCH(n) + 64), c->st); });
     timed(c, EV_EW, 0, 0, 8.0 * m, [&] { return launch_max(rs, m, mx, c->st); });
     timed(c, EV_EW, 0, 0, 8.0 * n, [&] { return launch_max(rs + m, n, mx + 1, c->st); });
     double hm[2];
@@ -1417,7 +1444,7 @@ int qpinv_alpha_features(qpinv_ctx* c, void* stream, int m, int n, const double*
     if (bad > 0.0) return fail(c, QPINV_E_NONFINITE, "A contains NaN or Inf");
     double* rs = (double*)buf(c, "rowsum", sizeof(double) * (size_t)(m + n) + 64);
     double* mx = (double*)buf(c, "maxes", sizeof(double) * 4);
-    ck(c, launch_abs_sums(av, m, n, rs, rs + m, c->st), "abs sums");
+    ck(c, launch_abs_sums(av, m, n, rs, rs + m, (double*)buf(c, "colpart", sizeof(double) * (size_t)COL_SCRATCH(n) + 64), c->st), "abs sums");
     ck(c, launch_max(rs, m, mx, c->st), "max");
     ck(c, launch_max(rs + m, n, mx + 1, c->st), "max");
     double hm[2];

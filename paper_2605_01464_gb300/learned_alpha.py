@@ -42,14 +42,38 @@ def sample_matrix(family, m, n, seed, device="cpu"):
     """(A planes (4, m, n), nonzero singular values descending)."""
     rng = np.random.default_rng(seed)
     if family == "dense":
+        import torch
         A = inputs.gaussian_quaternion(m, n, seed)
-        sv = np.linalg.svd(inputs.chi(A), compute_uv=False)[::2]
+        sv = torch.linalg.svdvals(torch.as_tensor(inputs.chi(A), device=device)).cpu().numpy()[::2]
         return A, sv
     k = min(m, n)
     r = k if family != "geometric" else int(rng.integers(max(1, k // 4), max(2, k // 2) + 1))
     sigma = _spectrum(family, r, rng) * 10.0 ** rng.uniform(-2, 2)
     U = inputs.orthonormal_columns(m, r, 2 * seed + 1, device)
     V = inputs.orthonormal_columns(n, r, 2 * seed + 2, device)
+    return inputs.with_spectrum(U, sigma, V, device), sigma
+
+
+def heldout_matrix(family, m, n, seed, device="cpu", umax=5.0):
+    """Full-rank held-out matrix (4, m, n) and its singular values: kappa =
+    10^u, u ~ U[1, umax]; sigma log-uniform random draws ("logspaced"),
+    geometric, or clustered around 2-4 centres; overall scale 10^U[-2, 2]."""
+    rng = np.random.default_rng(seed)
+    k = min(m, n)
+    u = rng.uniform(1.0, umax)
+    if family == "logspaced":
+        sigma = np.sort(10.0 ** -rng.uniform(0.0, u, size=k))[::-1]
+        sigma[0], sigma[-1] = 1.0, 10.0 ** -u
+    elif family == "geometric":
+        sigma = np.geomspace(1.0, 10.0 ** -u, k)
+    else:
+        centres = 10.0 ** -rng.uniform(0.0, u, size=rng.integers(2, 5))
+        centres[0], centres[-1] = 1.0, 10.0 ** -u
+        sigma = np.sort(centres[rng.integers(0, len(centres), size=k)] * np.exp(rng.normal(0.0, 0.05, size=k)))[::-1]
+        sigma[0] = max(sigma[0], 1.0)
+    sigma = sigma * 10.0 ** rng.uniform(-2, 2)
+    U = inputs.orthonormal_columns(m, k, 2 * seed + 1, device)
+    V = inputs.orthonormal_columns(n, k, 2 * seed + 2, device)
     return inputs.with_spectrum(U, sigma, V, device), sigma
 
 

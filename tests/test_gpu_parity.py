@@ -210,6 +210,16 @@ def test_qgemm_exact_slices_match_oracle(ctx, S, m, k, n):
     assert rel(C, oracle.matmul(A, B)) <= EMU_TOL[S], rel(C, oracle.matmul(A, B))
 
 
+@pytest.mark.parametrize("S,k", [(8, 13500), (4, 30000)])
+def test_qgemm_exact_slices_long_k(ctx, S, k):
+    """K beyond the fused kernel's int32 level sums (13107 for 8 slices,
+    21845 for 4): the chunked multi-launch path with int64 epilogues."""
+    A = I.gaussian_quaternion(40, k, 9)
+    B = I.gaussian_quaternion(k, 24, 10)
+    C = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=S).cpu().numpy()
+    assert rel(C, oracle.matmul(A, B)) <= EMU_TOL[S] * 4, rel(C, oracle.matmul(A, B))
+
+
 def test_qgemm_exact_slices_wide_dynamic_range(ctx):
     """Rows and columns spanning 2^-40 .. 2^40: per-row/column power-of-two
     scaling keeps every entry FP64-accurate relative to its row/column scale."""

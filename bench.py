@@ -172,15 +172,16 @@ def kernel_qgemm(args, torch, qpinv):
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / args.steps
     st = ctx.stats()
-    launches = max(st["tc_gemm_launches"], 1)
-    ms = st["tc_gemm_ms"] / launches
-    print(json.dumps({"kernel": "k_qgemm_tc", "n": n, "precision": prec, "split": args.split,
-                      "launches_per_product": launches / args.steps, "ms_per_launch": ms,
-                      "gemm_ms_per_product": st["tc_gemm_ms"] / args.steps,
-                      "all_kernels_ms_per_product": (st["tc_gemm_ms"] + st["ew_ms"]) / args.steps,
+    key = "emu" if st["emu_gemm_launches"] else "tc"
+    launches = max(st["%s_gemm_launches" % key], 1)
+    gms = st["%s_gemm_ms" % key]
+    print(json.dumps({"kernel": "k_qgemm_emu" if key == "emu" else "k_qgemm_tc", "n": n, "precision": prec,
+                      "split": args.split, "launches_per_product": launches / args.steps, "ms_per_launch": gms / launches,
+                      "gemm_ms_per_product": gms / args.steps,
+                      "all_kernels_ms_per_product": (gms + st["ew_ms"]) / args.steps,
                       "wall_ms_per_product": wall * 1e3,
-                      "tflops_algorithmic": st["tc_gemm_flops"] / st["tc_gemm_ms"] / 1e9,
-                      "tflops_issued": st["tc_gemm_flops_issued"] / st["tc_gemm_ms"] / 1e9}))
+                      "tflops_algorithmic": st["%s_gemm_flops" % key] / gms / 1e9,
+                      "tflops_issued": st["%s_gemm_flops_issued" % key] / gms / 1e9}))
     return 0
 
 
@@ -247,12 +248,8 @@ def bench_rankdef(args, torch, qpinv):
             st = ctx.stats()
             out[method] = {"ms_per_solve": statistics.mean(times), "iters": info["iters"], "status": info["status"],
                            "E_rel": info["E_rel"], "gemms": info["gemms"], "gpu_launches": st["kernel_launches"],
-                           "tc_gemm_ms": st["tc_gemm_ms"], "tc_gemm_flops_issued": st["tc_gemm_flops_issued"],
-                           "tc_gemm_flops": st["tc_gemm_flops"]}
+                           "roofline": kernel_rooflines(st)}
     q = out["qhpi19"]
-    bf16_burst, bf16_sust, hbm, src = peaks()
-    issued = q["tc_gemm_flops_issued"] / q["tc_gemm_ms"] / 1e9
-    alg = q["tc_gemm_flops"] / q["tc_gemm_ms"] / 1e9
     print(json.dumps({
         "metric": "rank-deficient pinv solves/s to rel. Penrose res (FP64 floor)", "value": 1e3 / q["ms_per_solve"],
         "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q["ms_per_solve"],
@@ -262,11 +259,7 @@ def bench_rankdef(args, torch, qpinv):
                                "orthonormal factors from Gaussian quaternion matrices (seeds 4, 5); left residual "
                                "(4096 side); EMU precision; rel. tol %g with plateau stop" % args.tol,
                    "l2": "inputs exceed L2"},
-        "roofline": {"bound": "tensor", "achieved": alg, "achieved_issued": issued, "peak": bf16_sust,
-                     "unit": "TFLOP/s", "frac": alg / bf16_sust, "frac_issued": issued / bf16_sust, "traffic": None,
-                     "kernel": "k_qgemm_tc (exact-slice passes)",
-                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src},
-        "result": out, "clocks": clk.summary()}), flush=True)
+        "roofline": q["roofline"][0], "result": out, "clocks": clk.summary()}), flush=True)
     return 0
 
 
@@ -327,6 +320,37 @@ def bench_learned(args, torch, qpinv):
                                 "mixed_learned_E1_rel": infol["E_rel"][0], "speedup": ms64 / msl},
         "clocks": clk.summary()}), flush=True)
     return 0
+
+
+# DRAM bytes (read + write) per launch from ncu captures of the current
+# kernels, scaled to the 2048 x 2048 x 2048 product of the dense workload;
+# None when the kernel changed after its capture.  Sources: profiles/.
+TRAFFIC_PER_LAUNCH = {"k_qgemm_emu": None, "k_qgemm_tc": None}
+
+
+def kernel_rooflines(st):
+    """Roofline entries of the two tensor-core GEMM kernels, dominant (by
+    time) first: achieved = algorithmic flops per launch (32 per quaternion
+    multiply-add) / average CUDA-event duration of a launch; issued = tensor
+    flops actually executed (slice or split passes)."""
+    bf16_burst, bf16_sust, hbm, src = peaks()
+    out = []
+    for key, name, desc in (("emu", "k_qgemm_emu", "fused exact-slice FP64-accurate quaternion GEMM"),
+                            ("tc", "k_qgemm_tc", "BF16-split quaternion GEMM")):
+        n = st["%s_gemm_launches" % key]
+        t = st["%s_gemm_ms" % key]
+        if n == 0 or t <= 0:
+            continue
+        ms = t / n
+        alg = st["%s_gemm_flops" % key] / n / (ms * 1e-3) / 1e12
+        iss = st["%s_gemm_flops_issued" % key] / n / (ms * 1e-3) / 1e12
+        out.append({"bound": "tensor", "achieved": alg, "peak": bf16_sust, "unit": "TFLOP/s",
+                    "frac": alg / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH[name],
+                    "kernel": "%s (%s)" % (name, desc), "launches": n, "ms_per_launch": ms, "total_ms": t,
+                    "achieved_issued": iss, "frac_issued": iss / bf16_sust,
+                    "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src})
+    out.sort(key=lambda r: -r["total_ms"])
+    return out or [None]
 
 
 def workload_config(args):
@@ -447,25 +471,18 @@ def main():
         if dist:
             dist.destroy_process_group()
         return 0
-    bf16_burst, bf16_sust, hbm, src = peaks()
-    tc_launch_ms = st["tc_gemm_ms"] / max(st["tc_gemm_launches"], 1)
-    tc_alg = st["tc_gemm_flops"] / max(st["tc_gemm_launches"], 1)
-    tc_iss = st["tc_gemm_flops_issued"] / max(st["tc_gemm_launches"], 1)
-    achieved = tc_alg / (tc_launch_ms * 1e-3) / 1e12 if tc_launch_ms > 0 else 0.0
-    issued = tc_iss / (tc_launch_ms * 1e-3) / 1e12 if tc_launch_ms > 0 else 0.0
+    roofs = kernel_rooflines(st)
     last = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16-split/f32-acc + exact-slice f64", "data": "synthetic",
         "config": workload_config(args),
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                     "frac": achieved / bf16_sust, "traffic": None,
-                     "kernel": "k_qgemm_tc (tcgen05 quaternion GEMM)",
-                     "achieved_issued": issued, "frac_issued": issued / bf16_sust,
-                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src},
+        "roofline": roofs[0],
+        "roofline_other": roofs[1:],
         "gpu_launches": st["kernel_launches"],
-        "kernel_time_ms": {"tc_gemm": st["tc_gemm_ms"], "f64_gemm": st["f64_gemm_ms"], "elementwise": st["ew_ms"]},
+        "kernel_time_ms": {"emu_gemm": st["emu_gemm_ms"], "tc_gemm": st["tc_gemm_ms"], "f64_gemm": st["f64_gemm_ms"],
+                           "elementwise": st["ew_ms"]},
         "result": {"iters": last["iters"], "tc_iters": last["tc_iters"], "polish_iters": last["polish_iters"],
                    "status": last["status"], "E_rel": last["E_rel"], "alpha": last["alpha"]},
         "clocks": clk.summary(),

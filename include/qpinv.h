@@ -135,7 +135,8 @@ typedef struct {
 
 typedef struct {
   long long kernel_launches;  /* every kernel of this library launched since the last reset */
-  long long tc_gemm_launches; /* tcgen05 quaternion GEMM launches */
+  long long tc_gemm_launches; /* tcgen05 quaternion GEMM launches (BF16 splits; chunked
+                                 exact-slice launches for K beyond the fused kernel's range) */
   double tc_gemm_ms;          /* their summed duration (CUDA events on the launch stream; profile=1) */
   double tc_gemm_flops;       /* algorithmic real flops: 32 per quaternion multiply-add */
   double tc_gemm_flops_issued;/* tensor-core flops issued (split products count each pass) */
@@ -145,6 +146,10 @@ typedef struct {
   long long ew_launches;      /* fused elementwise / reduction kernels */
   double ew_ms;
   double ew_bytes;            /* algorithmic HBM bytes of those kernels */
+  long long emu_gemm_launches;/* fused exact-slice (FP64-accurate) tensor-core GEMM launches */
+  double emu_gemm_ms;
+  double emu_gemm_flops;      /* algorithmic: 32 per quaternion multiply-add */
+  double emu_gemm_flops_issued;/* tensor-core flops issued: S(S+1)/2 slice-pair passes */
 } qpinv_stats;
 
 typedef struct qpinv_ctx qpinv_ctx;

@@ -53,7 +53,7 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-enum { EV_TC = 0, EV_F64 = 1, EV_EW = 2 };
+enum { EV_TC = 0, EV_F64 = 1, EV_EW = 2, EV_EMU = 3 };
 enum { PM_TC = 0, PM_F64 = 1, PM_EMU = 2 };
 
 struct EvRec {
@@ -206,6 +206,10 @@ void timed(qpinv_ctx* c, int kind, double flops, double issued, double bytes, F&
   } else if (kind == EV_F64) {
     c->stats.f64_gemm_launches++;
     c->stats.f64_gemm_flops += flops;
+  } else if (kind == EV_EMU) {
+    c->stats.emu_gemm_launches++;
+    c->stats.emu_gemm_flops += flops;
+    c->stats.emu_gemm_flops_issued += issued;
   } else {
     c->stats.ew_launches++;
     c->stats.ew_bytes += bytes;
@@ -223,6 +227,7 @@ void flush_events(qpinv_ctx* c) {
     cudaEventElapsedTime(&ms, r.a, r.b);
     if (r.kind == EV_TC) c->stats.tc_gemm_ms += ms;
     else if (r.kind == EV_F64) c->stats.f64_gemm_ms += ms;
+    else if (r.kind == EV_EMU) c->stats.emu_gemm_ms += ms;
     else c->stats.ew_ms += ms;
     c->pool.push_back(r.a);
     c->pool.push_back(r.b);
@@ -409,7 +414,7 @@ struct Solver {
       g.ps64 = (long)M * N;
       g.shift = shift;
       g.err = c->d_err;
-      timed(c, EV_TC, flops, flops * S * (S + 1) / 2, 0, [&] { return launch_qgemm_emu(g, c->st); });
+      timed(c, EV_EMU, flops, flops * S * (S + 1) / 2, 0, [&] { return launch_qgemm_emu(g, c->st); });
       return Acc{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
     }
     for (int hi = S - 1; hi >= 0; hi -= 2) {

@@ -42,10 +42,13 @@ def sample_matrix(family, m, n, seed, device="cpu"):
     """(A planes (4, m, n), nonzero singular values descending)."""
     rng = np.random.default_rng(seed)
     if family == "dense":
-        import torch
+        # singular values from the Hermitian eigenvalues of chi(A)^H chi(A) on
+        # the smaller side (each quaternion singular value appears twice)
         A = inputs.gaussian_quaternion(m, n, seed)
-        sv = torch.linalg.svdvals(torch.as_tensor(inputs.chi(A), device=device)).cpu().numpy()[::2]
-        return A, sv
+        C = inputs.chi(A)
+        G = C.conj().T @ C if n <= m else C @ C.conj().T
+        ev = np.sort(np.linalg.eigvalsh(G))[::-1][::2]
+        return A, np.sqrt(np.maximum(ev, 0.0))
     k = min(m, n)
     r = k if family != "geometric" else int(rng.integers(max(1, k // 4), max(2, k // 2) + 1))
     sigma = _spectrum(family, r, rng) * 10.0 ** rng.uniform(-2, 2)

@@ -51,7 +51,9 @@ class qpinv_stats(ctypes.Structure):
                 ("tc_gemm_ms", ctypes.c_double), ("tc_gemm_flops", ctypes.c_double),
                 ("tc_gemm_flops_issued", ctypes.c_double), ("f64_gemm_launches", ctypes.c_longlong),
                 ("f64_gemm_ms", ctypes.c_double), ("f64_gemm_flops", ctypes.c_double),
-                ("ew_launches", ctypes.c_longlong), ("ew_ms", ctypes.c_double), ("ew_bytes", ctypes.c_double)]
+                ("ew_launches", ctypes.c_longlong), ("ew_ms", ctypes.c_double), ("ew_bytes", ctypes.c_double),
+                ("emu_gemm_launches", ctypes.c_longlong), ("emu_gemm_ms", ctypes.c_double),
+                ("emu_gemm_flops", ctypes.c_double), ("emu_gemm_flops_issued", ctypes.c_double)]
 
 
 PTR4 = ctypes.c_void_p * 4

@@ -185,30 +185,49 @@ def kernel_qgemm(args, torch, qpinv):
     return 0
 
 
-def bench_batched(args, torch, qpinv):
+def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     """4096 pure-quaternion blocks (m, n ~ U[16, 256], rank ~ U[4, min(m, n)])
-    solved by qpinv_solve_batched in one persistent launch per step."""
+    solved by qpinv_solve_batched in one persistent launch per step.  With N
+    ranks each GPU solves its own 4096 blocks (weak scaling; no collective on
+    the data path, only the timing reduction)."""
     from paper_2605_01464_gb300 import inputs
-    mats = inputs.pure_quaternion_batch(4096, seed=3)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mats = inputs.pure_quaternion_batch(4096, seed=3 + 1000 * rank)
     As = [torch.from_numpy(a).cuda() for a in mats]
     Xs = [torch.empty((4, a.shape[2], a.shape[1]), dtype=torch.float64, device="cuda") for a in As]
-    ctx = qpinv.Context(0)
+    ctx = qpinv.Context(local)
     for _ in range(args.warmup):
         ctx.solve_batched(As, args.method, tol=args.tol, max_iter=200, Xs=Xs)
     torch.cuda.synchronize()
+    tune_ms = ctx.stats()["batched_tune_ms"]
+    ctx.reset_stats()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         for _ in range(args.steps):
             _, infos = ctx.solve_batched(As, args.method, tol=args.tol, max_iter=200, Xs=Xs)
         torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt, solves = reduce_timing(time.perf_counter() - t0, 4096 * args.steps, dist, "cuda")
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     e1 = [i["E_rel"][0] for i in infos]
     its = [i["iters"] for i in infos]
-    print(json.dumps({"metric": "batched pinv solves/s", "value": 4096 * args.steps / dt, "unit": "solves/s",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-                      "higher_is_better": True, "dtype": "df32 (double-FP32)", "data": "synthetic",
+    st = ctx.stats()
+    print(json.dumps({"metric": "batched pinv solves/s", "value": solves / dt, "unit": "solves/s",
+                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "dtype": "df32 (double-FP32)", "data": "synthetic",
                       "config": {"workload": "4096 pure-quaternion blocks, m, n ~ U[16,256], rank ~ U[4,min(m,n)], "
-                                             "seed 3, %s, rel. tol %g, one persistent launch" % (args.method, args.tol)},
+                                             "seed 3, %s, rel. tol %g, one persistent kernel per step replayed as a "
+                                             "captured CUDA graph, autotuned CTA GEMM tile" % (args.method, args.tol),
+                                 "tile": ["16x16", "32x32", "64x32", "32x64", "64x64"][st["batched_tile"]],
+                                 "autotune_ms": tune_ms, "graph_replays": st["batched_graph_replays"]},
+                      "gpu_launches": st["kernel_launches"],
                       "result": {"max_E1_rel": max(e1), "median_iters": sorted(its)[len(its) // 2],
                                  "statuses": sorted(set(i["status"] for i in infos))},
                       "clocks": clk.summary()}), flush=True)
@@ -322,10 +341,13 @@ def bench_learned(args, torch, qpinv):
     return 0
 
 
-# DRAM bytes (read + write) per launch from ncu captures of the current
-# kernels, scaled to the 2048 x 2048 x 2048 product of the dense workload;
-# None when the kernel changed after its capture.  Sources: profiles/.
-TRAFFIC_PER_LAUNCH = {"k_qgemm_emu": None, "k_qgemm_tc": None}
+# DRAM bytes (read + write) per issued tensor flop from one ncu capture of
+# each current kernel on a 2048^3 product (profiles/k_qgemm_emu_2048_slices8.md:
+# 8.11 GB for 36 passes; profiles/k_qgemm_tc_2048_split2.md: 245 MB for 3
+# pairs); a launch's traffic is estimated as this times its issued flops.
+# None once the kernel changes after its capture.
+TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 8.111e9 / (36 * 32 * 2048.0 ** 3),
+                           "k_qgemm_tc": 245.07e6 / (3 * 32 * 2048.0 ** 3)}
 
 
 def kernel_rooflines(st):
@@ -344,13 +366,29 @@ def kernel_rooflines(st):
         ms = t / n
         alg = st["%s_gemm_flops" % key] / n / (ms * 1e-3) / 1e12
         iss = st["%s_gemm_flops_issued" % key] / n / (ms * 1e-3) / 1e12
+        tpf = TRAFFIC_PER_ISSUED_FLOP[name]
+        traffic = tpf * st["%s_gemm_flops_issued" % key] / n if tpf else None
         out.append({"bound": "tensor", "achieved": alg, "peak": bf16_sust, "unit": "TFLOP/s",
-                    "frac": alg / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH[name],
+                    "frac": alg / bf16_sust, "traffic": traffic, "traffic_unit": "bytes per launch (estimate)",
                     "kernel": "%s (%s)" % (name, desc), "launches": n, "ms_per_launch": ms, "total_ms": t,
                     "achieved_issued": iss, "frac_issued": iss / bf16_sust,
                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src})
     out.sort(key=lambda r: -r["total_ms"])
     return out or [None]
+
+
+def reduce_timing(seconds, units, dist, device):
+    """Replicas on N GPUs: the job's time is the slowest rank's, its work the
+    sum of all ranks' units.  Returns (max seconds, total units); a no-op
+    without a process group."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def workload_config(args):
@@ -406,7 +444,7 @@ def main():
     if args.kernel == "qgemm":
         return kernel_qgemm(args, torch, qpinv)
     if args.workload == "batched":
-        return bench_batched(args, torch, qpinv)
+        return bench_batched(args, torch, qpinv, world, rank, local)
     if args.workload == "rankdef":
         return bench_rankdef(args, torch, qpinv)
     if args.workload == "learned":
@@ -438,11 +476,9 @@ def main():
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    sec, units = reduce_timing(ms / 1e3, args.steps, dist, "cuda")
+    ms = sec * 1e3
+    value = units / sec
 
     # end to end: host (pinned) A in, host X out, through the same C-ABI call
     e2e = None
@@ -458,13 +494,9 @@ def main():
         for _ in range(args.steps):
             _, info_h = ctx.solve(Ah, args.method, tol=args.tol, max_iter=200, X=Xh, stream=stream)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te, units = reduce_timing(time.perf_counter() - t0, args.steps, dist, "cuda")
         nbytes = 4 * args.n * args.n * 8
-        e2e = {"value": world * args.steps / te, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": units / te, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + 8 * 4 * 3}
 
     if rank != 0:

@@ -56,7 +56,10 @@ extern "C" {
 
 /* ---- solver outcome (qpinv_result.status) ----------------------------- */
 #define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
-#define QPINV_PLATEAU 1       /* relative step stopped decreasing after falling below 1e-3 (rounding floor); X is the iterate before that step */
+#define QPINV_PLATEAU 1       /* rounding floor reached: the relative step stopped decreasing after
+                                 falling below 1e-3 (X is the iterate before that step), or, after
+                                 MIXED's polish iterations, it is below 2^-53 sqrt(||A||_1 ||A||_inf)
+                                 ||X||_F */
 #define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
 #define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
 #define QPINV_NONFINITE_INPUT 4 /* qpinv_solve_batched: this A holds NaN/Inf; its X is left untouched */
@@ -99,9 +102,16 @@ enum { QPINV_STOP_PAPER_ABS = 0,  /* ||X_{j+1} - X_j||_F < tol (Algorithms 1-3) 
 typedef struct {
   int precision;     /* QPINV_PREC_FP64, _MIXED, _TC or _EMU; default MIXED */
   int split_level;   /* BF16 terms of the tensor-core R-products (polynomials in R): 1 = bf16,
-                        2 = bf16x3, 3 = bf16x6; 0 = automatic (2).  X-products use 3 terms
-                        or exact slices (see QPINV_PREC_MIXED) */
-  int polish_iters;  /* MIXED: iterations with an FP64 residual at the end (default 2) */
+                        2 = bf16x3, 3 = bf16x6; 0 = automatic (1 term while the relative step
+                        exceeds 0.5, then 2).  X-products use 2 terms (square MIXED) or 3, then
+                        exact slices once ||A|| ||X|| > 1e3 (4 for the residual; 3 for the update
+                        X t of square MIXED solves) */
+  int polish_iters;  /* MIXED: iterations with an FP64 residual at the end (default 2); the
+                        tensor-core phase ends when the step stalls, when the residual predicted
+                        after the polish iterations is negligible (||R_j||_F, or the spectral
+                        radius of R_j when the relative step suggests it), or when drel < 1e-6.
+                        Rectangular A is projected onto the pseudoinverse's row / column space
+                        after the first polish iteration */
   int alpha_mode;    /* QPINV_ALPHA_*, default SAFE */
   double alpha_user; /* used with QPINV_ALPHA_USER */
   int qrapid_N;      /* QRAPID step parameter N >= 0 (default 5) */
@@ -111,6 +121,9 @@ typedef struct {
   int stop_rule;     /* QPINV_STOP_*, default REL_PLATEAU */
   int penrose;       /* 1: compute E1..E4 in FP64 after the solve (default 1) */
   int profile;       /* 1: time every kernel launch with CUDA events (qpinv_get_stats) */
+  int batched_tile;  /* qpinv_solve_batched CTA GEMM tile: -1 = autotune (default; each batch
+                        signature is timed once per context on a sample of its matrices),
+                        0 = 16x16, 1 = 32x32, 2 = 64x32, 3 = 32x64, 4 = 64x64 */
 } qpinv_options;
 
 typedef struct {
@@ -150,6 +163,9 @@ typedef struct {
   double emu_gemm_ms;
   double emu_gemm_flops;      /* algorithmic: 32 per quaternion multiply-add */
   double emu_gemm_flops_issued;/* tensor-core flops issued: S(S+1)/2 slice-pair passes */
+  long long batched_tile;     /* CTA GEMM tile of the last batched call (see batched_tile) */
+  double batched_tune_ms;     /* time spent autotuning batched tiles */
+  long long batched_graph_replays; /* batched calls served by replaying a captured CUDA graph */
 } qpinv_stats;
 
 typedef struct qpinv_ctx qpinv_ctx;

@@ -57,26 +57,47 @@ __global__ void k_gemv(Planes<const float> A, int m, int n, const float* x, floa
     for (int c = 0; c < 4; c++) y[4 * row + c] = s[c];
 }
 
-// z = A^H y  (z_j = sum_i conj(A_ij) y_i) -- one thread per column.
-__global__ void k_gemv_h(Planes<const float> A, int m, int n, const float* y, float* z) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// z = A^H y  (z_j = sum_i conj(A_ij) y_i): blocks of 32 columns x one row
+// chunk (a warp reads 32 consecutive entries of a row) write partial sums per
+// (chunk, column); the finishing kernel adds the chunks in order.
+constexpr int GV_COLS = 32, GV_ROWS = 8, GV_MAX_CHUNKS = 64;
+
+__global__ void k_gemv_h_part(Planes<const float> A, int m, int n, const float* y, int chunk_rows, float* part) {
+  __shared__ float sh[GV_ROWS][4][GV_COLS];
+  const int j = blockIdx.x * GV_COLS + threadIdx.x;
+  const int r0 = blockIdx.y * chunk_rows, r1 = min(m, r0 + chunk_rows);
   float s[4] = {0, 0, 0, 0};
-  for (int i = 0; i < m; i++) {
-    float a[4], b[4];
-    for (int c = 0; c < 4; c++) {
-      a[c] = A.p[c * A.ps + (long)i * A.ld + j];
-      b[c] = y[4 * i + c];
+  if (j < n)
+    for (int i = r0 + threadIdx.y; i < r1; i += GV_ROWS) {
+      float a[4], b[4];
+      for (int c = 0; c < 4; c++) {
+        a[c] = A.p[c * A.ps + (long)i * A.ld + j];
+        b[c] = y[4 * i + c];
+      }
+      a[1] = -a[1];
+      a[2] = -a[2];
+      a[3] = -a[3];
+      s[0] += a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+      s[1] += a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+      s[2] += a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+      s[3] += a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
     }
-    a[1] = -a[1];
-    a[2] = -a[2];
-    a[3] = -a[3];
-    s[0] += a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
-    s[1] += a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
-    s[2] += a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
-    s[3] += a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
-  }
-  for (int c = 0; c < 4; c++) z[4 * j + c] = s[c];
+  for (int c = 0; c < 4; c++) sh[threadIdx.y][c][threadIdx.x] = s[c];
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n)
+    for (int c = 0; c < 4; c++) {
+      float t = s[c];
+      for (int r = 1; r < GV_ROWS; r++) t += sh[r][c][threadIdx.x];
+      part[((long)blockIdx.y * n + j) * 4 + c] = t;
+    }
+}
+
+__global__ void k_gemv_h_finish(const float* part, int chunks, int n, float* z) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // t = 4 j + c
+  if (t >= 4 * n) return;
+  float s = 0.f;
+  for (int ch = 0; ch < chunks; ch++) s += part[(long)ch * 4 * n + t];
+  z[t] = s;
 }
 
 // out[0] = sum a_k b_k over 4n floats (real part of the quaternion inner product).
@@ -94,14 +115,32 @@ __global__ void k_dot(const float* a, const float* b, int len, double* out) {
   }
 }
 
-// w = w - alpha q - beta qprev
-__global__ void k_lanczos_axpy(float* w, const float* q, const float* qprev, float alpha, float beta, int len) {
+// Lanczos scalars stay on the device: alpha_j = dal[0], beta_j^2 = dbe2[0]
+// (none for j = 0).  w = w - alpha_j q - beta_j qprev.
+__global__ void k_lanczos_axpy(float* w, const float* q, const float* qprev, const double* dal,
+                               const double* dbe2, int len) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < len) w[t] = w[t] - alpha * q[t] - beta * qprev[t];
+  if (t >= len) return;
+  const float a = (float)dal[0];
+  const float b = dbe2 ? (float)sqrt(fmax(dbe2[0], 0.0)) : 0.f;
+  w[t] = w[t] - a * q[t] - b * qprev[t];
 }
-__global__ void k_scale_copy(const float* w, float* q, float inv, int len) {
+// qprev = q, q = w / beta (beta^2 = dbe2[0]); a vanishing beta leaves q = 0,
+// and the host truncates the run there.
+__global__ void k_lanczos_next(const float* w, float* q, float* qprev, const double* dbe2, int len) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < len) q[t] = w[t] * inv;
+  if (t >= len) return;
+  const double b2 = dbe2[0];
+  const float inv = b2 > 1e-60 ? (float)(1.0 / sqrt(b2)) : 0.f;
+  qprev[t] = q[t];
+  q[t] = w[t] * inv;
+}
+// v = y / sqrt(d2[0]) (0 when the norm vanishes)
+__global__ void k_normalize(const float* y, float* v, const double* d2, int len) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  const double b2 = d2[0];
+  v[t] = b2 > 1e-60 ? y[t] * (float)(1.0 / sqrt(b2)) : 0.f;
 }
 
 // ------------------------------------------------------------ MLP kernels
@@ -256,7 +295,11 @@ int alpha_nweights() { return NWEIGHTS; }
 int alpha_ntrain() { return NTRAIN; }
 
 // Features of A (FP32 planes on the device; fro2, n1, ninf precomputed).  The
-// scratch buffers hold 4 * (2 max(m, n) + 3 n) floats and 2 doubles.
+// scratch buffers hold alpha_feature_scratch_floats(m, n) floats and 2 * 16
+// doubles; `pin` is pinned host memory for 2 * 16 doubles.  One host
+// synchronisation per call.
+int alpha_feature_scratch_floats(int m, int n) { return 4 * (3 * n + m) + 4 * GV_MAX_CHUNKS * n + 64; }
+
 cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fro2, double norm1, double norminf,
                            float* scratch, double* dscratch, double* pin, cudaStream_t st, float* feat,
                            double* theta1_out) {
@@ -265,6 +308,9 @@ cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fr
   float* qprev = q + 4 * n;
   float* w = qprev + 4 * n;
   float* y = w + 4 * n;
+  float* part = y + 4 * m;
+  double* dal = dscratch;
+  double* dbe2 = dscratch + K;
   std::vector<float> hq(4 * (size_t)n);
   double nrm = 0.0;
   for (int i = 0; i < 4 * n; i++) {
@@ -275,34 +321,34 @@ cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fr
   cudaError_t e;
   if ((e = cudaMemcpyAsync(q, hq.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(qprev, 0, sizeof(float) * 4 * n, st)) != cudaSuccess) return e;
-  std::vector<double> al, be;
-  double beta = 0.0;
   const int len = 4 * n, tb = 256, gb = (len + tb - 1) / tb;
-  int steps = std::min(K, n);
+  const int steps = std::min(K, n);
+  const int colblocks = (n + GV_COLS - 1) / GV_COLS;
+  int ch = (608 + colblocks - 1) / colblocks;
+  ch = std::max(1, std::min({ch, (m + 63) / 64, GV_MAX_CHUNKS}));
+  const int chunk_rows = (m + ch - 1) / ch;
   for (int j = 0; j < steps; j++) {
     k_gemv<<<(m * 32 + 255) / 256, 256, 0, st>>>(A, m, n, q, y);
-    k_gemv_h<<<(n + 127) / 128, 128, 0, st>>>(A, m, n, y, w);
-    k_dot<<<1, 256, 0, st>>>(q, w, len, dscratch);
-    if ((e = cudaMemcpyAsync(pin, dscratch, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    const double a = pin[0];
-    al.push_back(a);
-    k_lanczos_axpy<<<gb, tb, 0, st>>>(w, q, qprev, (float)a, (float)beta, len);
-    k_dot<<<1, 256, 0, st>>>(w, w, len, dscratch);
-    if ((e = cudaMemcpyAsync(pin, dscratch, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    beta = std::sqrt(std::max(pin[0], 0.0));
-    if (j + 1 < steps) {
-      if (!(beta > 1e-30 * std::max(1.0, std::fabs(a)))) {
-        steps = j + 1;
-        break;
-      }
-      be.push_back(beta);
-      if ((e = cudaMemcpyAsync(qprev, q, sizeof(float) * len, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
-      k_scale_copy<<<gb, tb, 0, st>>>(w, q, (float)(1.0 / beta), len);
-    }
+    k_gemv_h_part<<<dim3(colblocks, ch), dim3(GV_COLS, GV_ROWS), 0, st>>>(A, m, n, y, chunk_rows, part);
+    k_gemv_h_finish<<<gb, tb, 0, st>>>(part, ch, n, w);
+    k_dot<<<1, 256, 0, st>>>(q, w, len, dal + j);
+    k_lanczos_axpy<<<gb, tb, 0, st>>>(w, q, qprev, dal + j, j > 0 ? dbe2 + j - 1 : nullptr, len);
+    k_dot<<<1, 256, 0, st>>>(w, w, len, dbe2 + j);
+    if (j + 1 < steps) k_lanczos_next<<<gb, tb, 0, st>>>(w, q, qprev, dbe2 + j, len);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(pin, dscratch, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  std::vector<double> al, be;
+  for (int j = 0; j < steps; j++) {
+    al.push_back(pin[j]);
+    if (j + 1 < steps) {
+      const double beta = std::sqrt(std::max(pin[K + j], 0.0));
+      if (!(beta > 1e-30 * std::max(1.0, std::fabs(pin[j])))) break;  // invariant subspace found
+      be.push_back(beta);
+    }
+  }
   const int k = (int)al.size();
   std::vector<double> T((size_t)k * k, 0.0);
   for (int i = 0; i < k; i++) {
@@ -323,6 +369,42 @@ cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fr
   feat[7] = lg(t1 / (norm1 * norminf));
   for (int i = 0; i < 16; i++) feat[8 + i] = i < k ? (float)std::max(th[i] / t1, 0.0) : 0.f;
   for (int i = 0; i < 8; i++) feat[24 + i] = i + 1 < k ? lg(std::max(th[i + 1] / t1, 1e-30)) : lg(1e-30);
+  return cudaSuccess;
+}
+
+// Spectral radius of a square quaternion matrix M (FP32 planes, s x s) by
+// power iteration v <- M v / ||M v|| from the features' start vector: the
+// geometric mean of the last four norms ||M v_k|| (a complex-conjugate
+// dominant pair makes single norms oscillate).  Scratch: 8 s floats and
+// `steps` doubles; one host synchronisation.
+cudaError_t power_radius(const Planes<const float>& M, int s, int steps, float* scratch, double* dscratch,
+                         double* pin, cudaStream_t st, double* rho) {
+  float* v = scratch;
+  float* y = v + 4 * s;
+  std::vector<float> hv(4 * (size_t)s);
+  double nrm = 0.0;
+  for (int i = 0; i < 4 * s; i++) {
+    hv[i] = (float)(1.0 / (1.0 + 0.37 * (i % 7) + 0.11 * i));
+    nrm += (double)hv[i] * hv[i];
+  }
+  for (int i = 0; i < 4 * s; i++) hv[i] = (float)(hv[i] / std::sqrt(nrm));
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(v, hv.data(), sizeof(float) * 4 * s, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  const int len = 4 * s, tb = 256, gb = (len + tb - 1) / tb;
+  for (int k = 0; k < steps; k++) {
+    k_gemv<<<(s * 32 + 255) / 256, 256, 0, st>>>(M, s, s, v, y);
+    k_dot<<<1, 256, 0, st>>>(y, y, len, dscratch + k);
+    k_normalize<<<gb, tb, 0, st>>>(y, v, dscratch + k, len);
+  }
+  g_kernel_launches += 3 * steps;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(pin, dscratch, sizeof(double) * steps, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  const int last = std::min(4, steps);
+  double lg = 0.0;
+  for (int k = steps - last; k < steps; k++) lg += 0.5 * std::log(std::max(pin[k], 1e-300));
+  *rho = std::exp(lg / last);
   return cudaSuccess;
 }
 

@@ -31,7 +31,12 @@ namespace {
 constexpr int MAXD = 256;
 constexpr int NBUF = 22;  // workspace matrices per slot
 constexpr int TPB = 256;
-constexpr int BM = 32, BN = 32, BK = 8;  // CTA GEMM tile (quaternion entries)
+// CTA GEMM: a 16 x 16 thread grid, each thread RM x RN outputs 16 apart, so
+// the CTA tile is 16 RM x 16 RN quaternion entries; BK = K step.  The tile
+// shape is a template parameter of the kernel, chosen per batch by the
+// autotuner in qpinv_solve_batched (or fixed by the caller).
+constexpr int BK = 8;
+constexpr int TMAX = 64;  // largest tile side
 
 // ------------------------------------------------------------ df arithmetic
 struct dfv {
@@ -60,6 +65,21 @@ __device__ __forceinline__ dfv df_fma(dfv a, dfv b, dfv c) {
   return df_quick(s, t + e + c.lo);
 }
 __device__ __forceinline__ dfv df_mul(dfv a, dfv b) { return df_fma(a, b, dfv{0.f, 0.f}); }
+// Lazy accumulation for dot products (compensated summation in the manner of
+// Ogita, Rump and Oishi's Dot2, with df inputs): acc.hi is the running sum,
+// acc.lo collects every rounding and low-order term unnormalised; df_norm
+// turns it back into a df value at the end of the dot product.
+__device__ __forceinline__ void df_dot_add(dfv& acc, dfv a, dfv b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = acc.hi + p;
+  const float v = s - acc.hi;
+  acc.lo += ((acc.hi - (s - v)) + (p - v)) + e;
+  acc.hi = s;
+}
+__device__ __forceinline__ dfv df_norm(dfv a) { return df_quick(a.hi, a.lo); }
 __device__ __forceinline__ dfv df_from(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};
@@ -114,8 +134,8 @@ struct BatchParams {
 };
 
 struct Shared {
-  dfv a[4][BK][BM];
-  dfv b[4][BK][BN];
+  dfv a[4][BK][TMAX];
+  dfv b[4][BK][TMAX];
   double red[TPB / 32][2];
   double bc[4];
 };
@@ -133,17 +153,19 @@ __device__ double block_sum(double v, Shared& sh, int slot) {
 
 // C (P.rows x Q.cols) = epilogue(P Q), quaternion; every thread of the CTA calls it.
 // Returns (in every thread) the two norms of Epi::ref, if requested.
+template <int RM, int RN>
 __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Shared& sh, double* norms) {
+  constexpr int BM = 16 * RM, BN = 16 * RN;
   const int M = P.rows, K = P.cols, N = Q.cols;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float nd = 0.f, nx = 0.f;
   for (int i0 = 0; i0 < M; i0 += BM) {
     for (int j0 = 0; j0 < N; j0 += BN) {
-      dfv acc[2][2][4];
+      dfv acc[RM][RN][4];
 #pragma unroll
-      for (int a = 0; a < 2; a++)
+      for (int a = 0; a < RM; a++)
 #pragma unroll
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < RN; b++)
 #pragma unroll
           for (int c = 0; c < 4; c++) acc[a][b][c] = dfv{0.f, 0.f};
       for (int k0 = 0; k0 < K; k0 += BK) {
@@ -162,51 +184,51 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
         __syncthreads();
         const int kmax = min(BK, K - k0);
         for (int kk = 0; kk < kmax; kk++) {
-          dfv a[2][4], b[2][4];
+          dfv a[RM][4], b[RN][4];
 #pragma unroll
-          for (int r = 0; r < 2; r++)
+          for (int r = 0; r < RM; r++)
 #pragma unroll
             for (int c = 0; c < 4; c++) a[r][c] = sh.a[c][kk][ty + 16 * r];
 #pragma unroll
-          for (int q = 0; q < 2; q++)
+          for (int q = 0; q < RN; q++)
 #pragma unroll
             for (int c = 0; c < 4; c++) b[q][c] = sh.b[c][kk][tx + 16 * q];
 #pragma unroll
-          for (int r = 0; r < 2; r++)
+          for (int r = 0; r < RM; r++)
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
+            for (int q = 0; q < RN; q++) {
               dfv* o = acc[r][q];
               const dfv* x = a[r];
               const dfv* y = b[q];
               // Hamilton product x y (Sec. 2), accumulated per component
-              o[0] = df_fma(x[0], y[0], o[0]);
-              o[0] = df_fma(df_neg(x[1]), y[1], o[0]);
-              o[0] = df_fma(df_neg(x[2]), y[2], o[0]);
-              o[0] = df_fma(df_neg(x[3]), y[3], o[0]);
-              o[1] = df_fma(x[0], y[1], o[1]);
-              o[1] = df_fma(x[1], y[0], o[1]);
-              o[1] = df_fma(x[2], y[3], o[1]);
-              o[1] = df_fma(df_neg(x[3]), y[2], o[1]);
-              o[2] = df_fma(x[0], y[2], o[2]);
-              o[2] = df_fma(df_neg(x[1]), y[3], o[2]);
-              o[2] = df_fma(x[2], y[0], o[2]);
-              o[2] = df_fma(x[3], y[1], o[2]);
-              o[3] = df_fma(x[0], y[3], o[3]);
-              o[3] = df_fma(x[1], y[2], o[3]);
-              o[3] = df_fma(df_neg(x[2]), y[1], o[3]);
-              o[3] = df_fma(x[3], y[0], o[3]);
+              df_dot_add(o[0], x[0], y[0]);
+              df_dot_add(o[0], df_neg(x[1]), y[1]);
+              df_dot_add(o[0], df_neg(x[2]), y[2]);
+              df_dot_add(o[0], df_neg(x[3]), y[3]);
+              df_dot_add(o[1], x[0], y[1]);
+              df_dot_add(o[1], x[1], y[0]);
+              df_dot_add(o[1], x[2], y[3]);
+              df_dot_add(o[1], df_neg(x[3]), y[2]);
+              df_dot_add(o[2], x[0], y[2]);
+              df_dot_add(o[2], df_neg(x[1]), y[3]);
+              df_dot_add(o[2], x[2], y[0]);
+              df_dot_add(o[2], x[3], y[1]);
+              df_dot_add(o[3], x[0], y[3]);
+              df_dot_add(o[3], x[1], y[2]);
+              df_dot_add(o[3], df_neg(x[2]), y[1]);
+              df_dot_add(o[3], x[3], y[0]);
             }
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int r = 0; r < 2; r++)
+      for (int r = 0; r < RM; r++)
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
+        for (int q = 0; q < RN; q++) {
           const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * q;
           if (gi < M && gj < N) {
             for (int c = 0; c < 4; c++) {
-              dfv v = df_mul(e.ca, acc[r][q][c]);
+              dfv v = df_mul(e.ca, df_norm(acc[r][q][c]));
               for (int t = 0; t < 3; t++)
                 if (e.aux[t]) v = df_fma(e.ct[t], e.aux[t]->at(c, gi, gj), v);
               if (c == 0 && gi == gj) v = df_add(v, e.diag);
@@ -288,6 +310,7 @@ struct Ctx {
 enum { B_A = 0, B_X0, B_X1, B_R, B_R2, B_R4, B_S, B_FA, B_FB, B_U, B_V, B_W, B_G, B_T, B_Z0, B_Z1, B_Z2, B_E, B_P1,
        B_P2, B_P3, B_P4 };
 
+template <int RM, int RN>
 struct Solve {
   Ctx& c;
   DM A, X[2];
@@ -298,7 +321,7 @@ struct Solve {
   __device__ void gemm(const DM& P, const DM& Q, const DM& C, const Epi& e) {
     c.gemms++;
     double nrm[2] = {0, 0};
-    cta_gemm(P, Q, C, e, *c.sh, nrm);
+    cta_gemm<RM, RN>(P, Q, C, e, *c.sh, nrm);
     if (e.ref) {
       nd = nrm[0];
       nx = nrm[1];
@@ -441,7 +464,8 @@ struct Solve {
   }
 };
 
-__global__ void __launch_bounds__(TPB, 2) k_batched(BatchParams P) {
+template <int RM, int RN, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_batched(BatchParams P) {
   __shared__ Shared sh;
   __shared__ int next;
   Ctx c;
@@ -461,7 +485,7 @@ __global__ void __launch_bounds__(TPB, 2) k_batched(BatchParams P) {
     c.left = it.m > it.n;
     c.s = c.left ? it.n : it.m;
     c.gemms = 0;
-    Solve S(c);
+    Solve<RM, RN> S(c);
     S.A = c.buf(B_A, it.m, it.n);
     S.X[0] = c.buf(B_X0, it.n, it.m);
     S.X[1] = c.buf(B_X1, it.n, it.m);
@@ -605,21 +629,63 @@ __global__ void __launch_bounds__(TPB, 2) k_batched(BatchParams P) {
   }
 }
 
+template <int RM, int RN, int MINB>
+cudaError_t launch_tile(int slots, const BatchParams& P, cudaStream_t st) {
+  k_batched<RM, RN, MINB><<<slots, TPB, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched(int tile, int slots, const BatchParams& P, cudaStream_t st) {
+  switch (tile) {
+    case 0: return launch_tile<1, 1, 2>(slots, P, st);
+    case 1: return launch_tile<2, 2, 2>(slots, P, st);
+    case 2: return launch_tile<4, 2, 1>(slots, P, st);
+    case 3: return launch_tile<2, 4, 1>(slots, P, st);
+    case 4: return launch_tile<4, 4, 1>(slots, P, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int RM, int RN, int MINB>
+int occupancy() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<RM, RN, MINB>, TPB, 0) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
+unsigned long long mix(unsigned long long h, unsigned long long v) {
+  h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
 }  // namespace
 
-// Host entry used by qpinv_solve_batched (solver.cu).
-struct BatchedPlan {
-  std::vector<BatchItem> items;
-  std::vector<int> order;
-};
+const char* batched_tile_name(int tile) {
+  static const char* names[BATCH_TILES] = {"16x16", "32x32", "64x32", "32x64", "64x64"};
+  return tile >= 0 && tile < BATCH_TILES ? names[tile] : "?";
+}
 
+int batched_slots_per_sm(int tile) {
+  switch (tile) {
+    case 0: return occupancy<1, 1, 2>();
+    case 1: return occupancy<2, 2, 2>();
+    case 2: return occupancy<4, 2, 1>();
+    case 3: return occupancy<2, 4, 1>();
+    case 4: return occupancy<4, 4, 1>();
+    default: return 1;
+  }
+}
+
+// One batched call: host descriptors (largest cost first) into pinned
+// staging, then upload + counter reset + persistent kernel + result download
+// on `st` -- or, with `graph`, on the graph's own stream as one replayed CUDA
+// graph (captured again whenever the launch shape changes).
 cudaError_t run_batched(int batch, const int* m, const int* n, const double* const* A, const long* lda,
                         double* const* X, const long* ldx, int method, double tol, int max_iter, int qrapid_N,
-                        int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, void* ws,
-                        size_t ws_bytes, int slots, void* dev_items, void* dev_order, void* dev_results,
-                        int* dev_counter, std::vector<BatchResultHost>& out, cudaStream_t st) {
-  std::vector<BatchItem> items(batch);
-  std::vector<int> order(batch);
+                        int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, const BatchRun& r,
+                        BatchGraph* graph, std::vector<BatchResultHost>& out, cudaStream_t st) {
+  BatchItem* items = static_cast<BatchItem*>(r.host_items);
+  int* order = static_cast<int*>(r.host_order);
   std::vector<double> cost(batch);
   for (int b = 0; b < batch; b++) {
     BatchItem& it = items[b];
@@ -631,25 +697,18 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
     it.ldx = ldx[b];
     it.m = m[b];
     it.n = n[b];
-    const double s = std::min(m[b], n[b]), l = std::max(m[b], n[b]);
-    cost[b] = s * s * l;
+    const double sm = std::min(m[b], n[b]), l = std::max(m[b], n[b]);
+    cost[b] = sm * sm * l;
     order[b] = b;
   }
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(dev_items, items.data(), sizeof(BatchItem) * batch, cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaMemcpyAsync(dev_order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemsetAsync(dev_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+  std::stable_sort(order, order + batch, [&](int x, int y) { return cost[x] > cost[y]; });
   BatchParams P;
-  P.items = (const BatchItem*)dev_items;
-  P.order = (const int*)dev_order;
+  P.items = (const BatchItem*)r.dev_items;
+  P.order = (const int*)r.dev_order;
   P.count = batch;
-  P.counter = dev_counter;
-  P.results = (BatchResult*)dev_results;
-  P.ws = (dfv*)ws;
+  P.counter = r.dev_counter;
+  P.results = (BatchResult*)r.dev_results;
+  P.ws = (dfv*)r.ws;
   P.slot_elems = (long)NBUF * 4 * MAXD * MAXD;
   P.method = method;
   P.qrapid_N = qrapid_N;
@@ -659,14 +718,79 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
   P.tol = tol;
   P.alpha_user = alpha_user;
   for (int t = 0; t < 12; t++) P.k[t] = hpi19_k[t];
-  (void)ws_bytes;
-  k_batched<<<slots, TPB, 0, st>>>(P);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  std::vector<BatchResult> res(batch);
-  if ((e = cudaMemcpyAsync(res.data(), dev_results, sizeof(BatchResult) * batch, cudaMemcpyDeviceToHost, st)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(r.dev_items, r.host_items, sizeof(BatchItem) * batch, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(r.dev_order, r.host_order, sizeof(int) * batch, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(r.dev_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = launch_batched(r.tile, r.slots, P, s)) != cudaSuccess) return e;
+    ++g_kernel_launches;
+    return cudaMemcpyAsync(r.host_results, r.dev_results, sizeof(BatchResult) * batch, cudaMemcpyDeviceToHost, s);
+  };
+  cudaError_t e;
+  if (!graph) {
+    if ((e = enqueue(st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  } else {
+    // the launch shape: everything the captured nodes bake in
+    unsigned long long key = 1469598103934665603ull;
+    const unsigned long long parts[] = {(unsigned long long)batch, (unsigned long long)r.tile,
+                                        (unsigned long long)r.slots, (unsigned long long)(uintptr_t)r.ws,
+                                        (unsigned long long)(uintptr_t)r.dev_items,
+                                        (unsigned long long)(uintptr_t)r.host_items,
+                                        (unsigned long long)(uintptr_t)r.host_results,
+                                        (unsigned long long)method, (unsigned long long)max_iter,
+                                        (unsigned long long)qrapid_N, (unsigned long long)stop_rule,
+                                        (unsigned long long)alpha_mode};
+    for (unsigned long long v : parts) key = mix(key, v);
+    unsigned long long tb, ab;
+    memcpy(&tb, &tol, 8);
+    memcpy(&ab, &alpha_user, 8);
+    key = mix(mix(key, tb), ab);
+    if (!graph->exec || graph->key != key) {
+      if (graph->exec) {
+        cudaGraphExecDestroy(graph->exec);
+        graph->exec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      if ((e = cudaStreamBeginCapture(graph->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+      const long long launches_before = g_kernel_launches;
+      const cudaError_t eq = enqueue(graph->stream);
+      g_kernel_launches = launches_before;  // counted when the graph runs
+      e = cudaStreamEndCapture(graph->stream, &g);
+      if (eq != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return eq;
+      }
+      if (e != cudaSuccess) return e;
+      e = cudaGraphInstantiate(&graph->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        graph->exec = nullptr;
+        return e;
+      }
+      graph->key = key;
+      graph->replays = 0;
+    }
+    // order the replay after the caller's stream
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(graph->stream, ev, 0);
+    e = cudaGraphLaunch(graph->exec, graph->stream);
+    if (e == cudaSuccess) {
+      ++g_kernel_launches;
+      graph->replays++;
+      e = cudaStreamSynchronize(graph->stream);
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return e;
+  }
+  const BatchResult* res = static_cast<const BatchResult*>(r.host_results);
   out.resize(batch);
   for (int b = 0; b < batch; b++) {
     BatchResultHost& h = out[b];
@@ -689,10 +813,5 @@ size_t batched_slot_bytes() { return sizeof(float) * 2 * (size_t)NBUF * 4 * MAXD
 size_t batched_item_bytes() { return sizeof(BatchItem); }
 size_t batched_result_bytes() { return sizeof(BatchResult); }
 int batched_max_dim() { return MAXD; }
-int batched_slots_per_sm() {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, TPB, 0) != cudaSuccess) return 1;
-  return nb > 0 ? nb : 1;
-}
 
 }  // namespace qp

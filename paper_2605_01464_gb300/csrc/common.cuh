@@ -163,15 +163,37 @@ struct BatchResultHost {
 }  // namespace qp
 #include <vector>
 namespace qp {
+// CTA GEMM tile shapes of the batched kernel (quaternion entries):
+// 0: 16x16, 1: 32x32, 2: 64x32, 3: 32x64, 4: 64x64.
+constexpr int BATCH_TILES = 5;
+const char* batched_tile_name(int tile);
+// Device and pinned host buffers of one batched call (owned by the context).
+struct BatchRun {
+  int tile = 1, slots = 0;
+  void* ws = nullptr;  // slots * batched_slot_bytes()
+  void *dev_items = nullptr, *dev_order = nullptr, *dev_results = nullptr;
+  int* dev_counter = nullptr;
+  void *host_items = nullptr, *host_order = nullptr, *host_results = nullptr;  // pinned
+};
+// A captured CUDA graph of the call (upload, counter reset, the persistent
+// kernel, result download), replayed while the launch shape is unchanged.
+struct BatchGraph {
+  cudaStream_t stream = nullptr;  // capture / replay stream (non-blocking)
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long key = 0;
+  int replays = 0;
+};
 cudaError_t run_batched(int batch, const int* m, const int* n, const double* const* A, const long* lda,
                         double* const* X, const long* ldx, int method, double tol, int max_iter, int qrapid_N,
-                        int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, void* ws,
-                        size_t ws_bytes, int slots, void* dev_items, void* dev_order, void* dev_results,
-                        int* dev_counter, std::vector<BatchResultHost>& out, cudaStream_t st);
+                        int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, const BatchRun& r,
+                        BatchGraph* graph, std::vector<BatchResultHost>& out, cudaStream_t st);
 size_t batched_slot_bytes();
 // Learned alpha (alpha.cu).
 int alpha_nweights();
 int alpha_ntrain();
+int alpha_feature_scratch_floats(int m, int n);
+cudaError_t power_radius(const Planes<const float>& M, int s, int steps, float* scratch, double* dscratch,
+                         double* pin, cudaStream_t st, double* rho);
 cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fro2, double norm1, double norminf,
                            float* scratch, double* dscratch, double* pin, cudaStream_t st, float* feat,
                            double* theta1_out);
@@ -184,6 +206,6 @@ cudaError_t alpha_adam(float* dW, const float* dG, float* dM1, float* dM2, int t
 size_t batched_item_bytes();
 size_t batched_result_bytes();
 int batched_max_dim();
-int batched_slots_per_sm();
+int batched_slots_per_sm(int tile);
 
 }  // namespace qp

@@ -78,6 +78,11 @@ struct qpinv_ctx {
   cudaStream_t st = nullptr;
   bool trace = false;
   std::vector<float> alpha_w;  // learned-alpha network (empty: untrained)
+  // batched solves: pinned staging, the replayed CUDA graph, tuned tiles
+  void* bh_buf[3] = {nullptr, nullptr, nullptr};  // items, order, results (pinned)
+  size_t bh_cap[3] = {0, 0, 0};
+  qp::BatchGraph bgraph;
+  std::map<unsigned long long, int> tile_of;  // batch signature -> tuned tile
 };
 
 namespace {
@@ -267,6 +272,7 @@ struct Solver {
   int xmode = PM_TC;      // mode of the X-products this iteration
   int rmode = -1;         // mode of the R-products (-1: PM_F64 if L == 0, else PM_TC)
   int xS = 8;             // exact slices of X-products in PM_EMU mode
+  int xSu = 3;            // ... of the update product X t while the masters are FP32
   long long gemms = 0;
   QMat A, X[2];
   int cur = 0;
@@ -513,7 +519,9 @@ struct Solver {
     o.diag = diag;
     return o;
   }
-  void run(CombineArgs& a, bool with_partials = false) {
+  // with_partials: block partials of ||out - aux0||^2, ||out||^2 and the
+  // non-finite count, reduced into red_slot[0..2] of the "red" buffer.
+  void run(CombineArgs& a, bool with_partials = false, int red_slot = 0) {
     int blocks = ((a.cols + 31) / 32) * ((a.rows + 31) / 32);
     if (with_partials) {
       if (blocks > partial_cap) {
@@ -535,7 +543,8 @@ struct Solver {
     timed(c, EV_EW, 0, 0, bytes, [&] { return launch_combine(a, c->st, nullptr); });
     if (with_partials) {
       double* red = (double*)buf(c, "red", sizeof(double) * 8);
-      timed(c, EV_EW, 0, 0, 24.0 * blocks, [&] { return launch_reduce_partials(partials, blocks, 3, red, c->st); });
+      timed(c, EV_EW, 0, 0, 24.0 * blocks,
+            [&] { return launch_reduce_partials(partials, blocks, 3, red + red_slot, c->st); });
     }
   }
 
@@ -549,19 +558,24 @@ struct Solver {
   // Apply a side polynomial T (s x s) to Y (n x m): right Y*T, left T*Y.
   Acc apply(const QMat& Y, const QMat& T) {
     Lcur = Lx;
-    return left ? prod(T, Y, xmode) : prod(Y, T, xmode);
+    const int save = xS;
+    if (xmode == PM_EMU && !dbl) xS = xSu;
+    Acc r = left ? prod(T, Y, xmode) : prod(Y, T, xmode);
+    xS = save;
+    return r;
   }
   const char* tform() const { return left ? "fa" : "fb"; }
   QMat sq(const char* name, bool a, bool b) { return mat(c, name, s, s, MST_F | MST_D, a, b); }
   QMat big(const char* name) { return mat(c, name, n, m, MST_F | MST_D, true, true); }
 
   // R = I - (residual product of Y).
-  QMat residual(const QMat& Y, const char* name, const char* forms) {
+  // norm: also reduce ||R||_F^2 into red[4] (the iteration's own residual).
+  QMat residual(const QMat& Y, const char* name, const char* forms, bool norm = false) {
     Acc acc = res_prod(Y);
     QMat R = sq(name, strchr(forms, 'a') != nullptr, strchr(forms, 'b') != nullptr);
     CombineArgs a = base_args(s, s, &acc);
     out(a, R, forms, -1.0, 1.0);
-    run(a);
+    run(a, norm, 4);
     return R;
   }
 
@@ -578,13 +592,13 @@ struct Solver {
 
   // ---------------- one iteration of each method ----------------
   void step_ns() {
-    QMat R = residual(X[cur], "R", tform());
+    QMat R = residual(X[cur], "R", tform(), true);
     Acc acc = apply(X[cur], R);
     update(X[cur], acc);
   }
 
   void step_qsai(double b1, double b2) {
-    QMat R = residual(X[cur], "R", "fab");
+    QMat R = residual(X[cur], "R", "fab", true);
     Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", true, true);
     {
@@ -631,7 +645,7 @@ struct Solver {
   void step_qhpi19(const double* k) {
     // k: a1 a2 a3 b1 b2 c1 c2 d1 d2 d3 e1 e2
     const double c1 = k[5], c2 = k[6], d1 = k[7], d2 = k[8], d3 = k[9], e1 = k[10], e2 = k[11];
-    QMat R = residual(X[cur], "R", "fab");
+    QMat R = residual(X[cur], "R", "fab", true);
     Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", true, true), S = sq("S", true, false);
     {
@@ -708,7 +722,7 @@ struct Solver {
   }
 
   void step_qrapid(int N) {
-    QMat R = residual(X[cur], "R", "fab");
+    QMat R = residual(X[cur], "R", "fab", true);
     Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", false, true);
     {
@@ -920,10 +934,23 @@ int fail(qpinv_ctx* c, int code, const std::string& msg) {
 // Learned-alpha features of an m x n matrix whose FP32 master is A.f.
 void features_of(qpinv_ctx* c, const QMat& A, double fro2, double n1, double ninf, float* feat, double* theta1) {
   const int m = A.rows, n = A.cols;
-  float* sc = (float*)buf(c, "alpha.lanczos", sizeof(float) * 4 * (3 * (size_t)n + m) + 256);
-  double* ds = (double*)buf(c, "alpha.dot", sizeof(double) * 4);
+  float* sc = (float*)buf(c, "alpha.lanczos", sizeof(float) * (size_t)alpha_feature_scratch_floats(m, n) + 256);
+  double* ds = (double*)buf(c, "alpha.dot", sizeof(double) * 32);
+  const int steps = n < 16 ? n : 16;
   ck(c, alpha_features(fview(A), m, n, fro2, n1, ninf, sc, ds, c->h_pin, c->st, feat, theta1), "alpha features");
-  c->stats.kernel_launches += 16 * 6;
+  c->stats.kernel_launches += 7 * steps - 1;
+}
+
+// Spectral radius of a square FP32 matrix by 24 power-iteration steps.
+double spec_radius_est(qpinv_ctx* c, const QMat& M) {
+  const int steps = 24;
+  float* sc = (float*)buf(c, "rho.v", sizeof(float) * 8 * (size_t)M.rows + 256);
+  double* ds = (double*)buf(c, "rho.d", sizeof(double) * steps);
+  double rho = 0.0;
+  const long long before = g_kernel_launches;
+  ck(c, power_radius(fview(M), M.rows, steps, sc, ds, c->h_pin, c->st, &rho), "spectral radius estimate");
+  c->stats.kernel_launches += g_kernel_launches - before;
+  return rho;
 }
 
 // Network prediction y = log(alpha * theta_1) for one feature vector.
@@ -962,6 +989,7 @@ void qpinv_default_options(qpinv_options* o) {
   o->stop_rule = QPINV_STOP_REL_PLATEAU;
   o->penrose = 1;
   o->profile = 0;
+  o->batched_tile = -1;
 }
 
 static int check_opts(const qpinv_options* o) {
@@ -972,6 +1000,7 @@ static int check_opts(const qpinv_options* o) {
   if (o->alpha_mode == QPINV_ALPHA_USER && !(o->alpha_user > 0.0 && std::isfinite(o->alpha_user))) return 0;
   if (o->qrapid_N < 0 || o->qrapid_N > 30) return 0;
   if (o->side < 0 || o->side > 2 || o->stop_rule < 0 || o->stop_rule > 1) return 0;
+  if (o->batched_tile < -1 || o->batched_tile >= qp::BATCH_TILES) return 0;
   return 1;
 }
 
@@ -1019,6 +1048,10 @@ void qpinv_free(qpinv_ctx* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->d_err) cudaFree(c->d_err);
   if (c->h_pin) cudaFreeHost(c->h_pin);
+  for (void* p : c->bh_buf)
+    if (p) cudaFreeHost(p);
+  if (c->bgraph.exec) cudaGraphExecDestroy(c->bgraph.exec);
+  if (c->bgraph.stream) cudaStreamDestroy(c->bgraph.stream);
   delete c;
 }
 
@@ -1177,7 +1210,15 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       S.dbl = false;
       S.L = 3;
       S.Lr = Lr;
-      S.Lx = 3;
+      // X-products on 2-term splits for square MIXED solves: at K in the
+      // thousands the tensor cores' FP32 accumulation error (about 3e-5
+      // relative) already exceeds what a third term would add, and the polish
+      // iterations remove the rest.  TC precision keeps 3 terms (its output is
+      // the tensor-core iterate), and so does rectangular A, whose
+      // out-of-space component starts at the level of the FP32 phase.
+      const bool square_mixed = o.precision == QPINV_PREC_MIXED && m == n;
+      S.Lx = square_mixed ? 2 : 3;
+      S.xSu = square_mixed ? 3 : 4;
       S.xmode = PM_TC;
       ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
       ck(c, launch_f64_to_f32(dview(S.X[0]), n, m, S.X[0].f, c->st), "X0 to fp32");
@@ -1200,6 +1241,12 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
           S.xmode = PM_TC;
         }
       }
+      // R-products on single BF16 terms while the residual still has
+      // unresolved directions (relative step > 0.5): the rounding they leave in
+      // t puts resolved directions back at a residual of about 1e-2, which the
+      // next step's power of R removes; 2-term splits after (automatic
+      // split_level only).
+      if (!polish && !emu && o.split_level == 0) S.Lr = prev_rel > 0.5 ? 1 : Lr;
       switch (method) {
         case QPINV_NS: S.step_ns(); break;
         case QPINV_QSAI: S.step_qsai((1.0 + std::sqrt(5.0)) / 2.0, (1.0 - std::sqrt(5.0)) / 2.0); break;
@@ -1207,12 +1254,13 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         default: S.step_qhpi19(hpi19_k); break;
       }
       if (!fp64) check_kernel_error(c);
-      double h[3];
-      read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 3, h);
+      double h[8];
+      read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 6, h);
+      const double rnorm = std::sqrt(h[4]);  // ||R_j||_F of this step's residual
       const double d = std::sqrt(h[0]), nx = std::sqrt(h[1]);
       if (c->trace)
-        fprintf(stderr, "qpinv it %d %s xmode %d xS %d delta %.3e |X| %.3e rel %.3e\n", j,
-                polish ? "polish" : "tc", S.xmode, S.xS, d, nx, nx > 0 ? d / nx : d);
+        fprintf(stderr, "qpinv it %d %s xmode %d xS %d Lr %d delta %.3e |X| %.3e rel %.3e |R|_F %.3e\n", j,
+                polish ? "polish" : "tc", S.xmode, S.xS, S.Lr, d, nx, nx > 0 ? d / nx : d, rnorm);
       if (h[2] > 0.0 || !std::isfinite(d) || !std::isfinite(nx)) {
         res.status = QPINV_DIVERGED;
         break;  // X[cur] is the last finite iterate
@@ -1242,13 +1290,45 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         xnorm = nx;
       }
       if (stop) break;
+      // Rectangular A: the low-precision phase leaves X with a component
+      // outside the pseudoinverse's row (or column) space, of relative size
+      // delta ~ 1e-7, that no residual sees.  After the first polish iteration
+      // (range part at the FP64 level) an FP64-accurate projection takes it to
+      // second order, delta^2 kappa; the range error the projection itself
+      // adds (about kappa times the FP64 level) is what the following polish
+      // iterations correct.
+      if (o.precision == QPINV_PREC_MIXED && m != n && polish && polish_done == 1 && o.polish_iters >= 2)
+        S.range_projection();
       if (o.precision == QPINV_PREC_MIXED && !polish) {
         // Leave the tensor-core phase once the step stops shrinking fast or
         // is below the FP32 level: switch to FP64 masters and FP64-accurate
         // X-products for the polish iterations.
         const bool stalled = prev_rel < INFINITY && drel > 0.05 * prev_rel && drel < 1e-2;
-        if (stalled || drel < 1e-6 || (o.stop_rule == QPINV_STOP_PAPER_ABS && d < tol)) {
+        // In exact arithmetic the residual after this step is R_j^p (p the
+        // method's order) and after the polish iterations R_j^(p^(1+P)), P =
+        // polish_iters.  Leave the tensor-core phase once that is negligible:
+        // ||R_j||_F < lim bounds it directly; when the relative step (a cheap
+        // proxy for ||R_j||) already predicts it, a power-iteration estimate
+        // of the spectral radius of R_j (2 % margin) confirms it, which
+        // catches residuals that still have unresolved directions (the step
+        // dips between clusters of singular values, while R ~ 1 there).  The
+        // 2-norm is not used for that: R is not normal, and after single-term
+        // R-products its 2-norm exceeds 1 while the iteration converges.
+        const double order = method == QPINV_NS      ? 2.0
+                             : method == QPINV_QSAI  ? 10.0
+                             : method == QPINV_QRAPID ? 5.0
+                                                      : 19.0;
+        const double expo = std::pow(order, 1.0 + o.polish_iters);
+        const double lim = std::pow(1e-20, 1.0 / expo);  // largest ||R_j|| that qualifies
+        bool resolved = rnorm < lim;
+        if (!resolved && std::pow(drel, order) < 1e-6) {
+          const double rho = spec_radius_est(c, mat(c, "R", S.s, S.s, MST_F, false, false));
+          resolved = 1.02 * rho < lim;
+          if (c->trace) fprintf(stderr, "qpinv it %d rho(R) ~ %.4f (limit %.4f)\n", j, rho, lim);
+        }
+        if (stalled || resolved || drel < 1e-6 || (o.stop_rule == QPINV_STOP_PAPER_ABS && d < tol)) {
           polish = true;
+          S.Lr = Lr;  // polish R-products on the full split, whatever the last step used
           ck(c, launch_f32_to_f64(fview(S.X[S.cur]), n, m, S.X[S.cur].d, c->st), "X to fp64");
           S.dbl = true;
           S.xmode = PM_EMU;
@@ -1257,8 +1337,13 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
           continue;
         }
       } else if (o.precision == QPINV_PREC_MIXED && polish && polish_done >= o.polish_iters) {
-        res.status = (o.stop_rule == QPINV_STOP_PAPER_ABS ? d < tol : drel <= tol) ? QPINV_CONVERGED
-                                                                                   : QPINV_NOT_CONVERGED;
+        // After the polish iterations: CONVERGED if the stop rule holds,
+        // PLATEAU if the relative step is at the FP64 rounding floor of the
+        // update (unit roundoff times sqrt(||A||_1 ||A||_inf) ||X||_F, an
+        // upper estimate of the condition number), NOT_CONVERGED otherwise.
+        const bool conv = o.stop_rule == QPINV_STOP_PAPER_ABS ? d < tol : drel <= tol;
+        const double floor_rel = 0x1p-53 * a2est * nx;
+        res.status = conv ? QPINV_CONVERGED : drel <= floor_rel ? QPINV_PLATEAU : QPINV_NOT_CONVERGED;
         break;
       }
       prev_rel = drel;
@@ -1269,7 +1354,8 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       ck(c, launch_f32_to_f64(fview(S.X[S.cur]), n, m, S.X[S.cur].d, c->st), "X to fp64");
       S.dbl = true;
     }
-    if (!fp64 && !emu && m != n && res.status != QPINV_DIVERGED) S.range_projection();
+    // TC precision (no polish iterations): the projection is the last step.
+    if (o.precision == QPINV_PREC_TC && m != n && res.status != QPINV_DIVERGED) S.range_projection();
     QMat& Xf = S.X[S.cur];
     if (o.penrose) {
       penrose(c, S.A, Xf, fp64 ? PM_F64 : PM_EMU, res.E, res.E_rel, nullptr);
@@ -1389,22 +1475,99 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
   try {
     int nsm = 0;
     ck(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
-    int slots = nsm * batched_slots_per_sm();
-    if (slots > batch) slots = batch;
-    void* ws = buf(c, "batch.ws", batched_slot_bytes() * (size_t)slots);
-    void* items = buf(c, "batch.items", batched_item_bytes() * (size_t)batch + 64);
-    void* order = buf(c, "batch.order", sizeof(int) * (size_t)batch + 64);
-    void* results = buf(c, "batch.results", batched_result_bytes() * (size_t)batch + 64);
-    int* counter = (int*)buf(c, "batch.counter", 64);
+    int max_slots = 0;
+    for (int t = 0; t < BATCH_TILES; t++) max_slots = std::max(max_slots, nsm * batched_slots_per_sm(t));
+    max_slots = std::min(max_slots, batch);
+    BatchRun run;
+    run.ws = buf(c, "batch.ws", batched_slot_bytes() * (size_t)max_slots);
+    run.dev_items = buf(c, "batch.items", batched_item_bytes() * (size_t)batch + 64);
+    run.dev_order = buf(c, "batch.order", sizeof(int) * (size_t)batch + 64);
+    run.dev_results = buf(c, "batch.results", batched_result_bytes() * (size_t)batch + 64);
+    run.dev_counter = (int*)buf(c, "batch.counter", 64);
+    const size_t need[3] = {batched_item_bytes() * (size_t)batch, sizeof(int) * (size_t)batch,
+                            batched_result_bytes() * (size_t)batch};
+    for (int t = 0; t < 3; t++)
+      if (c->bh_cap[t] < need[t]) {
+        if (c->bh_buf[t]) cudaFreeHost(c->bh_buf[t]);
+        c->bh_buf[t] = nullptr;
+        c->bh_cap[t] = 0;
+        ck(c, cudaMallocHost(&c->bh_buf[t], need[t] + 64), "pinned staging");
+        c->bh_cap[t] = need[t];
+      }
+    run.host_items = c->bh_buf[0];
+    run.host_order = c->bh_buf[1];
+    run.host_results = c->bh_buf[2];
+    if (!c->bgraph.stream) ck(c, cudaStreamCreateWithFlags(&c->bgraph.stream, cudaStreamNonBlocking), "stream");
     std::vector<BatchResultHost> res;
     const int amode = c->opt.alpha_mode == QPINV_ALPHA_USER ? QPINV_ALPHA_USER
                       : c->opt.alpha_mode == QPINV_ALPHA_FRO ? QPINV_ALPHA_FRO
                                                               : QPINV_ALPHA_SAFE;
+    auto solve_with = [&](int tile, int cnt, const int* mm, const int* nn, const double* const* AA,
+                          const long* la, double* const* XX, const long* lx, BatchGraph* graph, int iters) {
+      run.tile = tile;
+      run.slots = std::min(cnt, nsm * batched_slots_per_sm(tile));
+      ck(c, run_batched(cnt, mm, nn, AA, la, XX, lx, (int)method, tol, iters, c->opt.qrapid_N, c->opt.stop_rule,
+                        amode, c->opt.alpha_user, hpi19_k, run, graph, res, c->st),
+         "batched solve");
+    };
+    int tile = c->opt.batched_tile;
+    if (tile < 0) {
+      // Autotuner: a batch signature (method, count, shape histogram) maps to
+      // the tile that ran three iterations on an evenly spaced sample of its
+      // matrices (one per SM) fastest.
+      unsigned long long sig = 0x51ED270B27A5B49Dull ^ ((unsigned long long)method << 40) ^ (unsigned long long)batch;
+      int hist[16] = {0};
+      for (int b = 0; b < batch; b++) hist[(std::max(m[b], n[b]) - 1) / 16]++;
+      for (int t = 0; t < 16; t++) sig = (sig ^ (unsigned long long)hist[t]) * 0x100000001B3ull;
+      auto hit = c->tile_of.find(sig);
+      if (hit != c->tile_of.end()) {
+        tile = hit->second;
+      } else {
+        const auto t0 = std::chrono::steady_clock::now();
+        const int cnt = std::min(batch, nsm);
+        std::vector<int> sm(cnt), sn(cnt);
+        std::vector<long> sla(cnt), slx(cnt);
+        std::vector<const double*> sa(4 * (size_t)cnt);
+        std::vector<double*> sx(4 * (size_t)cnt);
+        for (int k = 0; k < cnt; k++) {
+          const int b = (int)((long long)k * batch / cnt);
+          sm[k] = m[b];
+          sn[k] = n[b];
+          sla[k] = lda[b];
+          slx[k] = ldx[b];
+          for (int q = 0; q < 4; q++) {
+            sa[4 * k + q] = A[4 * b + q];
+            sx[4 * k + q] = X[4 * b + q];
+          }
+        }
+        double best = INFINITY;
+        tile = 1;
+        for (int t = 0; t < BATCH_TILES; t++) {
+          ck(c, cudaStreamSynchronize(c->st), "sync");
+          const auto a0 = std::chrono::steady_clock::now();
+          // three iterations per matrix: the tiles' relative speed, not a converged solve
+          solve_with(t, cnt, sm.data(), sn.data(), sa.data(), sla.data(), sx.data(), slx.data(), nullptr,
+                     std::min(max_iter, 3));
+          const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a0).count();
+          if (c->trace)
+            fprintf(stderr, "qpinv batched tile %s: %.2f ms on %d sampled matrices\n", batched_tile_name(t), ms, cnt);
+          if (ms < best) {
+            best = ms;
+            tile = t;
+          }
+        }
+        c->tile_of[sig] = tile;
+        c->stats.batched_tune_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+    c->stats.batched_tile = tile;
+    const int replays = c->bgraph.replays;
     timed(c, EV_EW, 0, 0, 0, [&] {
-      return run_batched(batch, m, n, A, lda, X, ldx, (int)method, tol, max_iter, c->opt.qrapid_N,
-                         c->opt.stop_rule, amode, c->opt.alpha_user, hpi19_k, ws, batched_slot_bytes() * slots,
-                         slots, items, order, results, counter, res, c->st);
+      solve_with(tile, batch, m, n, A, lda, X, ldx, &c->bgraph, max_iter);
+      return cudaSuccess;
     });
+    if (c->bgraph.replays > replays && c->bgraph.replays > 1) c->stats.batched_graph_replays++;
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (out) {

@@ -35,7 +35,7 @@ class qpinv_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("split_level", ctypes.c_int), ("polish_iters", ctypes.c_int),
                 ("alpha_mode", ctypes.c_int), ("alpha_user", ctypes.c_double), ("qrapid_N", ctypes.c_int),
                 ("side", ctypes.c_int), ("stop_rule", ctypes.c_int), ("penrose", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int)]
 
 
 class qpinv_result(ctypes.Structure):
@@ -53,7 +53,9 @@ class qpinv_stats(ctypes.Structure):
                 ("f64_gemm_ms", ctypes.c_double), ("f64_gemm_flops", ctypes.c_double),
                 ("ew_launches", ctypes.c_longlong), ("ew_ms", ctypes.c_double), ("ew_bytes", ctypes.c_double),
                 ("emu_gemm_launches", ctypes.c_longlong), ("emu_gemm_ms", ctypes.c_double),
-                ("emu_gemm_flops", ctypes.c_double), ("emu_gemm_flops_issued", ctypes.c_double)]
+                ("emu_gemm_flops", ctypes.c_double), ("emu_gemm_flops_issued", ctypes.c_double),
+                ("batched_tile", ctypes.c_longlong), ("batched_tune_ms", ctypes.c_double),
+                ("batched_graph_replays", ctypes.c_longlong)]
 
 
 PTR4 = ctypes.c_void_p * 4
@@ -192,16 +194,18 @@ class Context:
     """A libqpinv context bound to one CUDA device."""
 
     def __init__(self, device=0, precision="mixed", split_level=0, polish_iters=2, alpha="safe",
-                 alpha_user=0.0, qrapid_N=5, side="auto", stop="rel_plateau", penrose=True, profile=False):
+                 alpha_user=0.0, qrapid_N=5, side="auto", stop="rel_plateau", penrose=True, profile=False,
+                 batched_tile=-1):
         self.options = qpinv_default_options()
         self.device = device
         self.configure(precision=precision, split_level=split_level, polish_iters=polish_iters, alpha=alpha,
                        alpha_user=alpha_user, qrapid_N=qrapid_N, side=side, stop=stop, penrose=penrose,
-                       profile=profile, _apply=False)
+                       profile=profile, batched_tile=batched_tile, _apply=False)
         self.h = qpinv_init(device, self.options)
 
     def configure(self, precision=None, split_level=None, polish_iters=None, alpha=None, alpha_user=None,
-                  qrapid_N=None, side=None, stop=None, penrose=None, profile=None, _apply=True):
+                  qrapid_N=None, side=None, stop=None, penrose=None, profile=None, batched_tile=None,
+                  _apply=True):
         o = self.options
         if precision is not None: o.precision = PRECISION[precision]
         if split_level is not None: o.split_level = int(split_level)
@@ -213,6 +217,7 @@ class Context:
         if stop is not None: o.stop_rule = STOP[stop]
         if penrose is not None: o.penrose = int(bool(penrose))
         if profile is not None: o.profile = int(bool(profile))
+        if batched_tile is not None: o.batched_tile = int(batched_tile)
         if _apply:
             _check(self.h, lib().qpinv_set_options(self.h, ctypes.byref(o)), "qpinv_set_options")
 

@@ -83,3 +83,37 @@ def test_batched_rejects_oversize(qp):
         ctx.solve_batched([torch.zeros((4, 257, 3), dtype=torch.float64, device="cuda")], "ns")
     assert e.value.code == -1
     ctx.close()
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+def test_batched_every_tile_shape(qp, tile):
+    """Each CTA GEMM tile shape (16x16 .. 64x64) gives the same accuracy."""
+    mats = batch_inputs()[:12] + [I.gaussian_quaternion(70, 130, 91), I.gaussian_quaternion(200, 90, 92)]
+    ctx = qp.Context(0, batched_tile=tile)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, infos = ctx.solve_batched(As, "qhpi19", tol=1e-12, max_iter=200)
+    assert ctx.stats()["batched_tile"] == tile
+    for a, x, info in zip(mats, Xs, infos):
+        want, kappa = exact_pinv(a)
+        err = np.linalg.norm(x.cpu().numpy() - want) / np.linalg.norm(want)
+        assert err <= 1e-10 + 1e-12 * kappa ** 2, (a.shape, kappa, err, info)
+    ctx.close()
+
+
+def test_batched_autotune_and_graph_replay(qp):
+    """Autotuning picks a tile once per batch signature; the second identical
+    call replays the captured CUDA graph and reproduces X bit for bit."""
+    mats = batch_inputs()
+    ctx = qp.Context(0)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs1, _ = ctx.solve_batched(As, "qhpi19", tol=1e-12, max_iter=200)
+    X1 = [x.clone() for x in Xs1]
+    st1 = ctx.stats()
+    assert 0 <= st1["batched_tile"] < 5 and st1["batched_tune_ms"] > 0
+    Xs2, _ = ctx.solve_batched(As, "qhpi19", tol=1e-12, max_iter=200, Xs=Xs1)
+    st2 = ctx.stats()
+    assert st2["batched_tune_ms"] == st1["batched_tune_ms"]  # signature cached
+    assert st2["batched_graph_replays"] == st1["batched_graph_replays"] + 1
+    for a, b in zip(X1, Xs2):
+        assert torch.equal(a, b)
+    ctx.close()

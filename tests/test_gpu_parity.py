@@ -232,6 +232,22 @@ def test_qgemm_exact_slices_wide_dynamic_range(ctx):
     assert np.max(np.abs(C - Co) / scale[None]) <= 1e-15
 
 
+@pytest.mark.parametrize("m,n", [(640, 320), (320, 640)])
+def test_solve_rectangular_full_rank_mixed(ctx, m, n):
+    """Full-rank rectangular A with sigma geometric 1..1e-4: MIXED (no EMU
+    retry) must reach the FP64 level, which needs the component of X outside
+    the pseudoinverse's row / column space (left by the FP32 phase) removed."""
+    k = min(m, n)
+    s = np.geomspace(1.0, 1e-4, k)
+    U = I.orthonormal_columns(m, k, 31)
+    V = I.orthonormal_columns(n, k, 32)
+    A = I.with_spectrum(U, s, V)
+    X, info = ctx.solve(dev(A), "qhpi19", tol=1e-12)
+    assert info["precision"] == "mixed", info
+    assert info["E_rel"][0] <= 1e-10 and info["E_rel"][1] <= 1e-10, info
+    assert rel(X.cpu().numpy(), oracle.pinv_from_svd(U, s, V)) <= 1e-9, info
+
+
 @pytest.mark.parametrize("method", ["qhpi19", "qsai", "ns"])
 def test_solve_logspaced_kappa_1e6(ctx, method):
     """Square A = U diag(sigma) V^H with sigma log-spaced 1..1e-6 (the large

@@ -67,6 +67,7 @@ struct CombineArgs {
   int rows = 0, cols = 0;
   int f64 = 0;                // master type of aux inputs and outputs: 0 float, 1 double
   const void* acc = nullptr;  // accumulator planes, may be null
+  const long long* acc2 = nullptr;  // ACC_I64: a second accumulator of the same layout, summed
   int acc_kind = ACC_F32;     // ACC_I64: fixed point, value = acc * 2^(erow[i] + ecol[j] - shift)
   long ld_acc = 0, ps_acc = 0;
   const int* acc_erow = nullptr;
@@ -146,6 +147,7 @@ struct EmuGemmArgs {
   int S = 0;
   int kc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long* C64 = nullptr;
+  long long* C64b = nullptr;  // non-null: a second accumulator (same layout) for half of the levels
   long ld64 = 0, ps64 = 0;
   int shift = 0;
   int* err = nullptr;

@@ -101,7 +101,7 @@ __device__ __forceinline__ T acc_value(const CombineArgs& a, int c, int i, int j
   const long off = c * a.ps_acc + (long)i * a.ld_acc + j;
   if (a.acc_kind == ACC_F64) return (T)((const double*)a.acc)[off];
   if (a.acc_kind == ACC_I64) {
-    const long long q = ((const long long*)a.acc)[off];
+    const long long q = ((const long long*)a.acc)[off] + (a.acc2 ? a.acc2[off] : 0LL);
     const int e = a.acc_erow[i] + a.acc_ecol[j] - a.acc_shift;
     if (sizeof(T) == 4) return (T)ldexpf((float)q, e);
     return (T)ldexp((double)q, e);

@@ -9,8 +9,10 @@
 // it spans is short enough (host-chosen chunk per level); the two lowest
 // levels run over the whole K.
 //
-// One CTA owns a 128 x 64 quaternion output tile and walks all (level,
-// K-chunk) work items: the MMA warp accumulates a chunk into an FP32 TMEM
+// A persistent grid (one CTA per SM) walks work items (tile, level group):
+// the levels are split into two groups of equal cost, each summed into its
+// own int64 accumulator, so that 2 x tiles items balance over the SMs.  For
+// each level of its item the MMA warp accumulates a K-chunk into an FP32 TMEM
 // buffer (columns 0..255); the epilogue warps convert it exactly to int32 and
 // add it into an int32 TMEM accumulator of the level (columns 256..511), then
 // release the buffer for the next chunk.  At the end of a level the int32 sum
@@ -22,6 +24,8 @@
 // int32 range: a level-d sum is bounded by 4K 2^12 (d + 3) (2^14 for d = 0)
 // level units; launch_qgemm_emu refuses K beyond what keeps this below 2^31.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
@@ -47,13 +51,26 @@ constexpr uint32_t EIDESC_NEG_A = EIDESC | (1u << 13);
 struct EParams {
   int M, N, K, S;
   int Mt, Nt;
-  int kc[8];  // K chunk of each level (elements; multiple of EBK, or >= K); work items
-              // run level S-1 first, each level's chunks in K order
-  long long* C64;
+  int kc[8];  // K chunk of each level (elements; multiple of EBK, or >= K)
+  // Work items (tile, group): the levels are split into `ngroups` groups of
+  // about equal cost (level d costs d + 1 slice pairs), each with its own
+  // int64 accumulator, so that two CTAs share a tile without atomics and the
+  // persistent grid balances (tiles x groups) items instead of whole tiles.
+  int ngroups, items;
+  int nlv[2], lv[2][8];  // levels of each group, largest first
+  long long* C64g[2];
   long ld64, ps64;
   int shift;  // int64 fixed point: value * 2^shift
   int* err;
 };
+
+// Grouped rasterization of tile t: consecutive tiles walk EGROUP_M row tiles.
+__device__ __forceinline__ void tile_origin(const EParams& P, int t, int& m0, int& n0) {
+  const int per_group = EGROUP_M * P.Nt, group = t / per_group, local = t % per_group;
+  const int gm = min(EGROUP_M, P.Mt - group * EGROUP_M);
+  m0 = (group * EGROUP_M + local % gm) * EBM;
+  n0 = (local / gm) * EBN;
+}
 
 __global__ void __launch_bounds__(ETHREADS, 1)
     k_qgemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EParams P) {
@@ -64,9 +81,6 @@ __global__ void __launch_bounds__(ETHREADS, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per_group = EGROUP_M * P.Nt, group = blockIdx.x / per_group, local = blockIdx.x % per_group;
-  const int gm = min(EGROUP_M, P.Mt - group * EGROUP_M);
-  const int m0 = (group * EGROUP_M + local % gm) * EBM, n0 = (local / gm) * EBN;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -97,7 +111,12 @@ __global__ void __launch_bounds__(ETHREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       int u = 0;
       bool ok = true;
-      for (int d = P.S - 1; d >= 0 && ok; d--) {
+      for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
+       const int g = item % P.ngroups;
+       int m0, n0;
+       tile_origin(P, item / P.ngroups, m0, n0);
+       for (int li = 0; li < P.nlv[g] && ok; li++) {
+        const int d = P.lv[g][li];
         for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d]) {
           const int kb0 = k0 / EBK, kb1 = (min(P.K, k0 + P.kc[d]) + EBK - 1) / EBK;
           for (int kb = kb0; kb < kb1 && ok; kb++) {
@@ -119,6 +138,7 @@ __global__ void __launch_bounds__(ETHREADS, 1)
             }
           }
         }
+       }
       }
     }
   } else if (warp == 1) {
@@ -126,7 +146,10 @@ __global__ void __launch_bounds__(ETHREADS, 1)
     if (lane == 0) {
       int u = 0, w = 0;
       bool ok = true;
-      for (int d = P.S - 1; d >= 0 && ok; d--) {
+      for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
+       const int g = item % P.ngroups;
+       for (int li = 0; li < P.nlv[g] && ok; li++) {
+        const int d = P.lv[g][li];
         for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
           // the FP32 buffer is free once the epilogue has read chunk w - 1
           if (w > 0 && !mbar_wait(smem_u32(&bar_acc_empty), (w - 1) & 1, &abort_flag, P.err, 12)) {
@@ -168,18 +191,25 @@ __global__ void __launch_bounds__(ETHREADS, 1)
           }
           if (ok) mma_commit(smem_u32(&bar_acc_full));
         }
+       }
       }
     }
   } else {
     // ---------------- epilogue: exact FP32 -> int32 per chunk, int64 per level ----------------
     const int quarter = warp & 3;
-    const int row0 = m0 + quarter * 32;
     const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
     long long* st64 = reinterpret_cast<long long*>(smem + ESTAGES * ESTAGE) + (warp - 2) * (32 * 33);
-    const int nrow = min(32, P.M - row0);
     int w = 0;
     bool ok = true;
-    for (int d = P.S - 1; d >= 0 && ok; d--) {
+    for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
+     const int g = item % P.ngroups;
+     int m0, n0;
+     tile_origin(P, item / P.ngroups, m0, n0);
+     const int row0 = m0 + quarter * 32;
+     const int nrow = min(32, P.M - row0);
+     long long* const C64 = P.C64g[g];
+     for (int li = 0; li < P.nlv[g] && ok; li++) {
+      const int d = P.lv[g][li];
       const float scale = ldexpf(1.0f, 7 * (d + 2));  // level unit -> integer (a power of two: exact)
       const int sh = P.shift - 7 * (d + 2);
       for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
@@ -226,12 +256,13 @@ __global__ void __launch_bounds__(ETHREADS, 1)
           __syncwarp();
           const int c = p >> 1, col = n0 + (p & 1) * 32 + lane;
           if (col < P.N) {
-            long long* dst = P.C64 + c * P.ps64 + (long)row0 * P.ld64 + col;
+            long long* dst = C64 + c * P.ps64 + (long)row0 * P.ld64 + col;
             rmw_rows64(dst, P.ld64, nrow, st64 + lane);
           }
           __syncwarp();
         }
       }
+     }
     }
   }
 
@@ -272,7 +303,17 @@ cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st) {
     if (kc < a.K && (kc <= 0 || kc % EBK)) return cudaErrorInvalidValue;
     P.kc[d] = kc < a.K ? kc : a.K;
   }
-  P.C64 = a.C64;
+  // level groups: largest cost first, each to the lighter group
+  P.ngroups = a.C64b ? 2 : 1;
+  P.nlv[0] = P.nlv[1] = 0;
+  int load[2] = {0, 0};
+  for (int d = a.S - 1; d >= 0; d--) {
+    const int g = (P.ngroups == 2 && load[1] < load[0]) ? 1 : 0;
+    P.lv[g][P.nlv[g]++] = d;
+    load[g] += d + 1;
+  }
+  P.C64g[0] = a.C64;
+  P.C64g[1] = a.C64b ? a.C64b : a.C64;
   P.ld64 = a.ld64;
   P.ps64 = a.ps64;
   P.shift = a.shift;
@@ -288,7 +329,14 @@ cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_qgemm_emu<<<P.Mt * P.Nt, ETHREADS, ESMEM, st>>>(mA, mB, P);
+  P.items = P.Mt * P.Nt * P.ngroups;
+  static int nsm[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidValue;
+  if (!nsm[dev] && cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidValue;
+  const int grid = std::min(P.items, nsm[dev]);  // persistent: one CTA per SM
+  k_qgemm_emu<<<grid, ETHREADS, ESMEM, st>>>(mA, mB, P);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

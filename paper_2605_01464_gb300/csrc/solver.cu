@@ -287,6 +287,7 @@ struct Solver {
     const int* erow;
     const int* ecol;
     int shift;
+    const long long* p2 = nullptr;  // ACC_I64: second accumulator of the same layout, summed
   };
 
   Acc rprod(const QMat& P, const QMat& Q) {
@@ -415,13 +416,19 @@ struct Solver {
           g.kc[d] = (lim / 32) * 32;
         }
       }
+      // half of the levels go to a second accumulator (see qgemm_emu.cu)
+      long long* acc2 = (long long*)buf(c, "emu.acc2", sizeof(long long) * 4 * (size_t)M * N + 64);
+      ck(c, cudaMemsetAsync(acc2, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");
       g.C64 = acc;
+      g.C64b = S >= 2 ? acc2 : nullptr;
       g.ld64 = N;
       g.ps64 = (long)M * N;
       g.shift = shift;
       g.err = c->d_err;
       timed(c, EV_EMU, flops, flops * S * (S + 1) / 2, 0, [&] { return launch_qgemm_emu(g, c->st); });
-      return Acc{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
+      Acc r{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
+      r.p2 = g.C64b;
+      return r;
     }
     for (int hi = S - 1; hi >= 0; hi -= 2) {
       const int lo = hi - 1;  // second level of the launch (-1: none)
@@ -473,6 +480,7 @@ struct Solver {
       a.acc_erow = acc->erow;
       a.acc_ecol = acc->ecol;
       a.acc_shift = acc->shift;
+      a.acc2 = acc->p2;
     }
     return a;
   }

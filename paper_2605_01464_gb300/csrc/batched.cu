@@ -67,8 +67,8 @@ __device__ __forceinline__ dfv df_fma(dfv a, dfv b, dfv c) {
 __device__ __forceinline__ dfv df_mul(dfv a, dfv b) { return df_fma(a, b, dfv{0.f, 0.f}); }
 // Lazy accumulation for dot products (compensated summation in the manner of
 // Ogita, Rump and Oishi's Dot2, with df inputs): acc.hi is the running sum,
-// acc.lo collects every rounding and low-order term unnormalised; df_norm
-// turns it back into a df value at the end of the dot product.
+// acc.lo collects the rounding and low-order terms of a few products
+// unnormalised; df_norm turns it back into a df value.
 __device__ __forceinline__ void df_dot_add(dfv& acc, dfv a, dfv b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
@@ -217,6 +217,11 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
               df_dot_add(o[3], x[1], y[2]);
               df_dot_add(o[3], df_neg(x[2]), y[1]);
               df_dot_add(o[3], x[3], y[0]);
+              // renormalise after every quaternion term (four real terms): the
+              // unnormalised low part must stay near u |hi|, or its own
+              // rounding grows with the square of the dot-product length
+#pragma unroll
+              for (int c = 0; c < 4; c++) o[c] = df_norm(o[c]);
             }
         }
         __syncthreads();

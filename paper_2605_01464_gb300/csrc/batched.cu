@@ -79,7 +79,13 @@ __device__ __forceinline__ void df_dot_add(dfv& acc, dfv a, dfv b) {
   acc.lo += ((acc.hi - (s - v)) + (p - v)) + e;
   acc.hi = s;
 }
-__device__ __forceinline__ dfv df_norm(dfv a) { return df_quick(a.hi, a.lo); }
+// Renormalisation by a full two-sum: exact whichever part is larger (after
+// cancellation in the running sum the low part can exceed the high part).
+__device__ __forceinline__ dfv df_norm(dfv a) {
+  const float s = a.hi + a.lo;
+  const float v = s - a.hi;
+  return dfv{s, (a.hi - (s - v)) + (a.lo - v)};
+}
 __device__ __forceinline__ dfv df_from(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};

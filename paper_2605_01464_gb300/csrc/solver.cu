@@ -909,12 +909,28 @@ void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, do
   };
   product(A, X, Rr, 8, -1.0);
   product(X, A, Rl, 8, -1.0);
-  product(Rr, A, E1m, 8, 0.0);
-  product(Rl, X, E2m, 8, 0.0);
-  if (gemms) *gemms += S.gemms;
   Planes<const double> a = dview(A), x = dview(X);
-  E[0] = std::sqrt(fro2(c, dview(E1m), nullptr, m, n));
-  E[1] = std::sqrt(fro2(c, dview(E2m), nullptr, n, m));
+  const double fa = std::sqrt(fro2(c, a, nullptr, m, n)), fx = std::sqrt(fro2(c, x, nullptr, n, m));
+  // ||R Q||_F with R = AX - I or XA - I.  When R is small (square
+  // full-rank A) the product needs only a few digits relative to ||R|| ||Q||:
+  // 6 slices are accepted when the result exceeds 1e3 times a bound on their
+  // truncation error, 2^(10 - 7S) K ||R||_F ||Q||_F; otherwise 8 slices.
+  auto outer = [&](const QMat& R, const QMat& Q, QMat& Out, double fq) {
+    const int rows = R.rows, cols = Q.cols, K = R.cols;
+    if (mode == PM_EMU) {
+      const double fr = std::sqrt(fro2(c, dview(R), nullptr, R.rows, R.cols));
+      if (fr <= 1e-3) {
+        product(R, Q, Out, 6, 0.0);
+        const double e = std::sqrt(fro2(c, dview(Out), nullptr, rows, cols));
+        if (e >= 1e3 * std::ldexp(1.0, 10 - 7 * 6) * K * fr * fq) return e;
+      }
+    }
+    product(R, Q, Out, 8, 0.0);
+    return std::sqrt(fro2(c, dview(Out), nullptr, rows, cols));
+  };
+  E[0] = outer(Rr, A, E1m, fa);
+  E[1] = outer(Rl, X, E2m, fx);
+  if (gemms) *gemms += S.gemms;
   E[2] = std::sqrt(antiherm2(c, Rr));
   E[3] = std::sqrt(antiherm2(c, Rl));
   // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from AX = Rr + I instead
@@ -929,8 +945,8 @@ void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, do
     S.out(u, XA, "f", 0.0, 1.0).caux[0] = 1.0;
     S.run(u);
   }
-  const double nr[4] = {std::sqrt(fro2(c, a, nullptr, m, n)), std::sqrt(fro2(c, x, nullptr, n, m)),
-                        std::sqrt(fro2(c, dview(AX), nullptr, m, m)), std::sqrt(fro2(c, dview(XA), nullptr, n, n))};
+  const double nr[4] = {fa, fx, std::sqrt(fro2(c, dview(AX), nullptr, m, m)),
+                        std::sqrt(fro2(c, dview(XA), nullptr, n, n))};
   for (int t = 0; t < 4; t++) Er[t] = nr[t] > 0 ? E[t] / nr[t] : E[t];
 }
 

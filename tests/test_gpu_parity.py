@@ -180,6 +180,23 @@ def test_penrose_matches_oracle(ctx):
     assert np.allclose(R, Ro, rtol=1e-8, atol=1e-14)
 
 
+def test_penrose_small_residual_closed_form(ctx):
+    """Square unitary A = Q and X = Q^H + d E: E1 = ||Q (d E) Q|| = d ||E||
+    and E2 = ||d E + d^2 E Q E|| exactly (unitary invariance), small enough
+    that the outer products run on 6 exact slices after their error check."""
+    Q = I.orthonormal_columns(64, 64, 21)
+    E = I.gaussian_quaternion(64, 64, 22)
+    d = 1e-9
+    X = oracle.adjoint(Q) + d * E
+    ctx.configure(precision="emu")
+    got, _ = ctx.penrose(dev(Q), dev(X))
+    e1 = d * np.linalg.norm(E)
+    e2 = np.linalg.norm(d * E + d * d * oracle.matmul(oracle.matmul(E, Q), E))
+    assert abs(got[0] - e1) <= 1e-6 * e1, (got, e1)
+    assert abs(got[1] - e2) <= 1e-6 * e2, (got, e2)
+    ctx.configure(precision="mixed")
+
+
 def test_spectral_alpha_matches_oracle(ctx):
     A = I.gaussian_quaternion(40, 25, 13)
     ctx.configure(alpha="spectral")

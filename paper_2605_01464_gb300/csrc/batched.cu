@@ -225,9 +225,11 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
               df_dot_add(o[3], x[3], y[0]);
               // renormalise after every quaternion term (four real terms): the
               // unnormalised low part must stay near u |hi|, or its own
-              // rounding grows with the square of the dot-product length
+              // rounding grows with the square of the dot-product length (a
+              // fast two-sum; its rare inexact case under cancellation costs
+              // O(u^2) of the partial sums, the df level)
 #pragma unroll
-              for (int c = 0; c < 4; c++) o[c] = df_norm(o[c]);
+              for (int c = 0; c < 4; c++) o[c] = df_quick(o[c].hi, o[c].lo);
             }
         }
         __syncthreads();

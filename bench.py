@@ -343,10 +343,10 @@ def bench_learned(args, torch, qpinv):
 
 # DRAM bytes (read + write) per issued tensor flop from one ncu capture of
 # each current kernel on a 2048^3 product (profiles/k_qgemm_emu_2048_slices8.md:
-# 8.11 GB for 36 passes; profiles/k_qgemm_tc_2048_split2.md: 245 MB for 3
+# 11.54 GB for 36 passes; profiles/k_qgemm_tc_2048_split2.md: 245 MB for 3
 # pairs); a launch's traffic is estimated as this times its issued flops.
 # None once the kernel changes after its capture.
-TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": None,  # persistent level-group version not captured yet
+TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 11.536e9 / (36 * 32 * 2048.0 ** 3),
                            "k_qgemm_tc": 245.07e6 / (3 * 32 * 2048.0 ** 3)}
 
 

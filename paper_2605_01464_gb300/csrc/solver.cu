@@ -1243,6 +1243,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       const bool square_mixed = o.precision == QPINV_PREC_MIXED && m == n;
       S.Lx = square_mixed ? 2 : 3;
       S.xSu = square_mixed ? 3 : 4;
+      S.L = std::max(S.Lx, Lr);  // BF16 terms the operand forms need: no more are written
       S.xmode = PM_TC;
       ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
       ck(c, launch_f64_to_f32(dview(S.X[0]), n, m, S.X[0].f, c->st), "X0 to fp32");

@@ -216,7 +216,7 @@ void qpinv_free(qpinv_ctx* ctx);
 /* Message for the last error on this context (never NULL). */
 const char* qpinv_last_error(qpinv_ctx* ctx);
 
-/* ---- learned initial scaling (the benchmark spec's learned initializer) ----
+/* ---- learned initial scaling alpha for X_0 = alpha A^H (Thm. 1) ----
  * A 32 -> 64 -> 64 -> 1 tanh network maps 32 cheap sketched features of A to
  * y = log(alpha * theta_1), where theta_1 <= sigma_1^2 is the top Ritz value
  * of a 16-step Lanczos run on A^H A; labels are the optimum of Thm. 1's

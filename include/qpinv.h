@@ -57,9 +57,9 @@ extern "C" {
 /* ---- solver outcome (qpinv_result.status) ----------------------------- */
 #define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
 #define QPINV_PLATEAU 1       /* rounding floor reached: the relative step stopped decreasing after
-                                 falling below 1e-3 (X is the iterate before that step), or, after
-                                 MIXED's polish iterations, it is below 2^-53 sqrt(||A||_1 ||A||_inf)
-                                 ||X||_F */
+                                 falling below 1e-3 (X is the iterate before that step), or, in
+                                 MIXED's polish phase, the step (or the residual of X, which bounds
+                                 the next step) is below 2^-53 sqrt(||A||_1 ||A||_inf) ||X||_F */
 #define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
 #define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
 #define QPINV_NONFINITE_INPUT 4 /* qpinv_solve_batched: this A holds NaN/Inf; its X is left untouched */

@@ -273,6 +273,9 @@ struct Solver {
   int rmode = -1;         // mode of the R-products (-1: PM_F64 if L == 0, else PM_TC)
   int xS = 8;             // exact slices of X-products in PM_EMU mode
   int xSu = 3;            // ... of the update product X t while the masters are FP32
+  int xSp = 0;            // ... of the update product in a polish step (0: xS)
+  bool pre_res = false;   // pre_R is the residual of X[cur], computed ahead of the step
+  QMat pre_R;
   long long gemms = 0;
   QMat A, X[2];
   int cur = 0;
@@ -568,6 +571,7 @@ struct Solver {
     Lcur = Lx;
     const int save = xS;
     if (xmode == PM_EMU && !dbl) xS = xSu;
+    else if (xmode == PM_EMU && dbl && xSp > 0) xS = xSp;
     Acc r = left ? prod(T, Y, xmode) : prod(Y, T, xmode);
     xS = save;
     return r;
@@ -579,6 +583,10 @@ struct Solver {
   // R = I - (residual product of Y).
   // norm: also reduce ||R||_F^2 into red[4] (the iteration's own residual).
   QMat residual(const QMat& Y, const char* name, const char* forms, bool norm = false) {
+    if (pre_res && strcmp(name, "R") == 0) {  // computed ahead of the step for X[cur]
+      pre_res = false;
+      return pre_R;
+    }
     Acc acc = res_prod(Y);
     QMat R = sq(name, strchr(forms, 'a') != nullptr, strchr(forms, 'b') != nullptr);
     CombineArgs a = base_args(s, s, &acc);
@@ -1272,6 +1280,32 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       // next step's power of R removes; 2-term splits after (automatic
       // split_level only).
       if (!polish && !emu && o.split_level == 0) S.Lr = prev_rel > 0.5 ? 1 : Lr;
+      S.xSp = 0;
+      if (o.precision == QPINV_PREC_MIXED && polish && polish_done >= 1) {
+        // Later polish steps: form the residual of X_j first.  The step
+        // changes X by about ||X t|| <= ||X|| ||t||, ||t|| ~ ||R_j||, so when
+        // ||R_j||_F is at the rounding floor of the update (or within the
+        // relative tolerance) the step is not taken; otherwise the update
+        // product X t needs only enough exact slices for FP64 accuracy of
+        // X + X t: 53 + log2(4 ||R_j||_F) bits, plus one slice of guard.
+        S.pre_R = S.residual(S.X[S.cur], "R", "fab", true);
+        S.pre_res = true;
+        double hr[8];
+        read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 6, hr);
+        const double rn = std::sqrt(hr[4]);
+        const double floor_rel = 0x1p-53 * a2est * xnorm;
+        if (c->trace) fprintf(stderr, "qpinv it %d polish residual |R|_F %.3e floor %.3e\n", j, rn, floor_rel);
+        if (o.stop_rule != QPINV_STOP_PAPER_ABS && (rn <= tol || rn <= floor_rel)) {
+          S.pre_res = false;
+          res.status = rn <= tol ? QPINV_CONVERGED : QPINV_PLATEAU;
+          res.delta_rel = rn;  // the predicted relative step
+          break;
+        }
+        if (rn > 0.0) {
+          const int bits = 53 + (int)std::ceil(std::log2(4.0 * rn));
+          S.xSp = std::min(8, std::max(3, (bits + 6) / 7 + 1));
+        }
+      }
       switch (method) {
         case QPINV_NS: S.step_ns(); break;
         case QPINV_QSAI: S.step_qsai((1.0 + std::sqrt(5.0)) / 2.0, (1.0 - std::sqrt(5.0)) / 2.0); break;

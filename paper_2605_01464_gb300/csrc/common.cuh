@@ -85,6 +85,8 @@ struct CombineArgs {
 // Host-side launch helpers implemented in elementwise.cu / qgemm_*.cu.
 namespace qp {
 
+// blocks (and partials) launch_combine will use for these arguments
+int combine_blocks(const CombineArgs& a);
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_out);
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int nvals, double* out,
                                    cudaStream_t st);

@@ -186,6 +186,181 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
   }
 }
 
+// FP32 passes over column pairs: 32 rows x 64 columns per block, each thread
+// two adjacent columns (8-byte loads and stores, packed BF16 pairs), which
+// halves the index arithmetic and store instructions per element.  Needs even
+// leading dimensions and plane strides for every FP32 / FP64 / int64 plane it
+// touches (combine_pairs_ok); the BF16 forms have ld, ps multiples of 8.
+__device__ __forceinline__ void split_store2(bf16* base, long idx, long lstride, int levels, float x, float y) {
+  float rx = x, ry = y;
+  for (int l = 0; l < levels; l++) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(rx, ry);
+    *reinterpret_cast<__nv_bfloat162*>(base + l * lstride + idx) = t;
+    rx -= __low2float(t);
+    ry -= __high2float(t);
+  }
+}
+
+__device__ __forceinline__ void acc_pair(const CombineArgs& a, int c, int i, int j, bool two, float& x, float& y) {
+  const long off = c * a.ps_acc + (long)i * a.ld_acc + j;
+  if (a.acc_kind == ACC_F32) {
+    if (two) {
+      const float2 t = *reinterpret_cast<const float2*>((const float*)a.acc + off);
+      x = t.x;
+      y = t.y;
+    } else {
+      x = ((const float*)a.acc)[off];
+    }
+  } else if (a.acc_kind == ACC_F64) {
+    const double* p = (const double*)a.acc + off;
+    x = (float)p[0];
+    if (two) y = (float)p[1];
+  } else {
+    const long long* p = (const long long*)a.acc + off;
+    long long q0 = p[0], q1 = two ? p[1] : 0;
+    if (a.acc2) {
+      q0 += a.acc2[off];
+      if (two) q1 += a.acc2[off + 1];
+    }
+    const int er = a.acc_erow[i] - a.acc_shift;
+    x = ldexpf((float)q0, er + a.acc_ecol[j]);
+    if (two) y = ldexpf((float)q1, er + a.acc_ecol[j + 1]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_combine_f2(CombineArgs a) {
+  __shared__ float stage[4][2 * TILE][TILE + 1];  // [plane][column][row]
+  __shared__ double red[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * 2 * TILE;
+  const int j = c0 + 2 * tx;
+  float s_dx = 0.f, s_x = 0.f;
+  int s_bad = 0;
+
+  for (int o = 0; o < a.nout; o++) {
+    const OutSpec& O = a.out[o];
+    const float cacc = (float)O.cacc, diag = (float)O.diag;
+    for (int q = 0; q < TILE / TROWS; q++) {
+      const int i = r0 + ty + q * TROWS;
+      float v[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      const bool in0 = i < a.rows && j < a.cols, two = in0 && j + 1 < a.cols;
+      if (in0) {
+        if (a.acc && O.cacc != 0.0)
+          for (int c = 0; c < 4; c++) {
+            float x = 0.f, y = 0.f;
+            acc_pair(a, c, i, j, two, x, y);
+            v[c][0] = cacc * x;
+            v[c][1] = cacc * y;
+          }
+        for (int t = 0; t < 4; t++) {
+          if (!a.aux[t] || O.caux[t] == 0.0) continue;
+          const float* ap = (const float*)a.aux[t];
+          const float ct = (float)O.caux[t];
+          for (int c = 0; c < 4; c++) {
+            const long off = c * a.ps_aux[t] + (long)i * a.ld_aux[t] + j;
+            if (two) {
+              const float2 u = *reinterpret_cast<const float2*>(ap + off);
+              v[c][0] += ct * u.x;
+              v[c][1] += ct * u.y;
+            } else {
+              v[c][0] += ct * ap[off];
+            }
+          }
+        }
+        if (i == j) v[0][0] += diag;
+        if (two && i == j + 1) v[0][1] += diag;
+        if (o == 0 && a.partials) {
+          const float* x0p = (const float*)a.aux[0];
+          for (int c = 0; c < 4; c++)
+            for (int h = 0; h < (two ? 2 : 1); h++) {
+              const float x0 = x0p ? x0p[c * a.ps_aux[0] + (long)i * a.ld_aux[0] + j + h] : 0.f;
+              s_dx += (v[c][h] - x0) * (v[c][h] - x0);
+              s_x += v[c][h] * v[c][h];
+              s_bad += isfinite(v[c][h]) ? 0 : 1;
+            }
+        }
+        if (O.mp)
+          for (int c = 0; c < 4; c++) {
+            float* dst = (float*)O.mp + c * O.mps + (long)i * O.mld + j;
+            if (two) *reinterpret_cast<float2*>(dst) = make_float2(v[c][0], v[c][1]);
+            else dst[0] = v[c][0];
+          }
+        if (O.s16.a)
+          for (int c = 0; c < 4; c++) {
+            const long idx = c * O.s16.psa + (long)i * O.s16.lda + j;
+            if (O.exp_a) {
+              slice_store<float>(O.s16.a, idx, 4 * O.s16.psa, O.s16.levels, v[c][0], O.exp_a[i]);
+              if (two) slice_store<float>(O.s16.a, idx + 1, 4 * O.s16.psa, O.s16.levels, v[c][1], O.exp_a[i]);
+            } else if (two) {
+              split_store2(O.s16.a, idx, 4 * O.s16.psa, O.s16.levels, v[c][0], v[c][1]);
+            } else {
+              split_store(O.s16.a, idx, 4 * O.s16.psa, O.s16.levels, v[c][0]);
+            }
+          }
+      }
+      if (O.s16.b)
+        for (int c = 0; c < 4; c++) {
+          stage[c][2 * tx][ty + q * TROWS] = v[c][0];
+          stage[c][2 * tx + 1][ty + q * TROWS] = v[c][1];
+        }
+    }
+    if (O.s16.b) {
+      __syncthreads();
+      // B-form row jj (an output column) holds the block's 32 rows ii: thread
+      // t writes the pair ii = 2 (t % 16), +1 of columns t / 16 + 16 k.
+      const int p = threadIdx.x & 15;
+      for (int k = 0; k < 4; k++) {
+        const int jl = (threadIdx.x >> 4) + 16 * k, jj = c0 + jl, ii = r0 + 2 * p;
+        if (jj < a.cols && ii < a.rows) {
+          const bool pair = ii + 1 < a.rows;
+          for (int c = 0; c < 4; c++) {
+            const long idx = c * O.s16.psb + (long)jj * O.s16.ldb + ii;
+            const float x = stage[c][jl][2 * p], y = stage[c][jl][2 * p + 1];
+            if (O.exp_b) {
+              slice_store<float>(O.s16.b, idx, 4 * O.s16.psb, O.s16.levels, x, O.exp_b[jj]);
+              if (pair) slice_store<float>(O.s16.b, idx + 1, 4 * O.s16.psb, O.s16.levels, y, O.exp_b[jj]);
+            } else if (pair) {
+              split_store2(O.s16.b, idx, 4 * O.s16.psb, O.s16.levels, x, y);
+            } else {
+              split_store(O.s16.b, idx, 4 * O.s16.psb, O.s16.levels, x);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (a.partials) {
+    const long b = (long)blockIdx.y * gridDim.x + blockIdx.x;
+    const double t0 = block_sum((double)s_dx, red);
+    const double t1 = block_sum((double)s_x, red);
+    const double t2 = block_sum((double)s_bad, red);
+    if (threadIdx.x == 0) {
+      a.partials[3 * b + 0] = t0;
+      a.partials[3 * b + 1] = t1;
+      a.partials[3 * b + 2] = t2;
+    }
+  }
+}
+
+// The pair kernel applies to FP32 passes whose FP32 / FP64 / int64 planes all
+// have even leading dimensions, plane strides and 16-byte aligned bases.
+static bool combine_pairs_ok(const CombineArgs& a) {
+  if (a.f64) return false;
+  auto even = [](long x) { return (x & 1) == 0; };
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (a.acc && (!even(a.ld_acc) || !even(a.ps_acc) || !al(a.acc) || (a.acc2 && !al(a.acc2)))) return false;
+  for (int t = 0; t < 4; t++)
+    if (a.aux[t] && (!even(a.ld_aux[t]) || !even(a.ps_aux[t]) || !al(a.aux[t]))) return false;
+  for (int o = 0; o < a.nout; o++) {
+    const OutSpec& O = a.out[o];
+    if (O.mp && (!even(O.mld) || !even(O.mps) || !al(O.mp))) return false;
+    if (O.s16.a && (!al(O.s16.a) || (O.s16.lda & 1) || (O.s16.psa & 1))) return false;
+    if (O.s16.b && (!al(O.s16.b) || (O.s16.ldb & 1) || (O.s16.psb & 1))) return false;
+  }
+  return true;
+}
+
 __global__ void k_reduce_partials(const double* p, int nblocks, int nvals, double* out) {
   __shared__ double sh[8];
   for (int v = 0; v < nvals; v++) {
@@ -407,10 +582,22 @@ int grid_for(long total) {
 
 }  // namespace
 
+int combine_blocks(const CombineArgs& a) {
+  const int cw = combine_pairs_ok(a) ? 2 * TILE : TILE;
+  return ((a.cols + cw - 1) / cw) * ((a.rows + TILE - 1) / TILE);
+}
+
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, int* blocks_out) {
-  dim3 grid((a.cols + TILE - 1) / TILE, (a.rows + TILE - 1) / TILE);
+  const bool pairs = combine_pairs_ok(a);
+  const int cw = pairs ? 2 * TILE : TILE;
+  dim3 grid((a.cols + cw - 1) / cw, (a.rows + TILE - 1) / TILE);
   if (blocks_out) *blocks_out = grid.x * grid.y;
   if (a.rows <= 0 || a.cols <= 0) return cudaSuccess;
+  if (pairs) {
+    k_combine_f2<<<grid, TILE * TROWS, 0, st>>>(a);
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
   if (a.f64)
     k_combine<double><<<grid, TILE * TROWS, 0, st>>>(a);
   else

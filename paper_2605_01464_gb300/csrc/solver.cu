@@ -533,7 +533,7 @@ struct Solver {
   // with_partials: block partials of ||out - aux0||^2, ||out||^2 and the
   // non-finite count, reduced into red_slot[0..2] of the "red" buffer.
   void run(CombineArgs& a, bool with_partials = false, int red_slot = 0) {
-    int blocks = ((a.cols + 31) / 32) * ((a.rows + 31) / 32);
+    const int blocks = combine_blocks(a);
     if (with_partials) {
       if (blocks > partial_cap) {
         partials = (double*)buf(c, "partials", sizeof(double) * 3 * (size_t)blocks + 64);

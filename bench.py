@@ -31,7 +31,7 @@ METRIC = "pinv solves/s & quaternion-GEMM TFLOP/s (% TC peak) to rel. Penrose re
 # sample extrapolates to: iterations x 7 products + 4 Penrose products.  The
 # iteration count is the one the GPU arm reports for this workload
 # ("iters" in its JSON line).
-WORKLOAD_ITERS = 16
+WORKLOAD_ITERS = 14
 
 
 def peaks():

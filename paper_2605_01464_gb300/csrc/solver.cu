@@ -1403,6 +1403,17 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         const bool conv = o.stop_rule == QPINV_STOP_PAPER_ABS ? d < tol : drel <= tol;
         const double floor_rel = 0x1p-53 * a2est * nx;
         res.status = conv ? QPINV_CONVERGED : drel <= floor_rel ? QPINV_PLATEAU : QPINV_NOT_CONVERGED;
+        if (res.status == QPINV_NOT_CONVERGED && o.stop_rule != QPINV_STOP_PAPER_ABS) {
+          // The last step may have been large only because it corrected the
+          // range error of a projection (rectangular A): judge the returned X
+          // by the step its residual predicts, as in the polish steps above.
+          S.residual(S.X[S.cur], "R", "fab", true);
+          double hr[8];
+          read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 6, hr);
+          const double rn = std::sqrt(hr[4]);
+          if (rn <= tol) res.status = QPINV_CONVERGED;
+          else if (rn <= floor_rel) res.status = QPINV_PLATEAU;
+        }
         break;
       }
       prev_rel = drel;

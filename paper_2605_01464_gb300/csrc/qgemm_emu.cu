@@ -17,9 +17,10 @@
 // add it into an int32 TMEM accumulator of the level (columns 256..511), then
 // release the buffer for the next chunk.  At the end of a level the int32 sum
 // is shifted to the common 64-bit fixed point and added to the global int64
-// accumulator through a shared-memory transpose (coalesced rows).  Global
-// traffic per product is S read-modify-writes of the accumulator instead of
-// one per chunk, and there is a single launch per product.
+// accumulator of its group through a shared-memory transpose (coalesced
+// rows).  Global traffic per product is one read-modify-write of an
+// accumulator per level instead of one per chunk, and there is a single
+// launch per product.
 //
 // int32 range: a level-d sum is bounded by 4K 2^12 (d + 3) (2^14 for d = 0)
 // level units; launch_qgemm_emu refuses K beyond what keeps this below 2^31.

@@ -9,7 +9,8 @@
 //   r=2 -B2   +B3    +B0    -B1
 //   r=3 -B3   -B2    +B1    +B0
 // M(B) is never formed: per K step the kernel stages the four A planes and
-// the four B planes of a tile in shared memory (TMA, 128-byte swizzle) and
+// the four B planes of a tile in shared memory (TMA; 64-byte swizzle for the
+// two-CTA-per-SM shape, 128-byte for the two-accumulator shape) and
 // issues the 16 (r, c) products as separate tcgen05.mma instructions, each
 // reading plane r xor c of B and taking its sign from the instruction
 // descriptor's negate-A bit.  The four output components accumulate in FP32
@@ -20,7 +21,8 @@
 // accurate to about 2^-8 (1 term), 2^-16 (3 pairs) or 2^-24 (6 pairs).
 //
 // Roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and issues
-// the MMAs (one elected lane), warps 2-5 drain TMEM to global memory.
+// the MMAs (one elected lane), warps 2-5 drain TMEM to global memory through
+// a shared-memory transpose (coalesced rows).
 // Every wait is bounded (2 s of globaltimer); on expiry the kernel records
 // an error code, stops issuing work, drains what it started and frees TMEM.
 #include <cuda.h>

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3}
+METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3, "qhpim": 4}
 ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3}
 STOP = {"paper_abs": 0, "rel_plateau": 1}
 STATUS = {0: "converged", 1: "plateau", 2: "not_converged", 3: "diverged"}
@@ -127,12 +127,18 @@ def init_x0(A, alpha_value):
     return _from_q(x)
 
 
-def step(A, X, method="qhpi19", N=5, side="right"):
+def _param(method, N, order):
+    """The C interface's method parameter: QRAPID's N, or QHPIM's order k."""
+    return int(order if method == "qhpim" else N)
+
+
+def step(A, X, method="qhpi19", N=5, side="right", order=19):
     a, x = _to_q(A), _to_q(X)
     m, n = a.shape[:2]
     assert x.shape[:2] == (n, m)
     y = np.zeros((n, m, 4))
-    lib().qo_step(m, n, _ptr(a), _ptr(x), METHODS[method], int(N), int(side == "left"), _ptr(y))
+    lib().qo_step(m, n, _ptr(a), _ptr(x), METHODS[method], _param(method, N, order),
+                  int(side == "left"), _ptr(y))
     return _from_q(y)
 
 
@@ -146,8 +152,9 @@ def penrose(A, X):
 
 
 def solve(A, method="qhpi19", tol=1e-12, max_iter=500, alpha_mode="safe", alpha_user=0.0,
-          stop="rel_plateau", side="right", N=5, x0=None, trace=False):
-    """Runs the chosen iteration to the stop rule.  Returns (X, info)."""
+          stop="rel_plateau", side="right", N=5, x0=None, trace=False, order=19):
+    """Runs the chosen iteration to the stop rule.  Returns (X, info).
+    N: QRAPID's step parameter; order: the order k of QHPIM."""
     a = _to_q(A)
     m, n = a.shape[:2]
     x = np.zeros((n, m, 4))
@@ -157,8 +164,8 @@ def solve(A, method="qhpi19", tol=1e-12, max_iter=500, alpha_mode="safe", alpha_
     if x0 is not None:
         x0q = _to_q(x0)
         x0p = _ptr(x0q)
-    lib().qo_solve(m, n, _ptr(a), METHODS[method], int(N), ALPHA[alpha_mode], float(alpha_user),
-                   STOP[stop], float(tol), int(max_iter), int(side == "left"), x0p, _ptr(x),
+    lib().qo_solve(m, n, _ptr(a), METHODS[method], _param(method, N, order), ALPHA[alpha_mode],
+                   float(alpha_user), STOP[stop], float(tol), int(max_iter), int(side == "left"), x0p, _ptr(x),
                    _ptr(tr), ctypes.byref(res))
     info = dict(status=STATUS[res.status], iters=res.iters, alpha=res.alpha, delta=res.delta,
                 delta_rel=res.delta_rel, E=list(res.E), E_rel=list(res.E_rel), gemms=res.gemms)

@@ -1,6 +1,7 @@
 /*
  * qoracle.c -- plain, slow, FP64 CPU oracle for the quaternion hyperpower
- * pseudoinverse iterations (QRAPID, QSAI, QHPI19, Newton-Schulz).
+ * pseudoinverse iterations (QRAPID, QSAI, QHPI19, Newton-Schulz, and the
+ * unfactorized hyperpower iteration QHPIM of order k).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
  * call this file; only the tests, __graft_entry__.smoke() and the CPU-baseline
@@ -186,7 +187,7 @@ static hpi19_coef hpi19_coefficients(void) {
 
 /* -------- one iteration of each method ---------------------------------- */
 
-enum { M_NS = 0, M_QSAI = 1, M_QRAPID = 2, M_QHPI19 = 3 };
+enum { M_NS = 0, M_QSAI = 1, M_QRAPID = 2, M_QHPI19 = 3, M_QHPIM = 4 };
 
 /* Newton-Schulz (Sec. 1): X_{j+1} = X_j (2I - A X_j); left form (2I - X A) X. */
 static qmat step_ns(const qmat *A, const qmat *X, int left) {
@@ -307,11 +308,39 @@ static qmat step_qrapid(const qmat *A, const qmat *X, int N, int left) {
   return Xn;
 }
 
+/* Unfactorized hyperpower iteration of order k (Definition 1; the
+ * QHONSchultz(k) solvers of Example 3):  R = I - A X,
+ *   X_{j+1} = X (I + R + R^2 + ... + R^{k-1}).
+ * The powers are formed one after another (R^i = R^{i-1} R) and added in
+ * increasing order: k - 2 products for the powers, so k per iteration with
+ * the residual and the update.  Left form: R = I - X A and the sum
+ * multiplies X from the left.  k = 1 (the empty sum I) leaves X unchanged. */
+static qmat step_qhpim(const qmat *A, const qmat *X, int k, int left) {
+  if (g_mutation == 4) k -= 1; /* planted mistake: the highest power is dropped */
+  qmat P = left ? qm_mul(X, A) : qm_mul(A, X);
+  qmat R = qm_comb(-1.0, &P, 0.0, NULL, 1.0);
+  qmat Sum = qm_comb(0.0, &R, 0.0, NULL, 1.0); /* R^0 = I */
+  qmat Pw = qm_comb(0.0, &R, 0.0, NULL, 1.0);
+  for (int i = 1; i < k; i++) {
+    qmat next = i == 1 ? qm_copy(&R) : qm_mul(&Pw, &R);
+    qm_free(&Pw);
+    Pw = next;
+    qmat acc = qm_add(&Sum, &Pw);
+    qm_free(&Sum);
+    Sum = acc;
+  }
+  qmat Xn = left ? qm_mul(&Sum, X) : qm_mul(X, &Sum);
+  qm_free(&P); qm_free(&R); qm_free(&Sum); qm_free(&Pw);
+  return Xn;
+}
+
+/* N: QRAPID's step parameter, or the order k of QHPIM. */
 static qmat method_step(const qmat *A, const qmat *X, int method, int N, int left) {
   switch (method) {
     case M_NS: return step_ns(A, X, left);
     case M_QSAI: return step_qsai(A, X, left);
     case M_QRAPID: return step_qrapid(A, X, N, left);
+    case M_QHPIM: return step_qhpim(A, X, N, left);
     default: return step_qhpi19(A, X, left);
   }
 }

@@ -122,7 +122,10 @@ def residual_map(method, r, N=5):
     Thm. 2 for QRAPID: N = 0: 3/4 r^5 + 1/4 r^6; N = 1: (9 r^8 + 6 r^9 + r^10)/16;
     N >= 3: 4^(-a_{N+2}) (3 + r)^a_{N+2} r^nu_N with nu_N = 11 a_{N-1} + 7 a_{N-2} + 1.
     N = 2 (order 12 in the paper, no closed form printed) uses the N >= 3
-    formula, which at N = 2 gives order 12."""
+    formula, which at N = 2 gives order 12.  QHPIM of order k (Definition 1,
+    N = k): I - (I - R)(I + R + ... + R^(k-1)) = R^k."""
+    if method == "qhpim":
+        return r ** N
     if method == "qhpi19":
         return r ** 19
     if method == "qsai":
@@ -147,7 +150,7 @@ def check_diagonal_recurrence(method, N=5, side="right", tall=0):
     X = oracle.init_x0(A, alpha)
     for _ in range(3):
         r0 = [Fraction(1) - Fraction(float(d[i])) * Fraction(float(X[0, i, i])) for i in range(n)]
-        X = oracle.step(A, X, method, N=N, side=side)
+        X = oracle.step(A, X, method, N=N, side=side, order=N)
         # off-diagonal entries and imaginary planes stay exactly zero
         off = X.copy()
         off[0, np.arange(n), np.arange(n)] = 0
@@ -166,7 +169,7 @@ def check_matrix_recurrence(method, N=5, side="right", seed=11, shape=(9, 6)):
     m, n = shape
     A = I.gaussian_quaternion(m, n, seed)
     X0 = oracle.init_x0(A, oracle.alpha(A, "safe"))
-    X1 = oracle.step(A, X0, method, N=N, side=side)
+    X1 = oracle.step(A, X0, method, N=N, side=side, order=N)
     cA, c0, c1 = I.chi(A), I.chi(X0), I.chi(X1)
     if side == "right":
         R0 = np.eye(2 * m) - cA @ c0
@@ -175,7 +178,9 @@ def check_matrix_recurrence(method, N=5, side="right", seed=11, shape=(9, 6)):
         R0 = np.eye(2 * n) - c0 @ cA
         R1 = np.eye(2 * n) - c1 @ cA
     Id = np.eye(R0.shape[0])
-    if method in ("qhpi19", "qsai", "ns"):
+    if method == "qhpim":  # Definition 1: R_{j+1} = R_j^k
+        want = chi_pow(R0, N)
+    elif method in ("qhpi19", "qsai", "ns"):
         want = chi_pow(R0, {"qhpi19": 19, "qsai": 10, "ns": 2}[method])
     else:
         a = fib(N + 2)
@@ -237,17 +242,43 @@ def test_coefficient_identities():
 
 
 @pytest.mark.parametrize("method,N", [("ns", 0), ("qsai", 0), ("qhpi19", 0)]
-                         + [("qrapid", N) for N in range(6)])
+                         + [("qrapid", N) for N in range(6)]
+                         + [("qhpim", k) for k in (1, 2, 3, 5, 10, 19)])
 @pytest.mark.parametrize("side,tall", [("right", 0), ("left", 0), ("right", 3)])
 def test_diagonal_closed_form_recurrence(method, N, side, tall):
     check_diagonal_recurrence(method, N, side, tall)
 
 
 @pytest.mark.parametrize("method,N", [("ns", 0), ("qsai", 0), ("qhpi19", 0)]
-                         + [("qrapid", N) for N in (0, 1, 3, 5)])
+                         + [("qrapid", N) for N in (0, 1, 3, 5)]
+                         + [("qhpim", k) for k in (2, 3, 7, 10, 19)])
 @pytest.mark.parametrize("side", ["right", "left"])
 def test_matrix_residual_recurrence(method, N, side):
     check_matrix_recurrence(method, N, side)
+
+
+@pytest.mark.parametrize("k,factorized", [(2, "ns"), (10, "qsai"), (19, "qhpi19")])
+@pytest.mark.parametrize("side", ["right", "left"])
+def test_unfactorized_equals_factorized_polynomial(k, factorized, side):
+    # The factorized methods evaluate the same polynomial sum_{i<k} R^i in
+    # fewer products (Sec. 3.2, 3.3, Example 3): Newton-Schulz is k = 2,
+    # QSAI k = 10, QHPI19 k = 19.  Separate code paths, equal iterates.
+    A = I.gaussian_quaternion(10, 7, 41)
+    X = Y = oracle.init_x0(A, oracle.alpha(A, "safe"))
+    for _ in range(3):
+        X = oracle.step(A, X, "qhpim", side=side, order=k)
+        Y = oracle.step(A, Y, factorized, side=side)
+        assert rel(X, Y) <= 1e-13, (k, factorized, rel(X, Y))
+
+
+def test_unfactorized_order_one_is_identity_step():
+    # k = 1: the sum is I, so X_{j+1} = X_j; the stop rule sees a zero step
+    A = I.gaussian_quaternion(6, 5, 42)
+    X0 = oracle.init_x0(A, oracle.alpha(A, "safe"))
+    assert np.array_equal(oracle.step(A, X0, "qhpim", order=1), X0)
+    X, info = oracle.solve(A, "qhpim", order=1, tol=1e-12, max_iter=5)
+    assert info["status"] == "converged" and info["iters"] == 1 and info["delta"] == 0.0
+    assert np.array_equal(X, X0)
 
 
 @pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19"])
@@ -261,23 +292,25 @@ def test_left_and_right_forms_agree(method):
         assert rel(X, Y) <= 1e-12
 
 
-@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19"])
+@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19", "qhpim"])
 def test_gemm_counts_per_iteration(method):
     A = I.gaussian_quaternion(6, 5, 2)
     X = oracle.init_x0(A, oracle.alpha(A, "safe"))
-    for N in ([0, 1, 5] if method == "qrapid" else [0]):
+    Ns = {"qrapid": [0, 1, 5], "qhpim": [2, 3, 10, 19]}.get(method, [0])
+    for N in Ns:
         g0 = oracle.gemm_count()
-        oracle.step(A, X, method, N=N)
-        want = {"ns": 2, "qsai": 6, "qhpi19": 7}.get(method, 8 + 2 * N)
+        oracle.step(A, X, method, N=N, order=N)
+        # QHPIM(k): residual, k - 2 powers, update (Example 3: O(k n^3) per step)
+        want = {"ns": 2, "qsai": 6, "qhpi19": 7, "qhpim": N}.get(method, 8 + 2 * N)
         assert oracle.gemm_count() - g0 == want
 
 
-@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19"])
+@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19", "qhpim"])
 @pytest.mark.parametrize("shape", [(12, 7), (7, 12)])
 def test_full_rank_closed_forms(method, shape):
     m, n = shape
     A = I.gaussian_quaternion(m, n, 31)
-    X, info = oracle.solve(A, method, tol=1e-14, max_iter=200)
+    X, info = oracle.solve(A, method, tol=1e-14, max_iter=200, order=5)
     assert info["status"] in ("converged", "plateau")
     C = I.chi(A)
     if m > n:  # full column rank: (A^H A)^{-1} A^H
@@ -310,7 +343,7 @@ def test_quaternion_diagonal_reciprocal():
 
 
 @pytest.mark.parametrize("method,tol_x", [("ns", 1e-10), ("qsai", 1e-10), ("qhpi19", 1e-10),
-                                          ("qrapid", 1e-9)])
+                                          ("qrapid", 1e-9), ("qhpim", 1e-10)])
 @pytest.mark.parametrize("side", ["right", "left"])
 def test_rank_deficient_matches_lapack_pinv(method, tol_x, side):
     A, QL, s, QR = I.rank_deficient(20, 14, 6, 1e-2, seed_l=8, seed_r=9)
@@ -323,7 +356,7 @@ def test_rank_deficient_matches_lapack_pinv(method, tol_x, side):
     assert info["E_rel"][0] <= 1e-12
 
 
-@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19"])
+@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19", "qhpim"])
 def test_proposition1_invariants(method):
     A, QL, s, QR = I.rank_deficient(11, 9, 5, 1e-1, seed_l=12, seed_r=13)
     C = I.chi(A)
@@ -342,12 +375,12 @@ def test_proposition1_invariants(method):
 
 def test_convergence_order_measured():
     # scalar case: log r_{j+1} / log r_j equals the order for every method
-    for method, p in [("ns", 2), ("qsai", 10), ("qhpi19", 19)]:
+    for method, p in [("ns", 2), ("qsai", 10), ("qhpi19", 19), ("qhpim", 7), ("qhpim", 12)]:
         A = np.zeros((4, 1, 1))
         A[0, 0, 0] = 1.0
         X = oracle.init_x0(A, 0.5)
         r0 = 1 - X[0, 0, 0]
-        X = oracle.step(A, X, method)
+        X = oracle.step(A, X, method, order=p)
         r1 = 1 - X[0, 0, 0]
         assert math.isclose(math.log(r1) / math.log(r0), p, rel_tol=1e-9)
 
@@ -377,7 +410,9 @@ def test_warm_start_resume_is_bitwise():
     (1, check_hamilton), (1, check_matmul_chi), (2, check_adjoint_chi),
     (2, lambda: check_example1("qsai", 1)), (3, check_coefficients),
     (3, lambda: check_matrix_recurrence("qhpi19")),
-    (3, lambda: check_diagonal_recurrence("qhpi19"))])
+    (3, lambda: check_diagonal_recurrence("qhpi19")),
+    (4, lambda: check_matrix_recurrence("qhpim", 5)),
+    (4, lambda: check_diagonal_recurrence("qhpim", 7))])
 def test_planted_mistakes_are_caught(mutation, check):
     oracle.set_mutation(mutation)
     try:

@@ -234,13 +234,13 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     return 0
 
 
-def _timed_solve(ctx, torch, A, method, tol):
+def _timed_solve(ctx, torch, A, method, tol, max_iter=500):
     """One solve on the current stream, timed with CUDA events."""
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    _, info = ctx.solve(A, method, tol=tol, max_iter=500, stream=stream)
+    _, info = ctx.solve(A, method, tol=tol, max_iter=max_iter, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), info
@@ -279,6 +279,71 @@ def bench_rankdef(args, torch, qpinv):
                                "(4096 side); EMU precision; rel. tol %g with plateau stop" % args.tol,
                    "l2": "inputs exceed L2"},
         "roofline": q["roofline"][0], "result": out, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
+# Example 3's table (n = 800, CPU seconds): QHPI19 6.188, QSAI 6.594,
+# QHONSchultz(19) 13.87, QHONSchultz(10) 11.05.
+PAPER_EX3_SECONDS = {"qhpi19": 6.188, "qsai": 6.594, "qhpim19": 13.87, "qhpim10": 11.05}
+
+
+def bench_hyper(args, torch, qpinv):
+    """Example 3: factorized (QHPI19, QSAI) against unfactorized hyperpower
+    iterations (QHPIM of order 19 and 10, the example's QHONSchultz) on n x n
+    Gaussian quaternion matrices (every component N(0, 1), seed 0), stop at
+    ||X_{j+1} - X_j||_F <= 1e-10 as in the example; n = 800 with its fixed
+    alpha = 7.8798e-5, n = 2048 with alpha = 1 / sigma_1^2 (power iteration,
+    outside the timed region).  Mixed precision, and at n = 800 also every
+    product FP64-accurate (EMU, the counterpart of the example's FP64
+    arithmetic, where all products cost the same).  One step = one solve of
+    each solver; the line's value is QHPIM(19) at n = 800, mixed precision."""
+    from paper_2605_01464_gb300 import inputs
+    solvers = (("qhpi19", "qhpi19", 19), ("qsai", "qsai", 10), ("qhpim19", "qhpim", 19), ("qhpim10", "qhpim", 10))
+    out, roof = {}, None
+    with ClockSampler(0) as clk:
+        for n, precision, key in ((800, "mixed", "800"), (800, "emu", "800_emu"), (2048, "mixed", "2048")):
+            A = torch.from_numpy(inputs.gaussian_quaternion(n, n, 0)).cuda()
+            ctx = qpinv.Context(0, precision=precision, stop="paper_abs", profile=True)
+            if n == 800:
+                ctx.configure(alpha="user", alpha_user=7.8798e-5)
+            else:
+                ctx.configure(alpha="spectral")
+                _, info = ctx.solve(A, "ns", tol=1.0, max_iter=1)
+                ctx.configure(alpha="user", alpha_user=info["alpha"])
+            res = {}
+            for name, method, k in solvers:
+                ctx.configure(hyper_order=k)
+                for _ in range(args.warmup):
+                    _timed_solve(ctx, torch, A, method, 1e-10, max_iter=100)
+                ctx.reset_stats()
+                times = []
+                for _ in range(args.steps):
+                    ms, info = _timed_solve(ctx, torch, A, method, 1e-10, max_iter=100)
+                    times.append(ms)
+                st = ctx.stats()
+                res[name] = {"ms_per_solve": statistics.mean(times), "iters": info["iters"],
+                             "status": info["status"], "E": info["E"], "gemms": info["gemms"],
+                             "alpha": info["alpha"], "gpu_launches": st["kernel_launches"] // args.steps}
+                if key == "800" and name == "qhpim19":
+                    roof = kernel_rooflines(st)[0]
+            res["time_ratio_order19"] = res["qhpim19"]["ms_per_solve"] / res["qhpi19"]["ms_per_solve"]
+            res["time_ratio_order10"] = res["qhpim10"]["ms_per_solve"] / res["qsai"]["ms_per_solve"]
+            out[key] = res
+            ctx.close()
+    paper = {"time_ratio_order19": PAPER_EX3_SECONDS["qhpim19"] / PAPER_EX3_SECONDS["qhpi19"],
+             "time_ratio_order10": PAPER_EX3_SECONDS["qhpim10"] / PAPER_EX3_SECONDS["qsai"],
+             "iters": {"qhpi19": 8, "qsai": 10, "qhpim19": 8, "qhpim10": 10}}
+    q = out["800"]["qhpim19"]
+    print(json.dumps({
+        "metric": "unfactorized hyperpower QHONSchultz(19) solves/s (Example 3)", "value": 1e3 / q["ms_per_solve"],
+        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q["ms_per_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split/exact-slice (mixed)",
+        "data": "synthetic",
+        "config": {"workload": "n x n Gaussian quaternion matrices (components N(0,1), seed 0), n = 800 (alpha "
+                               "7.8798e-5) and 2048 (alpha = 1/sigma_1^2); QHPI19, QSAI, QHPIM(19), QHPIM(10); "
+                               "mixed precision (and EMU at n = 800); stop ||X_{j+1} - X_j||_F <= 1e-10",
+                   "l2": "inputs of 20 MB (n = 800) fit in L2; no flush between solves"},
+        "roofline": roof, "result": out, "paper_example3": paper, "clocks": clk.summary()}), flush=True)
     return 0
 
 
@@ -408,7 +473,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048)
-    ap.add_argument("--method", default="qhpi19", choices=["ns", "qsai", "qrapid", "qhpi19"])
+    ap.add_argument("--method", default="qhpi19", choices=["ns", "qsai", "qrapid", "qhpi19", "qhpim"])
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--polish", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -418,10 +483,10 @@ def main():
     ap.add_argument("--split", type=int, default=1,
                     help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
     ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "rankdef", "learned"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "rankdef", "learned", "hyper"],
                     help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "
                          "rankdef: rank-2048 8192x4096 (QHPI19 and NS, EMU); learned: learned-alpha training "
-                         "and held-out evaluation")
+                         "and held-out evaluation; hyper: factorized vs unfactorized hyperpower (Example 3)")
     ap.add_argument("--train-count", type=int, default=1500, help="--workload learned: training matrices")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
@@ -449,6 +514,8 @@ def main():
         return bench_rankdef(args, torch, qpinv)
     if args.workload == "learned":
         return bench_learned(args, torch, qpinv)
+    if args.workload == "hyper":
+        return bench_hyper(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist

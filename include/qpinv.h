@@ -55,12 +55,16 @@ extern "C" {
 #define QPINV_NOALLOC_MAX_DIM 256
 
 /* ---- solver outcome (qpinv_result.status) ----------------------------- */
-#define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1} */
+#define QPINV_CONVERGED 0     /* stop rule met; X is X_{j+1}.  In MIXED's polish phase also when the
+                                 residual R of the returned X bounds the next step below tol:
+                                 ||R||_F <= tol (relative rule) or ||X||_F r / (1 - r) < tol,
+                                 r = ||R||_F (absolute rule) */
 #define QPINV_PLATEAU 1       /* rounding floor reached: the relative step stopped decreasing after
                                  falling below 1e-3 (X is the iterate before that step), or, in
                                  MIXED's polish phase, the step (or the residual of X, which bounds
                                  the next step) is below 2^-53 sqrt(||A||_1 ||A||_inf) ||X||_F */
-#define QPINV_NOT_CONVERGED 2 /* max_iter updates done; X is the last iterate */
+#define QPINV_NOT_CONVERGED 2 /* max_iter updates (or MIXED's polish iterations) done without the
+                                 above; X is the last iterate */
 #define QPINV_DIVERGED 3      /* a non-finite iterate appeared; X is the last finite iterate */
 #define QPINV_NONFINITE_INPUT 4 /* qpinv_solve_batched: this A holds NaN/Inf; its X is left untouched */
 
@@ -69,7 +73,10 @@ typedef enum {
   QPINV_NS = 0,     /* Newton-Schulz, order 2, 2 products per iteration (Sec. 1) */
   QPINV_QSAI = 1,   /* Algorithm 2, order 10, 6 products per iteration */
   QPINV_QRAPID = 2, /* Algorithm 1 with step parameter N, 8+2N products per iteration */
-  QPINV_QHPI19 = 3  /* Algorithm 3, order 19, 7 products per iteration */
+  QPINV_QHPI19 = 3, /* Algorithm 3, order 19, 7 products per iteration */
+  QPINV_QHPIM = 4   /* unfactorized hyperpower iteration of order k = hyper_order (Definition 1;
+                       QHONSchultz(k) of Example 3): X_{j+1} = X_j (I + R + ... + R^{k-1}),
+                       the sum by Horner's rule, k products per iteration */
 } qpinv_method;
 
 /* ---- options --------------------------------------------------------- */
@@ -124,6 +131,8 @@ typedef struct {
   int batched_tile;  /* qpinv_solve_batched CTA GEMM tile: -1 = autotune (default; each batch
                         signature is timed once per context on a sample of its matrices),
                         0 = 16x16, 1 = 32x32, 2 = 64x32, 3 = 32x64, 4 = 64x64 */
+  int hyper_order;   /* QPINV_QHPIM order k, 2..64 (default 19; k = 2 is Newton-Schulz, and
+                        k = 1, X_{j+1} = X_j, makes no progress and is rejected) */
 } qpinv_options;
 
 typedef struct {

@@ -134,7 +134,7 @@ struct BatchParams {
   BatchResult* results;
   dfv* ws;
   long slot_elems;
-  int method, qrapid_N, stop_rule, max_iter, alpha_mode;
+  int method, mparam, stop_rule, max_iter, alpha_mode;  // mparam: QRAPID's N or QHPIM's order k
   double tol, alpha_user;
   double k[12];  // QHPI19 coefficients a1 a2 a3 b1 b2 c1 c2 d1 d2 d3 e1 e2
 };
@@ -467,13 +467,31 @@ struct Solve {
     apply(X[cur], t, X[cur], Z[0], false);       // U
     rapid_correct(Z[0], X[cur], Z[1], false);    // V
     int y = 0, w = 1;
-    for (int it = 1; it <= c.P->qrapid_N; it++) {
+    for (int it = 1; it <= c.P->mparam; it++) {
       const int z = 3 - y - w;
       rapid_correct(Z[w], Z[y], Z[z], false);
       y = w;
       w = z;
     }
     rapid_correct(Z[w], X[cur], X[cur ^ 1], true);
+  }
+
+  // Unfactorized hyperpower iteration of order k (Definition 1): X + X t
+  // with t = R + R^2 + ... + R^(k-1) by Horner's rule h <- R + R h from h = R.
+  __device__ void step_qhpim() {
+    const int s = c.s, k = c.P->mparam;
+    const DM R = c.buf(B_R, s, s);
+    const DM H[2] = {c.buf(B_U, s, s), c.buf(B_V, s, s)};
+    residual(X[cur], R);
+    const DM* h = &R;
+    for (int i = 2; i < k; i++) {
+      Epi e;  // h <- R h + R
+      e.aux[0] = &R;
+      e.ct[0] = dc(1.0);
+      gemm(R, *h, H[i & 1], e);
+      h = &H[i & 1];
+    }
+    apply(X[cur], *h, X[cur], X[cur ^ 1], true);
   }
 };
 
@@ -582,6 +600,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_batched(BatchParams P) {
           case QPINV_NS: S.step_ns(); break;
           case QPINV_QSAI: S.step_qsai(); break;
           case QPINV_QRAPID: S.step_qrapid(); break;
+          case QPINV_QHPIM: S.step_qhpim(); break;
           default: S.step_qhpi19(); break;
         }
         const double d = sqrt(S.nd), xn = sqrt(S.nx);
@@ -694,7 +713,7 @@ int batched_slots_per_sm(int tile) {
 // on `st` -- or, with `graph`, on the graph's own stream as one replayed CUDA
 // graph (captured again whenever the launch shape changes).
 cudaError_t run_batched(int batch, const int* m, const int* n, const double* const* A, const long* lda,
-                        double* const* X, const long* ldx, int method, double tol, int max_iter, int qrapid_N,
+                        double* const* X, const long* ldx, int method, double tol, int max_iter, int mparam,
                         int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, const BatchRun& r,
                         BatchGraph* graph, std::vector<BatchResultHost>& out, cudaStream_t st) {
   BatchItem* items = static_cast<BatchItem*>(r.host_items);
@@ -724,7 +743,7 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
   P.ws = (dfv*)r.ws;
   P.slot_elems = (long)NBUF * 4 * MAXD * MAXD;
   P.method = method;
-  P.qrapid_N = qrapid_N;
+  P.mparam = mparam;
   P.stop_rule = stop_rule;
   P.max_iter = max_iter;
   P.alpha_mode = alpha_mode;
@@ -757,7 +776,7 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
                                         (unsigned long long)(uintptr_t)r.host_items,
                                         (unsigned long long)(uintptr_t)r.host_results,
                                         (unsigned long long)method, (unsigned long long)max_iter,
-                                        (unsigned long long)qrapid_N, (unsigned long long)stop_rule,
+                                        (unsigned long long)mparam, (unsigned long long)stop_rule,
                                         (unsigned long long)alpha_mode};
     for (unsigned long long v : parts) key = mix(key, v);
     unsigned long long tb, ab;

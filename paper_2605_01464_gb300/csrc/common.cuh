@@ -188,7 +188,7 @@ struct BatchGraph {
   int replays = 0;
 };
 cudaError_t run_batched(int batch, const int* m, const int* n, const double* const* A, const long* lda,
-                        double* const* X, const long* ldx, int method, double tol, int max_iter, int qrapid_N,
+                        double* const* X, const long* ldx, int method, double tol, int max_iter, int mparam,
                         int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, const BatchRun& r,
                         BatchGraph* graph, std::vector<BatchResultHost>& out, cudaStream_t st);
 size_t batched_slot_bytes();

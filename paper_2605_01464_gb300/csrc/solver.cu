@@ -16,6 +16,8 @@
 //   QRAPID (Alg. 1): U = X (13I - P(15I - P(7I - P)))/4 = X + X (R + R2 + R3/4)
 //     (P = I - R); V = U + X(I - AU); Z_l = W + Y(I - AW); X_{j+1} = Z + X(I - AZ).
 //     8 + 2N products.
+//   QHPIM(k) (Definition 1, unfactorized): X (I + R + ... + R^(k-1)) = X + X t,
+//     t by Horner's rule h <- R + R h from h = R.  k products.
 // Side: the paper's right form (R = I_m - A X, m x m) or the left form
 // (R = I_n - X A, X_{j+1} = p(R) X), identical in exact arithmetic since
 // X (AX)^k = (XA)^k X; AUTO picks the smaller residual.
@@ -723,6 +725,27 @@ struct Solver {
     update(X[cur], xt);
   }
 
+  // Unfactorized hyperpower iteration of order k (Definition 1):
+  // X_{j+1} = X (I + R + ... + R^(k-1)) = X + X t, t = R + R^2 + ... + R^(k-1)
+  // by Horner's rule h <- R + R h from h = R: k - 2 R-products, then the
+  // update; k products per iteration with the residual.
+  void step_qhpim(int k) {
+    QMat R = residual(X[cur], "R", k == 2 ? tform() : "fab", true);
+    QMat H[2] = {sq("h0", true, true), sq("h1", true, true)};
+    const QMat* h = &R;
+    for (int i = 2; i < k; i++) {
+      Acc acc = rprod(R, *h);
+      QMat& hn = H[i & 1];
+      CombineArgs a = base_args(s, s, &acc);
+      aux(a, 0, R);
+      out(a, hn, i == k - 1 ? tform() : "fb", 1.0).caux[0] = 1.0;
+      run(a);
+      h = &hn;
+    }
+    Acc xt = apply(X[cur], *h);
+    update(X[cur], xt);
+  }
+
   // QRAPID correction  W + Y (I - A W)  (right) / W + (I - W A) Y (left) into Z.
   void rapid_correct(const QMat& W, const QMat& Y, QMat& Z, bool is_final) {
     QMat E = residual(W, "E", tform());
@@ -1022,6 +1045,7 @@ void qpinv_default_options(qpinv_options* o) {
   o->penrose = 1;
   o->profile = 0;
   o->batched_tile = -1;
+  o->hyper_order = 19;
 }
 
 static int check_opts(const qpinv_options* o) {
@@ -1033,6 +1057,7 @@ static int check_opts(const qpinv_options* o) {
   if (o->qrapid_N < 0 || o->qrapid_N > 30) return 0;
   if (o->side < 0 || o->side > 2 || o->stop_rule < 0 || o->stop_rule > 1) return 0;
   if (o->batched_tile < -1 || o->batched_tile >= qp::BATCH_TILES) return 0;
+  if (o->hyper_order < 2 || o->hyper_order > 64) return 0;
   return 1;
 }
 
@@ -1116,7 +1141,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
                 double tol, int max_iter, double* const X[4], long ldx, qpinv_result* out) {
   if (!c) return QPINV_E_INVALID;
   if (m <= 0 || n <= 0 || lda < n || ldx < m || !planes_ok(A) || !planes_ok((const double* const*)X) ||
-      max_iter < 1 || !(tol >= 0.0) || (int)method < 0 || (int)method > 3)
+      max_iter < 1 || !(tol >= 0.0) || (int)method < 0 || (int)method > 4)
     return fail(c, QPINV_E_INVALID, "invalid argument");
   const auto t_start = std::chrono::steady_clock::now();
   DeviceGuard g(c->device);
@@ -1310,6 +1335,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         case QPINV_NS: S.step_ns(); break;
         case QPINV_QSAI: S.step_qsai((1.0 + std::sqrt(5.0)) / 2.0, (1.0 - std::sqrt(5.0)) / 2.0); break;
         case QPINV_QRAPID: S.step_qrapid(o.qrapid_N); break;
+        case QPINV_QHPIM: S.step_qhpim(o.hyper_order); break;
         default: S.step_qhpi19(hpi19_k); break;
       }
       if (!fp64) check_kernel_error(c);
@@ -1376,6 +1402,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         const double order = method == QPINV_NS      ? 2.0
                              : method == QPINV_QSAI  ? 10.0
                              : method == QPINV_QRAPID ? 5.0
+                             : method == QPINV_QHPIM  ? (double)o.hyper_order
                                                       : 19.0;
         const double expo = std::pow(order, 1.0 + o.polish_iters);
         const double lim = std::pow(1e-20, 1.0 / expo);  // largest ||R_j|| that qualifies
@@ -1403,15 +1430,21 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         const bool conv = o.stop_rule == QPINV_STOP_PAPER_ABS ? d < tol : drel <= tol;
         const double floor_rel = 0x1p-53 * a2est * nx;
         res.status = conv ? QPINV_CONVERGED : drel <= floor_rel ? QPINV_PLATEAU : QPINV_NOT_CONVERGED;
-        if (res.status == QPINV_NOT_CONVERGED && o.stop_rule != QPINV_STOP_PAPER_ABS) {
+        if (res.status == QPINV_NOT_CONVERGED) {
           // The last step may have been large only because it corrected the
-          // range error of a projection (rectangular A): judge the returned X
-          // by the step its residual predicts, as in the polish steps above.
+          // range error of a projection (rectangular A) or the R-product
+          // rounding of the first polish step: judge the returned X by the
+          // step its residual predicts, as in the polish steps above.  The
+          // absolute rule uses the bound ||X t||_F <= ||X||_F r / (1 - r),
+          // r = ||R||_F, t = R + R^2 + ... (every method's t is a polynomial
+          // in R of this kind with coefficients at most 1 in modulus).
           S.residual(S.X[S.cur], "R", "fab", true);
           double hr[8];
           read_back(c, (const double*)buf(c, "red", sizeof(double) * 8), 6, hr);
           const double rn = std::sqrt(hr[4]);
-          if (rn <= tol) res.status = QPINV_CONVERGED;
+          const bool next_ok = o.stop_rule == QPINV_STOP_PAPER_ABS ? rn < 1.0 && nx * rn / (1.0 - rn) < tol
+                                                                   : rn <= tol;
+          if (next_ok) res.status = QPINV_CONVERGED;
           else if (rn <= floor_rel) res.status = QPINV_PLATEAU;
         }
         break;
@@ -1529,7 +1562,7 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
                         const long* ldx, qpinv_result* out) {
   if (!c) return QPINV_E_INVALID;
   if (batch < 1 || !m || !n || !A || !X || !lda || !ldx || max_iter < 1 || !(tol >= 0.0) || (int)method < 0 ||
-      (int)method > 3)
+      (int)method > 4)
     return fail(c, QPINV_E_INVALID, "invalid argument");
   const int maxd = batched_max_dim();
   for (int b = 0; b < batch; b++) {
@@ -1572,11 +1605,12 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
     const int amode = c->opt.alpha_mode == QPINV_ALPHA_USER ? QPINV_ALPHA_USER
                       : c->opt.alpha_mode == QPINV_ALPHA_FRO ? QPINV_ALPHA_FRO
                                                               : QPINV_ALPHA_SAFE;
+    const int mparam = method == QPINV_QHPIM ? c->opt.hyper_order : c->opt.qrapid_N;
     auto solve_with = [&](int tile, int cnt, const int* mm, const int* nn, const double* const* AA,
                           const long* la, double* const* XX, const long* lx, BatchGraph* graph, int iters) {
       run.tile = tile;
       run.slots = std::min(cnt, nsm * batched_slots_per_sm(tile));
-      ck(c, run_batched(cnt, mm, nn, AA, la, XX, lx, (int)method, tol, iters, c->opt.qrapid_N, c->opt.stop_rule,
+      ck(c, run_batched(cnt, mm, nn, AA, la, XX, lx, (int)method, tol, iters, mparam, c->opt.stop_rule,
                         amode, c->opt.alpha_user, hpi19_k, run, graph, res, c->st),
          "batched solve");
     };
@@ -1585,7 +1619,8 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
       // Autotuner: a batch signature (method, count, shape histogram) maps to
       // the tile that ran three iterations on an evenly spaced sample of its
       // matrices (one per SM) fastest.
-      unsigned long long sig = 0x51ED270B27A5B49Dull ^ ((unsigned long long)method << 40) ^ (unsigned long long)batch;
+      unsigned long long sig = 0x51ED270B27A5B49Dull ^ ((unsigned long long)method << 40) ^
+                               ((unsigned long long)mparam << 48) ^ (unsigned long long)batch;
       int hist[16] = {0};
       for (int b = 0; b < batch; b++) hist[(std::max(m[b], n[b]) - 1) / 16]++;
       for (int t = 0; t < 16; t++) sig = (sig ^ (unsigned long long)hist[t]) * 0x100000001B3ull;

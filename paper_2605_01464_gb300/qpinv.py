@@ -19,7 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqpinv.so")
 
-METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3}
+METHODS = {"ns": 0, "qsai": 1, "qrapid": 2, "qhpi19": 3, "qhpim": 4}
 PRECISION = {"fp64": 0, "mixed": 1, "tc": 2, "emu": 3}
 PRECISION_NAME = {0: "fp64", 1: "mixed", 2: "tc", 3: "emu", 4: "df32"}
 ALPHA = {"safe": 0, "spectral": 1, "fro": 2, "user": 3, "learned": 4}
@@ -35,7 +35,7 @@ class qpinv_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("split_level", ctypes.c_int), ("polish_iters", ctypes.c_int),
                 ("alpha_mode", ctypes.c_int), ("alpha_user", ctypes.c_double), ("qrapid_N", ctypes.c_int),
                 ("side", ctypes.c_int), ("stop_rule", ctypes.c_int), ("penrose", ctypes.c_int),
-                ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int), ("hyper_order", ctypes.c_int)]
 
 
 class qpinv_result(ctypes.Structure):
@@ -195,17 +195,17 @@ class Context:
 
     def __init__(self, device=0, precision="mixed", split_level=0, polish_iters=2, alpha="safe",
                  alpha_user=0.0, qrapid_N=5, side="auto", stop="rel_plateau", penrose=True, profile=False,
-                 batched_tile=-1):
+                 batched_tile=-1, hyper_order=19):
         self.options = qpinv_default_options()
         self.device = device
         self.configure(precision=precision, split_level=split_level, polish_iters=polish_iters, alpha=alpha,
                        alpha_user=alpha_user, qrapid_N=qrapid_N, side=side, stop=stop, penrose=penrose,
-                       profile=profile, batched_tile=batched_tile, _apply=False)
+                       profile=profile, batched_tile=batched_tile, hyper_order=hyper_order, _apply=False)
         self.h = qpinv_init(device, self.options)
 
     def configure(self, precision=None, split_level=None, polish_iters=None, alpha=None, alpha_user=None,
                   qrapid_N=None, side=None, stop=None, penrose=None, profile=None, batched_tile=None,
-                  _apply=True):
+                  hyper_order=None, _apply=True):
         o = self.options
         if precision is not None: o.precision = PRECISION[precision]
         if split_level is not None: o.split_level = int(split_level)
@@ -218,6 +218,7 @@ class Context:
         if penrose is not None: o.penrose = int(bool(penrose))
         if profile is not None: o.profile = int(bool(profile))
         if batched_tile is not None: o.batched_tile = int(batched_tile)
+        if hyper_order is not None: o.hyper_order = int(hyper_order)
         if _apply:
             _check(self.h, lib().qpinv_set_options(self.h, ctypes.byref(o)), "qpinv_set_options")
 

@@ -36,6 +36,8 @@ def test_default_options():
     o = qpinv.qpinv_default_options()
     assert o.precision == 1 and o.polish_iters == 2 and o.qrapid_N == 5 and o.penrose == 1
     assert o.alpha_mode == 0 and o.side == 0 and o.stop_rule == 1
+    # the trailing fields pin the ctypes mirror of the struct layout
+    assert o.batched_tile == -1 and o.hyper_order == 19
 
 
 def test_null_context_is_rejected_without_cuda():

@@ -168,3 +168,53 @@ def pure_quaternion_batch(count: int = 4096, seed: int = 3, lo: int = 16, hi: in
         A[1:] = Bx @ W
         mats.append(A)
     return mats
+
+
+# ------------------------------------------------------- image completion
+
+def synthetic_rgb_image(m: int = 512, n: int = 768, seed: int = 16, texture: float = 0.02) -> np.ndarray:
+    """Smooth synthetic colour image as a pure quaternion matrix (zero real
+    plane; planes x, y, z = R, G, B in [0, 1]), standing in for a natural
+    photograph such as kodim16 (512 x 768).  Channel c: 24 plane waves of
+    random orientation with up to 6 cycles across the frame and amplitudes
+    falling as 1 / (1 + frequency), plus 8 Gaussian blobs (width 3-15 % of
+    the frame), scaled into [0.1, 0.9]; then N(0, texture^2) pixel texture;
+    clipped to [0, 1].  Channel c draws from stream `seed` at offset c << 32."""
+    y = (np.arange(m, dtype=np.float64)[:, None] + 0.5) / m
+    x = (np.arange(n, dtype=np.float64)[None, :] + 0.5) / n
+    img = np.zeros((4, m, n))
+    for c in range(3):
+        off = c << 32
+        w = uniform(seed, 4 * 24, off).reshape(24, 4)
+        b = uniform(seed, 5 * 8, off + 96).reshape(8, 5)
+        f = np.zeros((m, n))
+        for fy, fx, ph, amp in w:
+            ky, kx = (fy - 0.5) * 12.0, (fx - 0.5) * 12.0
+            f += amp / (1.0 + math.hypot(ky, kx)) * np.cos(2.0 * math.pi * (ky * y + kx * x + ph))
+        for cy, cx, wd, amp, sgn in b:
+            s = 0.03 + 0.12 * wd
+            f += (2.0 * amp) * (1.0 if sgn < 0.5 else -1.0) * np.exp(-((y - cy) ** 2 + (x - cx) ** 2) / (2 * s * s))
+        f = 0.1 + 0.8 * (f - f.min()) / max(f.max() - f.min(), 1e-300)
+        f += texture * normal(seed, m * n, off + 256).reshape(m, n)
+        img[1 + c] = np.clip(f, 0.0, 1.0)
+    return img
+
+
+def completion_mask(m: int, n: int, observed: float = 0.3, seed: int = 17) -> np.ndarray:
+    """(m, n) uint8 mask, 1 = observed pixel, each independently with
+    probability `observed` (0.3: 70 % of the pixels removed)."""
+    return (uniform(seed, m * n).reshape(m, n) < observed).astype(np.uint8)
+
+
+def cur_index_sets(m: int, n: int, r: int, iters: int, seed: int = 18):
+    """Row and column index sets of a rank-r cross approximation for each of
+    `iters` completion iterations: (iters, r) int32 arrays I and J, each row
+    r distinct indices drawn uniformly without replacement (the first r of a
+    random permutation), sorted ascending.  Iteration t uses stream `seed`
+    at offsets t << 33 (rows) and (t << 33) + (1 << 32) (columns)."""
+    I = np.empty((iters, r), dtype=np.int32)
+    J = np.empty((iters, r), dtype=np.int32)
+    for t in range(iters):
+        I[t] = np.sort(np.argsort(uniform(seed, m, t << 33), kind="stable")[:r])
+        J[t] = np.sort(np.argsort(uniform(seed, n, (t << 33) + (1 << 32)), kind="stable")[:r])
+    return I, J

@@ -262,6 +262,44 @@ int qpinv_alpha_gradient(qpinv_ctx* ctx, void* stream, int count, const float* f
 /* Reads (set = 0) or loads (set = 1) the QPINV_ALPHA_NWEIGHTS weight block (host). */
 int qpinv_alpha_weights(qpinv_ctx* ctx, float* w, int count, int set);
 
+/* ---- application: CUR image completion (Sec. 5.1) ----------------------
+ * Impute-reconstruct loop (eq. (update)): C^(0) = Omega . M (unobserved
+ * pixels 0); for t = 0 .. iters-1:
+ *   C_J = C^(t)(:, J_t), R_I = C^(t)(I_t, :);
+ *   U = C_J^dagger C^(t) R_I^dagger   (form 0: eq. (Uopt), A read as the
+ *                                      current filled matrix), or
+ *   U = W^dagger, W = C^(t)(I_t, J_t) (form 1: the cross form, eq. (Ucross));
+ *   X^(t) = (C_J U) R_I, then, if sigma > 0, the 2-D Gaussian filter of
+ *   standard deviation sigma on every plane (sampled on |x| <= ceil(2 sigma),
+ *   normalised, replicated borders);
+ *   C^(t+1) = Omega . M + (1 - Omega) . X^(t).
+ * Each pseudoinverse is a qpinv_solve with the context's options (method,
+ * tol, max_iter as given); the products are FP64-accurate (exact-slice
+ * tensor-core GEMMs; CUDA-core FP64 when the context's precision is FP64).
+ *   - M: four planes of the m x n image (colour images: zero real plane,
+ *     R, G, B in x, y, z), ldm >= n; values at unobserved pixels are ignored.
+ *     mask: m x n bytes, nonzero = observed, row stride ldmask >= n.  Device
+ *     or host pointers.
+ *   - r in [1, min(m, n)]; I, J: HOST arrays of iters x r row / column
+ *     indices (0-based; row t holds the sets of iteration t).
+ *   - C: four planes (device or host, ldc >= n) receive C^(iters).
+ *   - out (host, may be NULL): summary of the pseudoinverse solves.
+ *   - Errors: QPINV_E_INVALID for bad sizes, strides, indices, form, method,
+ *     or sigma outside [0, 8]; errors of the inner solves are returned as is
+ *     (their message prefixed "pseudoinverse:"). */
+typedef struct {
+  int pinv_solves;        /* pseudoinverse solves run (2 per iteration, 1 with the cross form) */
+  int pinv_iters;         /* their iterations, summed */
+  int pinv_worst_status;  /* largest qpinv_result.status among them */
+  double pinv_max_E1_rel; /* largest E1/||.||_F among them */
+  double time_ms;         /* wall time of the call */
+} qpinv_cur_result;
+
+int qpinv_cur_complete(qpinv_ctx* ctx, void* stream, int m, int n, const double* const M[4], long ldm,
+                       const unsigned char* mask, long ldmask, int r, int iters, const int* I, const int* J,
+                       int form, qpinv_method method, double tol, int max_iter, double sigma,
+                       double* const C[4], long ldc, qpinv_cur_result* out);
+
 /* ---- building blocks, exposed for tests and measurement ---------------- */
 
 /* C = A B for quaternion matrices (Hamilton product, Sec. 2): A is m x k

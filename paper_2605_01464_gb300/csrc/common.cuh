@@ -212,4 +212,25 @@ size_t batched_result_bytes();
 int batched_max_dim();
 int batched_slots_per_sm(int tile);
 
+// CUR image completion (cur.cu): the data-consistency fill, the gather of the
+// CUR factors and the Gaussian filter, on contiguous planes (ps = m * n).
+struct CurFill {
+  const double* M[4] = {nullptr, nullptr, nullptr, nullptr};  // observed planes, row stride ldm
+  long ldm = 0;
+  const unsigned char* mask = nullptr;  // nonzero = observed, row stride ldk
+  long ldk = 0;
+  const double* X = nullptr;  // estimate for the unobserved pixels (null: 0); may alias C
+  double* C = nullptr;
+  int m = 0, n = 0;
+};
+constexpr int kMaxGaussRadius = 16;
+struct GaussTaps {
+  int radius = 0;
+  double w[2 * kMaxGaussRadius + 1];
+};
+cudaError_t launch_cur_fill(const CurFill& f, cudaStream_t st);
+cudaError_t launch_cur_gather(const double* C, int m, int n, int r, const int* I, const int* J, double* CJ,
+                              double* RI, double* W, cudaStream_t st);
+cudaError_t launch_cur_gauss(const double* in, double* out, int m, int n, const GaussTaps& g, cudaStream_t st);
+
 }  // namespace qp

@@ -1557,6 +1557,123 @@ int qpinv_penrose(qpinv_ctx* c, void* stream, int m, int n, const double* const 
   return QPINV_OK;
 }
 
+int qpinv_cur_complete(qpinv_ctx* c, void* stream, int m, int n, const double* const M[4], long ldm,
+                       const unsigned char* mask, long ldmask, int r, int iters, const int* I, const int* J, int form,
+                       qpinv_method method, double tol, int max_iter, double sigma, double* const C[4], long ldc,
+                       qpinv_cur_result* out) {
+  if (!c) return QPINV_E_INVALID;
+  if (m <= 0 || n <= 0 || r < 1 || r > std::min(m, n) || iters < 1 || ldm < n || ldmask < n || ldc < n ||
+      !planes_ok(M) || !planes_ok((const double* const*)C) || !mask || !I || !J || (form != 0 && form != 1) ||
+      (int)method < 0 || (int)method > 4 || !(tol >= 0.0) || max_iter < 1 || !(sigma >= 0.0) ||
+      std::ceil(2.0 * sigma) > kMaxGaussRadius)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  for (long t = 0; t < (long)iters * r; t++)
+    if (I[t] < 0 || I[t] >= m || J[t] < 0 || J[t] >= n) return fail(c, QPINV_E_INVALID, "index out of range");
+  const auto t_start = std::chrono::steady_clock::now();
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  c->st = st;
+  qpinv_cur_result res;
+  memset(&res, 0, sizeof(res));
+  try {
+    const bool fp64 = c->opt.precision == QPINV_PREC_FP64;
+    if (!fp64 && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    // caller data (device or host) into contiguous workspace planes
+    QMat Mo = mat(c, "cur.M", m, n, MST_D, false, false);
+    load_planes(c, M, ldm, m, n, Mo);
+    unsigned char* dmask = (unsigned char*)buf(c, "cur.mask", (size_t)m * n + 64);
+    ck(c, cudaMemcpy2DAsync(dmask, n, mask, ldmask, n, m, is_device_ptr(mask) ? cudaMemcpyDeviceToDevice
+                                                                               : cudaMemcpyHostToDevice, st),
+       "copy mask");
+    int* didx = (int*)buf(c, "cur.idx", sizeof(int) * 2 * (size_t)iters * r + 64);
+    ck(c, cudaMemcpyAsync(didx, I, sizeof(int) * (size_t)iters * r, cudaMemcpyHostToDevice, st), "copy I");
+    ck(c, cudaMemcpyAsync(didx + (size_t)iters * r, J, sizeof(int) * (size_t)iters * r, cudaMemcpyHostToDevice, st),
+       "copy J");
+    QMat Cm = mat(c, "cur.C", m, n, MST_D, false, false), Xm = mat(c, "cur.X", m, n, MST_D, false, false);
+    QMat CJ = mat(c, "cur.CJ", m, r, MST_D, false, false), RI = mat(c, "cur.RI", r, n, MST_D, false, false);
+    QMat W = mat(c, "cur.W", r, r, MST_D, false, false), U = mat(c, "cur.U", r, r, MST_D, false, false);
+    QMat CJp = mat(c, "cur.CJp", r, m, MST_D, false, false), RIp = mat(c, "cur.RIp", n, r, MST_D, false, false);
+    QMat T1 = mat(c, "cur.T1", r, n, MST_D, false, false), T2 = mat(c, "cur.T2", m, r, MST_D, false, false);
+    const double bytes_mn = 32.0 * m * n;
+    CurFill f;
+    for (int q = 0; q < 4; q++) f.M[q] = Mo.d.p + q * Mo.d.ps;
+    f.ldm = n;
+    f.mask = dmask;
+    f.ldk = n;
+    f.C = Cm.d.p;
+    f.m = m;
+    f.n = n;
+    timed(c, EV_EW, 0, 0, bytes_mn * 2, [&] { return launch_cur_fill(f, st); });  // C^(0): missing = 0
+    GaussTaps taps;
+    if (sigma > 0.0) {  // sampled Gaussian on |x| <= ceil(2 sigma), normalised
+      taps.radius = (int)std::ceil(2.0 * sigma);
+      double sum = 0.0;
+      for (int a = -taps.radius; a <= taps.radius; a++) sum += taps.w[a + taps.radius] = std::exp(-a * a / (2.0 * sigma * sigma));
+      for (int a = 0; a <= 2 * taps.radius; a++) taps.w[a] /= sum;
+    }
+    // C = P Q on the tensor cores (FP64-accurate exact slices), or the FP64 kernel
+    auto gemm = [&](const QMat& P, const QMat& Q, const QMat& R) {
+      Solver S;
+      S.c = c;
+      S.dbl = true;
+      S.L = 0;
+      S.xS = 8;
+      Solver::Acc acc = S.prod(P, Q, fp64 ? PM_F64 : PM_EMU);
+      CombineArgs a = S.base_args(R.rows, R.cols, &acc);
+      S.out(a, R, "f", 1.0);
+      S.run(a);
+      if (!fp64) check_kernel_error(c);
+    };
+    auto planes = [](const QMat& Q, double* p[4]) {
+      for (int q = 0; q < 4; q++) p[q] = Q.d.p + q * Q.d.ps;
+    };
+    // pseudoinverse of P (rows x cols) into Pp (cols x rows) by the chosen iteration
+    auto pinv = [&](const QMat& P, const QMat& Pp) {
+      double* a[4];
+      double* x[4];
+      planes(P, a);
+      planes(Pp, x);
+      qpinv_result pr;
+      const int rc = qpinv_solve(c, stream, P.rows, P.cols, a, P.cols, method, tol, max_iter, x, P.rows, &pr);
+      if (rc != QPINV_OK) throw QpError{rc, "pseudoinverse: " + c->err};
+      res.pinv_solves++;
+      res.pinv_iters += pr.iters;
+      res.pinv_worst_status = std::max(res.pinv_worst_status, pr.status);
+      res.pinv_max_E1_rel = std::max(res.pinv_max_E1_rel, pr.E_rel[0]);
+    };
+    for (int t = 0; t < iters; t++) {
+      const int* It = didx + (size_t)t * r;
+      const int* Jt = didx + (size_t)iters * r + (size_t)t * r;
+      timed(c, EV_EW, 0, 0, 64.0 * r * (m + n + r),
+            [&] { return launch_cur_gather(Cm.d.p, m, n, r, It, Jt, CJ.d.p, RI.d.p, form ? W.d.p : nullptr, st); });
+      if (form == 0) {  // U = C_J^dagger C R_I^dagger (eq. Uopt with A the filled matrix)
+        pinv(CJ, CJp);
+        pinv(RI, RIp);
+        gemm(CJp, Cm, T1);
+        gemm(T1, RIp, U);
+      } else {  // U = W^dagger (eq. Ucross)
+        pinv(W, U);
+      }
+      gemm(CJ, U, T2);
+      gemm(T2, RI, Xm);  // X^(t) = C_J U R_I
+      f.X = Xm.d.p;
+      if (sigma > 0.0) {
+        timed(c, EV_EW, 0, 0, bytes_mn * 2, [&] { return launch_cur_gauss(Xm.d.p, Cm.d.p, m, n, taps, st); });
+        f.X = Cm.d.p;  // filtered X; the fill below overwrites it in place
+      }
+      timed(c, EV_EW, 0, 0, bytes_mn * 2.5, [&] { return launch_cur_fill(f, st); });  // C^(t+1)
+    }
+    store_planes(c, Cm, C, ldc, m, n);
+    ck(c, cudaStreamSynchronize(st), "stream sync");
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  res.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (out) *out = res;
+  return QPINV_OK;
+}
+
 int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, const int* n, const double* const* A,
                         const long* lda, qpinv_method method, double tol, int max_iter, double* const* X,
                         const long* ldx, qpinv_result* out) {

@@ -58,6 +58,11 @@ class qpinv_stats(ctypes.Structure):
                 ("batched_graph_replays", ctypes.c_longlong)]
 
 
+class qpinv_cur_result(ctypes.Structure):
+    _fields_ = [("pinv_solves", ctypes.c_int), ("pinv_iters", ctypes.c_int), ("pinv_worst_status", ctypes.c_int),
+                ("pinv_max_E1_rel", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
 PTR4 = ctypes.c_void_p * 4
 _lib = None
 
@@ -65,7 +70,7 @@ _lib = None
 EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_solve", "qpinv_solve_batched",
            "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
            "qpinv_reset_stats", "qpinv_qgemm_noalloc", "qpinv_alpha_features", "qpinv_alpha_train",
-           "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights")
+           "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights", "qpinv_cur_complete")
 ALPHA_NFEAT, ALPHA_NWEIGHTS, ALPHA_NTRAIN = 32, 6401, 6337
 
 
@@ -101,6 +106,9 @@ def lib():
         L.qpinv_alpha_predict.argtypes = [vp, vp, fp, dp]
         L.qpinv_alpha_gradient.argtypes = [vp, vp, i, fp, fp, fp, dp]
         L.qpinv_alpha_weights.argtypes = [vp, fp, i, i]
+        ip = ctypes.POINTER(i)
+        L.qpinv_cur_complete.argtypes = [vp, vp, i, i, PTR4, l, vp, l, i, i, ip, ip, i, i, d, i, d, PTR4, l,
+                                         ctypes.POINTER(qpinv_cur_result)]
         _lib = L
     return _lib
 
@@ -251,6 +259,43 @@ class Context:
         if kx is not X:  # host copy made for contiguity
             X[...] = kx
         return X, result_dict(res)
+
+    def cur_complete(self, M, mask, I, J, method="qhpi19", tol=1e-12, max_iter=200, sigma=0.5, cross=False,
+                     C=None, stream=None):
+        """CUR image completion (qpinv_cur_complete).  M: (4, m, n) planes;
+        mask: (m, n) uint8 (nonzero = observed), a tensor on M's device or a
+        numpy array; I, J: (iters, r) integer index sets.  Returns (C, info)."""
+        m, n = M.shape[1], M.shape[2]
+        I = np.ascontiguousarray(I, dtype=np.int32)
+        J = np.ascontiguousarray(J, dtype=np.int32)
+        assert I.shape == J.shape and I.ndim == 2
+        iters, r = I.shape
+        if C is None:
+            if _is_torch(M):
+                import torch
+                C = torch.empty((4, m, n), dtype=torch.float64, device=M.device)
+            else:
+                C = np.empty((4, m, n))
+        pm, ldm, km = _planes(M)
+        pc, ldc, kc = _planes(C)
+        if _is_torch(mask):
+            assert mask.dtype.itemsize == 1 and mask.stride(1) == 1
+            mp, ldk = mask.data_ptr(), mask.stride(0)
+        else:
+            mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            mp, ldk = mask.ctypes.data, mask.shape[1]
+        res = qpinv_cur_result()
+        ip = ctypes.POINTER(ctypes.c_int)
+        rc = lib().qpinv_cur_complete(self.h, _stream_handle(stream), m, n, pm, ldm, mp, ldk, r, iters,
+                                      I.ctypes.data_as(ip), J.ctypes.data_as(ip), 1 if cross else 0,
+                                      METHODS[method], float(tol), int(max_iter), float(sigma), pc, ldc,
+                                      ctypes.byref(res))
+        _check(self.h, rc, "qpinv_cur_complete")
+        if kc is not C:
+            C[...] = kc
+        return C, dict(pinv_solves=res.pinv_solves, pinv_iters=res.pinv_iters,
+                       pinv_worst_status=STATUS.get(res.pinv_worst_status, res.pinv_worst_status),
+                       pinv_max_E1_rel=res.pinv_max_E1_rel, time_ms=res.time_ms)
 
     def solve_batched(self, As, method="qhpi19", tol=1e-6, max_iter=100, Xs=None, stream=None):
         import torch

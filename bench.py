@@ -428,7 +428,7 @@ def bench_cur(args, torch, qpinv):
         "unit": "completions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (exact-slice products)",
         "data": "synthetic",
-        "config": {"workload": "512x768 synthetic colour image (pure quaternions), 70% of pixels removed, CUR rank 60 "
+        "config": {"workload": "512x768 synthetic colour image (pure quaternions), 70%% of pixels removed, CUR rank 60 "
                                "with U = C_J^+ C R_I^+, 25 impute-reconstruct iterations, Gaussian filter 0.5, "
                                "%s pseudoinverses (mixed precision, rel. tol 1e-12)" % args.method.upper(),
                    "l2": "working set of 19 MB per image plane set fits in L2; no flush"},

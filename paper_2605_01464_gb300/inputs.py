@@ -218,3 +218,48 @@ def cur_index_sets(m: int, n: int, r: int, iters: int, seed: int = 18):
         I[t] = np.sort(np.argsort(uniform(seed, m, t << 33), kind="stable")[:r])
         J[t] = np.sort(np.argsort(uniform(seed, n, (t << 33) + (1 << 32)), kind="stable")[:r])
     return I, J
+
+
+# ------------------------------------------------- Lorenz signal filtering
+
+def lorenz_trajectory(dt: float, t_end: float, y0=(1.0, 1.0, 1.0), sigma: float = 10.0, delta: float = 8.0 / 3.0,
+                      gamma: float = 28.0, substeps: int = 10) -> np.ndarray:
+    """Samples (u, v, w) of the Lorenz system du/dt = sigma (v - u),
+    dv/dt = u (gamma - w) - v, dw/dt = u v - delta w at t = 0, dt, ..., t_end
+    ((K + 1, 3) array), by the classical fourth-order Runge-Kutta method with
+    `substeps` steps per sample (stands in for an adaptive ode45 run sampled at
+    dt: the flow is chaotic, so two accurate integrators agree only up to
+    t ~ 20 in any case)."""
+    def rhs(y):
+        u, v, w = y
+        return np.array([sigma * (v - u), u * (gamma - w) - v, u * v - delta * w])
+    K = int(round(t_end / dt))
+    h = dt / substeps
+    y = np.array(y0, dtype=np.float64)
+    out = np.empty((K + 1, 3))
+    out[0] = y
+    for k in range(K):
+        for _ in range(substeps):
+            k1 = rhs(y)
+            k2 = rhs(y + 0.5 * h * k1)
+            k3 = rhs(y + 0.5 * h * k2)
+            k4 = rhs(y + h * k3)
+            y = y + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        out[k + 1] = y
+    return out
+
+
+def lorenz_signals(dt: float = 0.01, tau: float = 1.0, t_end: float = 40.0, noise: float = 0.5, seed: int = 19):
+    """Reference and observed quaternion signals of the filtering example:
+    s_k = u(t_k) i + v(t_k) j + w(t_k) k and x_k = s(t_k - tau) + eta_k at
+    t_k = tau + k dt, k = 0 .. N-1 (N = t_end / dt + 1), with eta_k purely
+    imaginary, each component N(0, noise^2) (stream `seed`).  Returns
+    (x, s), each (4, N) planes (zero real plane)."""
+    d = int(round(tau / dt))
+    N = int(round(t_end / dt)) + 1
+    tr = lorenz_trajectory(dt, t_end + d * dt)
+    x = np.zeros((4, N))
+    s = np.zeros((4, N))
+    s[1:] = tr[d:d + N].T
+    x[1:] = tr[0:N].T + noise * normal(seed, 3 * N).reshape(3, N)
+    return x, s

@@ -443,6 +443,88 @@ def bench_cur(args, torch, qpinv):
     return 0
 
 
+# Sec. 5.2's table (CPU seconds; QSVD, QNS, QSAI) per step size.
+PAPER_LORENZ_SECONDS = {0.01: (994.45, 254.35, 74.34), 0.02: (115.61, 37.27, 10.21), 0.03: (35.34, 14.71, 4.22),
+                        0.04: (15.11, 6.19, 1.70), 0.05: (6.89, 3.29, 0.98)}
+
+
+def bench_filter(args, torch, qpinv):
+    """Quaternion filtering of Lorenz signals (Sec. 5.2): for each step size
+    dt in 0.01 .. 0.05 over [0, 40] (N = 40/dt + 1 samples, delay tau = 1,
+    noise 0.5 per component), the (p+1) x (p+1) data matrix with p = (N-1)/2,
+    h = X^+ s by QSAI and by Newton-Schulz (MIXED, rel. tol 1e-12), s_hat =
+    X h and its error.  One step = one filter design at dt = 0.01 (2001 x 2001)
+    with QSAI; the other cases are timed the same way and reported."""
+    import numpy as np
+    from paper_2605_01464_gb300 import inputs
+    ctx = qpinv.Context(0, profile=True)
+    stream = torch.cuda.current_stream()
+    out, roof, line = {}, None, None
+    with ClockSampler(0) as clk:
+        for dt in (0.01, 0.02, 0.03, 0.04, 0.05):
+            x, s = inputs.lorenz_signals(dt=dt)
+            p = (x.shape[1] - 1) // 2
+            xd, sd = torch.from_numpy(x).cuda(), torch.from_numpy(s).cuda()
+            res = {"p": p}
+            for method in ("qsai", "ns"):
+                for _ in range(args.warmup):
+                    ctx.toeplitz_filter(xd, sd, p, method=method, tol=1e-12, max_iter=2000, stream=stream)
+                ctx.reset_stats()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    h, sh, err, info = ctx.toeplitz_filter(xd, sd, p, method=method, tol=1e-12, max_iter=2000,
+                                                           stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                st = ctx.stats()
+                res[method] = {"ms": ms, "err": err, "iters": info["iters"], "status": info["status"],
+                               "E1_rel": info["E_rel"][0], "gpu_launches": st["kernel_launches"] // args.steps}
+                if dt == 0.01 and method == "qsai":
+                    roof = kernel_rooflines(st)[0]
+                    line = (ms, st["kernel_launches"] // args.steps)
+                    xh = torch.from_numpy(x).pin_memory().numpy()
+                    shh = torch.from_numpy(s).pin_memory().numpy()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(args.steps):
+                        ctx.toeplitz_filter(xh, shh, p, method=method, tol=1e-12, max_iter=2000, stream=stream)
+                    torch.cuda.synchronize()
+                    res["e2e_ms"] = (time.perf_counter() - t0) * 1e3 / args.steps
+                    e2e_bytes = (x.nbytes + s.nbytes, 2 * 4 * 8 * (p + 1))
+            res["paper_cpu_seconds_qsvd_qns_qsai"] = PAPER_LORENZ_SECONDS[dt]
+            out[str(dt)] = res
+    base = None
+    if not args.no_cpu_baseline:
+        from oracle import lorenz
+        x, s = inputs.lorenz_signals(dt=0.05)
+        p5 = (x.shape[1] - 1) // 2
+        t0 = time.perf_counter()
+        lorenz.design(x, s, p5, p5, "qsai", tol=1e-12, max_iter=2000)
+        t5 = time.perf_counter() - t0
+        scale = (2001.0 / (p5 + 1)) ** 3
+        base = {"value": 1.0 / (t5 * scale), "unit": "designs/s", "cores": 1, "kind": "oracle",
+                "sample": "QSAI design at dt = 0.05 (401 x 401) by the FP64 oracle, %.2f s, extrapolated by "
+                          "(2001/401)^3 to dt = 0.01" % t5}
+    ms, launches = line
+    print(json.dumps({
+        "metric": "Lorenz quaternion filter designs/s (dt 0.01: 2001x2001 data matrix, QSAI)", "value": 1e3 / ms,
+        "unit": "designs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split/exact-slice (mixed)",
+        "data": "synthetic",
+        "config": {"workload": "Lorenz system (sigma 10, delta 8/3, gamma 28, start (1,1,1)) sampled at dt over "
+                               "[0, 40] by RK4, delay tau = 1, purely imaginary noise N(0, 0.25) per component; "
+                               "square Toeplitz data matrix of half the samples; h = X^+ s, QSAI, mixed precision",
+                   "l2": "one 2001^2 quaternion matrix is 128 MB of FP64 planes, about L2: no flush"},
+        "e2e": {"value": 1e3 / out["0.01"]["e2e_ms"], "unit": "designs/s", "h2d_bytes_per_step": e2e_bytes[0],
+                "d2h_bytes_per_step": e2e_bytes[1]},
+        "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "result": out,
+        "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def bench_learned(args, torch, qpinv):
     """Learned initial scaling: train the MLP on generator families at sizes
     32..256, then solve held-out full-rank 1024^2 and 2048 x 1024 matrices
@@ -580,11 +662,11 @@ def main():
                     help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
     ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "batched", "rankdef", "learned", "hyper", "cur"],
+                    choices=["dense", "batched", "rankdef", "learned", "hyper", "cur", "filter"],
                     help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "
                          "rankdef: rank-2048 8192x4096 (QHPI19 and NS, EMU); learned: learned-alpha training "
                          "and held-out evaluation; hyper: factorized vs unfactorized hyperpower (Example 3); "
-                         "cur: CUR image completion (Sec. 5.1)")
+                         "cur: CUR image completion (Sec. 5.1); filter: Lorenz signal filtering (Sec. 5.2)")
     ap.add_argument("--train-count", type=int, default=1500, help="--workload learned: training matrices")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
@@ -616,6 +698,8 @@ def main():
         return bench_hyper(args, torch, qpinv)
     if args.workload == "cur":
         return bench_cur(args, torch, qpinv)
+    if args.workload == "filter":
+        return bench_filter(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist

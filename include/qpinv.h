@@ -300,6 +300,23 @@ int qpinv_cur_complete(qpinv_ctx* ctx, void* stream, int m, int n, const double*
                        int form, qpinv_method method, double tol, int max_iter, double sigma,
                        double* const C[4], long ldc, qpinv_cur_result* out);
 
+/* ---- application: quaternion signal filtering (Sec. 5.2) ---------------
+ * Filter s(t) ~ sum_{m=0}^{p} x(t - m) h_m (eq. (conv)) as X h = s with the
+ * (p+1) x (p+1) data matrix X(i, j) = x(t0 + i - j) and s(i) = s(t0 + i),
+ * i, j = 0..p: h = X^dagger s by qpinv_solve (the context's options, method,
+ * tol and max_iter as given), s_hat = X h (FP64-accurate products) and
+ * err = ||s_hat - s|| / ||s||.
+ *   - x, s: four planes of N samples each (device or host; plane c of a
+ *     quaternion signal in x[c]); p >= 0 and p <= t0 <= N - 1 - p.
+ *   - h, s_hat: four planes of p + 1 values each (device or host), written.
+ *   - pinv_out (host, may be NULL) receives the outcome of the solve for
+ *     X^dagger; err (host, may be NULL) the relative error.
+ *   - Errors: QPINV_E_INVALID for bad sizes, pointers or method; errors of
+ *     the solve are returned as is (message prefixed "pseudoinverse:"). */
+int qpinv_toeplitz_filter(qpinv_ctx* ctx, void* stream, int N, const double* const x[4], const double* const s[4],
+                          int p, int t0, qpinv_method method, double tol, int max_iter, double* const h[4],
+                          double* const s_hat[4], qpinv_result* pinv_out, double* err);
+
 /* ---- building blocks, exposed for tests and measurement ---------------- */
 
 /* C = A B for quaternion matrices (Hamilton product, Sec. 2): A is m x k

@@ -232,5 +232,8 @@ cudaError_t launch_cur_fill(const CurFill& f, cudaStream_t st);
 cudaError_t launch_cur_gather(const double* C, int m, int n, int r, const int* I, const int* J, double* CJ,
                               double* RI, double* W, cudaStream_t st);
 cudaError_t launch_cur_gauss(const double* in, double* out, int m, int n, const GaussTaps& g, cudaStream_t st);
+// Signal filtering (toeplitz.cu): X(i, j) = x(t0 + i - j), (p+1) x (p+1),
+// from planes of samples with plane stride xps; X contiguous.
+cudaError_t launch_toeplitz(const double* x, long xps, int p, int t0, double* X, cudaStream_t st);
 
 }  // namespace qp

@@ -1674,6 +1674,69 @@ int qpinv_cur_complete(qpinv_ctx* c, void* stream, int m, int n, const double* c
   return QPINV_OK;
 }
 
+int qpinv_toeplitz_filter(qpinv_ctx* c, void* stream, int N, const double* const x[4], const double* const s[4],
+                          int p, int t0, qpinv_method method, double tol, int max_iter, double* const h[4],
+                          double* const s_hat[4], qpinv_result* pinv_out, double* err) {
+  if (!c) return QPINV_E_INVALID;
+  if (N < 1 || p < 0 || t0 - p < 0 || t0 + p >= N || !planes_ok(x) || !planes_ok(s) ||
+      !planes_ok((const double* const*)h) || !planes_ok((const double* const*)s_hat) || (int)method < 0 ||
+      (int)method > 4 || !(tol >= 0.0) || max_iter < 1)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  c->st = st;
+  try {
+    const bool fp64 = c->opt.precision == QPINV_PREC_FP64;
+    if (!fp64 && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
+    const int n = p + 1;
+    QMat xs = mat(c, "flt.x", 1, N, MST_D, false, false), ss = mat(c, "flt.s", 1, N, MST_D, false, false);
+    load_planes(c, x, N, 1, N, xs);
+    load_planes(c, s, N, 1, N, ss);
+    QMat X = mat(c, "flt.X", n, n, MST_D, false, false), Xp = mat(c, "flt.Xp", n, n, MST_D, false, false);
+    QMat S = mat(c, "flt.S", n, 1, MST_D, false, false), H = mat(c, "flt.h", n, 1, MST_D, false, false);
+    QMat Sh = mat(c, "flt.sh", n, 1, MST_D, false, false);
+    timed(c, EV_EW, 0, 0, 32.0 * n * n, [&] { return launch_toeplitz(xs.d.p, xs.d.ps, p, t0, X.d.p, st); });
+    for (int q = 0; q < 4; q++)  // s(t0 + i), i = 0..p
+      ck(c, cudaMemcpyAsync(S.d.p + q * S.d.ps, ss.d.p + q * ss.d.ps + t0, sizeof(double) * n,
+                            cudaMemcpyDeviceToDevice, st),
+         "copy target");
+    double* a[4];
+    double* xp[4];
+    for (int q = 0; q < 4; q++) {
+      a[q] = X.d.p + q * X.d.ps;
+      xp[q] = Xp.d.p + q * Xp.d.ps;
+    }
+    qpinv_result pr;
+    const int rc = qpinv_solve(c, stream, n, n, a, n, method, tol, max_iter, xp, n, &pr);
+    if (rc != QPINV_OK) throw QpError{rc, "pseudoinverse: " + c->err};
+    auto gemm = [&](const QMat& P, const QMat& Q, const QMat& R) {  // FP64-accurate R = P Q
+      Solver S2;
+      S2.c = c;
+      S2.dbl = true;
+      S2.L = 0;
+      S2.xS = 8;
+      Solver::Acc acc = S2.prod(P, Q, fp64 ? PM_F64 : PM_EMU);
+      CombineArgs ca = S2.base_args(R.rows, R.cols, &acc);
+      S2.out(ca, R, "f", 1.0);
+      S2.run(ca);
+      if (!fp64) check_kernel_error(c);
+    };
+    gemm(Xp, S, H);   // h = X^dagger s
+    gemm(X, H, Sh);   // s_hat = X h
+    const Planes<const double> sv = dview(S);  // eps = ||s_hat - s|| / ||s||
+    const double num = fro2(c, dview(Sh), &sv, n, 1), den = fro2(c, sv, nullptr, n, 1);
+    store_planes(c, H, h, 1, n, 1);
+    store_planes(c, Sh, s_hat, 1, n, 1);
+    ck(c, cudaStreamSynchronize(st), "stream sync");
+    if (err) *err = den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
+    if (pinv_out) *pinv_out = pr;
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  return QPINV_OK;
+}
+
 int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, const int* n, const double* const* A,
                         const long* lda, qpinv_method method, double tol, int max_iter, double* const* X,
                         const long* ldx, qpinv_result* out) {

@@ -70,7 +70,8 @@ _lib = None
 EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_solve", "qpinv_solve_batched",
            "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
            "qpinv_reset_stats", "qpinv_qgemm_noalloc", "qpinv_alpha_features", "qpinv_alpha_train",
-           "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights", "qpinv_cur_complete")
+           "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights", "qpinv_cur_complete",
+           "qpinv_toeplitz_filter")
 ALPHA_NFEAT, ALPHA_NWEIGHTS, ALPHA_NTRAIN = 32, 6401, 6337
 
 
@@ -109,6 +110,8 @@ def lib():
         ip = ctypes.POINTER(i)
         L.qpinv_cur_complete.argtypes = [vp, vp, i, i, PTR4, l, vp, l, i, i, ip, ip, i, i, d, i, d, PTR4, l,
                                          ctypes.POINTER(qpinv_cur_result)]
+        L.qpinv_toeplitz_filter.argtypes = [vp, vp, i, PTR4, PTR4, i, i, i, d, i, PTR4, PTR4,
+                                            ctypes.POINTER(qpinv_result), dp]
         _lib = L
     return _lib
 
@@ -296,6 +299,29 @@ class Context:
         return C, dict(pinv_solves=res.pinv_solves, pinv_iters=res.pinv_iters,
                        pinv_worst_status=STATUS.get(res.pinv_worst_status, res.pinv_worst_status),
                        pinv_max_E1_rel=res.pinv_max_E1_rel, time_ms=res.time_ms)
+
+    def toeplitz_filter(self, x, s, p, t0=None, method="qsai", tol=1e-12, max_iter=500, stream=None):
+        """Quaternion filter design (qpinv_toeplitz_filter).  x, s: (4, N)
+        sample planes (tensors or numpy arrays); t0 defaults to p.  Returns
+        (h, s_hat, err, info of the pseudoinverse solve); h and s_hat are
+        (4, p + 1, 1), allocated like x."""
+        N = x.shape[1]
+        t0 = p if t0 is None else t0
+        if _is_torch(x):
+            import torch
+            h = torch.empty((4, p + 1, 1), dtype=torch.float64, device=x.device)
+            sh = torch.empty_like(h)
+        else:
+            h, sh = np.empty((4, p + 1, 1)), np.empty((4, p + 1, 1))
+        px, _, kx = _planes(x[:, None, :])
+        ps, _, ks = _planes(s[:, None, :])
+        ph, _, kh = _planes(h)
+        psh, _, ksh = _planes(sh)
+        res, err = qpinv_result(), ctypes.c_double()
+        rc = lib().qpinv_toeplitz_filter(self.h, _stream_handle(stream), N, px, ps, int(p), int(t0), METHODS[method],
+                                         float(tol), int(max_iter), ph, psh, ctypes.byref(res), ctypes.byref(err))
+        _check(self.h, rc, "qpinv_toeplitz_filter")
+        return h, sh, err.value, result_dict(res)
 
     def solve_batched(self, As, method="qhpi19", tol=1e-6, max_iter=100, Xs=None, stream=None):
         import torch

@@ -263,3 +263,48 @@ def lorenz_signals(dt: float = 0.01, tau: float = 1.0, t_end: float = 40.0, nois
     s[1:] = tr[d:d + N].T
     x[1:] = tr[0:N].T + noise * normal(seed, 3 * N).reshape(3, N)
     return x, s
+
+
+# ------------------------------------------- preconditioned Krylov systems
+
+def reservoir_matrix(nx: int = 14, ny: int = 17, seed: int = 20, log_sd: float = 2.0, drift: float = 0.3,
+                     storage: float = 1e-7) -> np.ndarray:
+    """Real nonsymmetric (nx ny) x (nx ny) matrix standing in for saylr1
+    (238 x 238, a 14 x 17 reservoir-simulation grid): 5-point finite-volume
+    pressure operator with log-normal cell permeabilities (log standard
+    deviation log_sd, stream `seed`), harmonic-mean transmissibilities T,
+    an upwind drift term drift * T along x (the nonsymmetric part), and a
+    small storage term storage * mean(k) on the diagonal (without it the
+    no-flow operator is singular)."""
+    n = nx * ny
+    k = np.exp(log_sd * normal(seed, n))
+    A = np.zeros((n, n))
+    for iy in range(ny):
+        for ix in range(nx):
+            p = iy * nx + ix
+            for q, along_x in ((p + 1, True) if ix + 1 < nx else (None, True), (p + nx, False) if iy + 1 < ny
+                               else (None, False)):
+                if q is None:
+                    continue
+                T = 2.0 * k[p] * k[q] / (k[p] + k[q])
+                A[p, p] += T
+                A[q, q] += T
+                A[p, q] -= T
+                A[q, p] -= T
+                if along_x:  # upwind transport from p into q
+                    A[q, p] -= drift * T
+                    A[p, p] += drift * T
+    A[np.arange(n), np.arange(n)] += storage * k.mean()
+    return A
+
+
+def krylov_system(m: int = 3, nx: int = 14, ny: int = 17, seed: int = 20):
+    """The quaternion system of the preconditioning example: A = A_s + A_x i +
+    A_y j + A_z k with A_x = -A_s, A_y = 2 A_s, A_z = 1.5 A_s (A_s from
+    reservoir_matrix), and B (n x m) with every component uniform in [0, 1)
+    (stream seed + 1).  Returns (A, B) as planes."""
+    As = reservoir_matrix(nx, ny, seed)
+    n = As.shape[0]
+    A = np.stack([As, -As, 2.0 * As, 1.5 * As])
+    B = uniform(seed + 1, 4 * n * m).reshape(4, n, m)
+    return A, B

@@ -525,6 +525,94 @@ def bench_filter(args, torch, qpinv):
     return 0
 
 
+# Example 4's table: (IT, seconds) of Gl-QFOM, Gl-QGMRES, preconditioned Gl-QFOM, preconditioned Gl-QGMRES.
+PAPER_KRYLOV = {3: ((697, 10.94), (697, 10.71), (308, 2.07), (244, 1.29)),
+                6: ((1268, 50.56), (1264, 49.98), (542, 8.78), (419, 5.16)),
+                9: ((1756, 278.15), (1752, 140.89), (746, 24.00), (568, 13.27)),
+                12: ((2218, 449.83), (2212, 265.02), (951, 47.64), (703, 23.99))}
+
+
+def bench_krylov(args, torch, qpinv):
+    """Example 4 (Sec. 3.5): A X = B with A = A_s (1 - i + 2j + 1.5k), A_s the
+    238 x 238 reservoir operator standing in for saylr1, B with uniform
+    entries and m = 3, 6, 9, 12 columns; Gl-QFOM and Gl-QGMRES, plain and left
+    preconditioned by QSAI (2 iterations), unrestarted, X_0 = 0, RR <= 1e-6,
+    at most 3000 steps.  One step = one preconditioned Gl-QGMRES solve at
+    m = 3 (the line's value); the rest are timed the same way and reported."""
+    import numpy as np
+    from paper_2605_01464_gb300 import inputs
+    ctx = qpinv.Context(0, profile=True)
+    stream = torch.cuda.current_stream()
+    variants = (("fom", "fom", 0), ("gmres", "gmres", 0), ("prec_fom", "fom", 2), ("prec_gmres", "gmres", 2))
+    out, line = {}, None
+    _, _, hbm, src = peaks()
+    with ClockSampler(0) as clk:
+        for m in (3, 6, 9, 12):
+            A, B = inputs.krylov_system(m)
+            Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            res = {}
+            for name, kind, pk in variants:
+                steps = args.steps if (m == 3 and name == "prec_gmres") else 1
+                for _ in range(args.warmup if steps > 1 else 1):
+                    ctx.global_krylov(Ad, Bd, kind, precond_iters=pk, tol=1e-6, max_iter=3000, stream=stream)
+                ctx.reset_stats()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(steps):
+                    X, info = ctx.global_krylov(Ad, Bd, kind, precond_iters=pk, tol=1e-6, max_iter=3000,
+                                                stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                st = ctx.stats()
+                res[name] = {"ms": ms, "iters": info["iters"], "converged": info["converged"],
+                             "rel_res": info["rel_res"], "true_rel_res": info["true_rel_res"],
+                             "gpu_launches": st["kernel_launches"] // steps}
+                if m == 3 and name == "prec_gmres":
+                    gbs = st["ew_bytes"] / (st["ew_ms"] * 1e-3) / 1e9 if st["ew_ms"] > 0 else None
+                    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                            "frac": gbs / hbm if gbs else None, "traffic": None,
+                            "kernel": "global Gram-Schmidt / update kernels (k_block_dot, k_block_sub, "
+                                      "k_norm_scale, k_basis_add; bytes counted per launch)",
+                            "ew_ms_per_solve": st["ew_ms"] / steps, "f64_gemm_ms_per_solve": st["f64_gemm_ms"] / steps,
+                            "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % src}
+                    line = (ms, st["kernel_launches"] // steps, roof)
+                    Ah = torch.from_numpy(A).pin_memory().numpy()
+                    Bh = torch.from_numpy(B).pin_memory().numpy()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(steps):
+                        ctx.global_krylov(Ah, Bh, kind, precond_iters=pk, tol=1e-6, max_iter=3000, stream=stream)
+                    torch.cuda.synchronize()
+                    e2e = ((time.perf_counter() - t0) * 1e3 / steps, A.nbytes + B.nbytes, B.nbytes)
+            res["paper_it_seconds"] = dict(zip([v[0] for v in variants], PAPER_KRYLOV[m]))
+            out[str(m)] = res
+    base = None
+    if not args.no_cpu_baseline:
+        from oracle import krylov
+        A, B = inputs.krylov_system(3)
+        t0 = time.perf_counter()
+        krylov.global_krylov(A, B, "gmres", precond_iters=2, tol=1e-6, max_iter=3000)
+        t_cpu = time.perf_counter() - t0
+        base = {"value": 1.0 / t_cpu, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": "one preconditioned Gl-QGMRES solve at m = 3 by the FP64 oracle, %.1f s" % t_cpu}
+    ms, launches, roof = line
+    print(json.dumps({
+        "metric": "QSAI-preconditioned Gl-QGMRES solves/s (238x238 reservoir operator, m = 3, RR 1e-6)",
+        "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "A = A_s (1 - i + 2j + 1.5k), A_s a 14x17-grid 5-point reservoir operator (log-normal "
+                               "permeability, upwind drift) standing in for saylr1; B uniform, m = 3..12 columns; "
+                               "unrestarted Gl-QFOM / Gl-QGMRES, plain and QSAI-preconditioned (2 iterations)",
+                   "l2": "the Krylov basis (at most 3000 x 0.27 MB) streams from HBM; no flush"},
+        "e2e": {"value": 1e3 / e2e[0], "unit": "solves/s", "h2d_bytes_per_step": e2e[1], "d2h_bytes_per_step": e2e[2]},
+        "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "result": out,
+        "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def bench_learned(args, torch, qpinv):
     """Learned initial scaling: train the MLP on generator families at sizes
     32..256, then solve held-out full-rank 1024^2 and 2048 x 1024 matrices
@@ -662,11 +750,12 @@ def main():
                     help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
     ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "batched", "rankdef", "learned", "hyper", "cur", "filter"],
+                    choices=["dense", "batched", "rankdef", "learned", "hyper", "cur", "filter", "krylov"],
                     help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "
                          "rankdef: rank-2048 8192x4096 (QHPI19 and NS, EMU); learned: learned-alpha training "
                          "and held-out evaluation; hyper: factorized vs unfactorized hyperpower (Example 3); "
-                         "cur: CUR image completion (Sec. 5.1); filter: Lorenz signal filtering (Sec. 5.2)")
+                         "cur: CUR image completion (Sec. 5.1); filter: Lorenz signal filtering (Sec. 5.2); "
+                         "krylov: QSAI-preconditioned global Krylov solvers (Sec. 3.5)")
     ap.add_argument("--train-count", type=int, default=1500, help="--workload learned: training matrices")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
@@ -700,6 +789,8 @@ def main():
         return bench_cur(args, torch, qpinv)
     if args.workload == "filter":
         return bench_filter(args, torch, qpinv)
+    if args.workload == "krylov":
+        return bench_krylov(args, torch, qpinv)
     dist = None
     if world > 1:
         import torch.distributed as dist

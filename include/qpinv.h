@@ -317,6 +317,34 @@ int qpinv_toeplitz_filter(qpinv_ctx* ctx, void* stream, int N, const double* con
                           int p, int t0, qpinv_method method, double tol, int max_iter, double* const h[4],
                           double* const s_hat[4], qpinv_result* pinv_out, double* err);
 
+/* ---- application: preconditioned global Krylov solvers (Sec. 3.5) -------
+ * Solves A X = B (A n x n, B n x m quaternion) by Gl-QGMRES (kind 0) or
+ * Gl-QFOM (kind 1): global Arnoldi with the real inner product
+ * <V, W> = Re tr(V^H W) (classical Gram-Schmidt applied twice), Givens
+ * rotations for the residual estimate, restarts every `restart` steps
+ * (0 = none), X_0 = 0.  With precond_iters = k > 0 the system is left
+ * preconditioned, M A X = M B, M = X_k of k QSAI iterations on A (Alg. 2,
+ * safe alpha, FP64 products).  Stop: ||B' - A' X_j||_F / ||B'||_F <= tol for
+ * the system solved, or max_iter Arnoldi steps.  Products are FP64 (CUDA
+ * cores); the small Hessenberg least-squares updates run on the host.
+ *   - A (lda >= n), B (ldb >= m), X (ldx >= m, written): four planes each,
+ *     device or host.
+ *   - out (host, may be NULL): iterations, convergence, the relative residual
+ *     of the system solved and the true one ||B - A X|| / ||B||.
+ *   - Errors: QPINV_E_INVALID for bad sizes, kind, restart < 0,
+ *     precond_iters outside [0, 100], max_iter outside [1, 100000]. */
+typedef struct {
+  int iters;           /* Arnoldi steps, over all restarts */
+  int converged;       /* 1 if the stop tolerance was met */
+  double rel_res;      /* ||B' - A' X||_F / ||B'||_F of the system solved (explicit) */
+  double true_rel_res; /* ||B - A X||_F / ||B||_F */
+  double time_ms;      /* wall time of the call */
+} qpinv_krylov_result;
+
+int qpinv_global_krylov(qpinv_ctx* ctx, void* stream, int n, int m, const double* const A[4], long lda,
+                        const double* const B[4], long ldb, int kind, int restart, int precond_iters, double tol,
+                        int max_iter, double* const X[4], long ldx, qpinv_krylov_result* out);
+
 /* ---- building blocks, exposed for tests and measurement ---------------- */
 
 /* C = A B for quaternion matrices (Hamilton product, Sec. 2): A is m x k

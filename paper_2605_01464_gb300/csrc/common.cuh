@@ -235,5 +235,12 @@ cudaError_t launch_cur_gauss(const double* in, double* out, int m, int n, const 
 // Signal filtering (toeplitz.cu): X(i, j) = x(t0 + i - j), (p+1) x (p+1),
 // from planes of samples with plane stride xps; X contiguous.
 cudaError_t launch_toeplitz(const double* x, long xps, int p, int t0, double* X, cudaStream_t st);
+// Global Krylov solvers (krylov.cu): blocks of L doubles, basis stride L.
+cudaError_t launch_block_dot(const double* V, int c, const double* W, long L, double* h, cudaStream_t st);
+cudaError_t launch_block_sub(double* W, const double* V, const double* h, int c, long L, double* hcol,
+                             cudaStream_t st);
+cudaError_t launch_norm_scale(const double* W, long L, double* nrm, double* out, cudaStream_t st);
+cudaError_t launch_basis_add(double* X, const double* V, const double* y, int k, long L, cudaStream_t st);
+cudaError_t launch_sub(double* out, const double* a, const double* b, long L, cudaStream_t st);
 
 }  // namespace qp

@@ -1,0 +1,123 @@
+// krylov.cu -- vector kernels of the global quaternion Krylov solvers
+// (Gl-QGMRES / Gl-QFOM, Sec. 3.5).  A block is an n x m quaternion matrix
+// stored as L = 4 n m contiguous doubles (four planes); the global inner
+// product <V, W> = Re tr(V^H W) is the plain dot product of those arrays.
+// The basis V_0, V_1, ... is one array of blocks with stride L.  Reductions
+// are deterministic (fixed block shapes, tree sums in shared memory).
+#include "common.cuh"
+
+namespace qp {
+namespace {
+
+constexpr int KT = 256;
+
+__device__ double block_reduce(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// h[i] = <V_i, W>, i < c: block i reduces over the L elements.
+__global__ void __launch_bounds__(KT) k_block_dot(const double* __restrict__ V, int c, const double* __restrict__ W,
+                                                   long L, double* __restrict__ h) {
+  __shared__ double sh[KT / 32];
+  const double* v = V + (long)blockIdx.x * L;
+  double s = 0.0;
+  for (long e = threadIdx.x; e < L; e += KT) s += v[e] * W[e];
+  s = block_reduce(s, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = s;
+}
+
+// W -= sum_{i<c} h[i] V_i; block 0 also adds h into the Hessenberg column.
+__global__ void k_block_sub(double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ h, int c,
+                            long L, double* __restrict__ hcol) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
+    double w = W[e];
+    for (int i = 0; i < c; i++) w -= h[i] * V[(long)i * L + e];
+    W[e] = w;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && hcol)
+    for (int i = 0; i < c; i++) hcol[i] += h[i];
+}
+
+// nrm = ||W||; out = W / nrm (out may alias W; left unscaled when nrm = 0).
+// One block: the blocks of these solvers are small (L = 4 n m).
+__global__ void __launch_bounds__(1024) k_norm_scale(const double* W, long L, double* __restrict__ nrm, double* out) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  double s = 0.0;
+  for (long e = threadIdx.x; e < L; e += blockDim.x) s += W[e] * W[e];
+  s = block_reduce(s, sh);
+  if (threadIdx.x == 0) {
+    tot = sqrt(s);
+    *nrm = tot;
+  }
+  __syncthreads();
+  const double t = tot;
+  if (out && t > 0.0)
+    for (long e = threadIdx.x; e < L; e += blockDim.x) out[e] = W[e] / t;
+}
+
+// X += sum_{i<k} y[i] V_i
+__global__ void k_basis_add(double* __restrict__ X, const double* __restrict__ V, const double* __restrict__ y, int k,
+                            long L) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
+    double x = X[e];
+    for (int i = 0; i < k; i++) x += y[i] * V[(long)i * L + e];
+    X[e] = x;
+  }
+}
+
+// out = a - b
+__global__ void k_sub(double* __restrict__ out, const double* __restrict__ a, const double* __restrict__ b, long L) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x)
+    out[e] = a[e] - b[e];
+}
+
+int grid_of(long L) {
+  long b = (L + KT - 1) / KT;
+  return (int)(b < 1 ? 1 : b > 4096 ? 4096 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_block_dot(const double* V, int c, const double* W, long L, double* h, cudaStream_t st) {
+  k_block_dot<<<c, KT, 0, st>>>(V, c, W, L, h);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_sub(double* W, const double* V, const double* h, int c, long L, double* hcol,
+                             cudaStream_t st) {
+  k_block_sub<<<grid_of(L), KT, 0, st>>>(W, V, h, c, L, hcol);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_scale(const double* W, long L, double* nrm, double* out, cudaStream_t st) {
+  k_norm_scale<<<1, 1024, 0, st>>>(W, L, nrm, out);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_basis_add(double* X, const double* V, const double* y, int k, long L, cudaStream_t st) {
+  k_basis_add<<<grid_of(L), KT, 0, st>>>(X, V, y, k, L);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(double* out, const double* a, const double* b, long L, cudaStream_t st) {
+  k_sub<<<grid_of(L), KT, 0, st>>>(out, a, b, L);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace qp

@@ -1737,6 +1737,166 @@ int qpinv_toeplitz_filter(qpinv_ctx* c, void* stream, int N, const double* const
   return QPINV_OK;
 }
 
+int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* const A[4], long lda,
+                        const double* const B[4], long ldb, int kind, int restart, int precond_iters, double tol,
+                        int max_iter, double* const X[4], long ldx, qpinv_krylov_result* out) {
+  if (!c) return QPINV_E_INVALID;
+  if (n < 1 || m < 1 || lda < n || ldb < m || ldx < m || !planes_ok(A) || !planes_ok(B) ||
+      !planes_ok((const double* const*)X) || (kind != 0 && kind != 1) || restart < 0 || precond_iters < 0 ||
+      precond_iters > 100 || !(tol >= 0.0) || max_iter < 1 || max_iter > 100000)
+    return fail(c, QPINV_E_INVALID, "invalid argument");
+  const auto t_start = std::chrono::steady_clock::now();
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  c->st = st;
+  qpinv_krylov_result res;
+  memset(&res, 0, sizeof(res));
+  try {
+    const long L = 4L * n * m;
+    QMat Ao = mat(c, "kry.A", n, n, MST_D, false, false), Bo = mat(c, "kry.B", n, m, MST_D, false, false);
+    load_planes(c, A, lda, n, n, Ao);
+    load_planes(c, B, ldb, n, m, Bo);
+    QMat As = Ao, Bs = Bo;  // the system solved: A X = B, or M A X = M B
+    auto f64 = [&](const QMat& P, const QMat& Q, const QMat& R) {
+      timed(c, EV_F64, 32.0 * P.rows * P.cols * Q.cols, 32.0 * P.rows * P.cols * Q.cols, 0,
+            [&] { return launch_qgemm_f64(P.rows, P.cols, Q.cols, dview(P), dview(Q), R.d, st); });
+    };
+    if (precond_iters > 0) {
+      // M = X_k of QSAI (Alg. 2) from X_0 = alpha A^H, safe alpha, FP64 products
+      QMat M = mat(c, "kry.M", n, n, MST_D, false, false);
+      const qpinv_options saved = c->opt;
+      c->opt.precision = QPINV_PREC_FP64;
+      c->opt.penrose = 0;
+      c->opt.stop_rule = QPINV_STOP_PAPER_ABS;
+      c->opt.alpha_mode = QPINV_ALPHA_SAFE;
+      c->opt.side = QPINV_SIDE_AUTO;
+      double* a[4];
+      double* x[4];
+      for (int q = 0; q < 4; q++) {
+        a[q] = Ao.d.p + q * Ao.d.ps;
+        x[q] = M.d.p + q * M.d.ps;
+      }
+      qpinv_result pr;
+      const int rc = qpinv_solve(c, stream, n, n, a, n, QPINV_QSAI, 0.0, precond_iters, x, n, &pr);
+      c->opt = saved;
+      c->st = st;
+      if (rc != QPINV_OK) throw QpError{rc, "preconditioner: " + c->err};
+      As = mat(c, "kry.MA", n, n, MST_D, false, false);
+      Bs = mat(c, "kry.MB", n, m, MST_D, false, false);
+      f64(M, Ao, As);
+      f64(M, Bo, Bs);
+    }
+    const int cycle = restart > 0 ? std::min(restart, max_iter) : max_iter;
+    double* V = (double*)buf(c, "kry.V", sizeof(double) * (size_t)(cycle + 1) * L + 64);
+    QMat Xm = mat(c, "kry.X", n, m, MST_D, false, false), R = mat(c, "kry.R", n, m, MST_D, false, false);
+    QMat Wm = mat(c, "kry.W", n, m, MST_D, false, false);
+    double* dh = (double*)buf(c, "kry.h", sizeof(double) * (size_t)(2 * cycle + 4) + 64);  // h | Hessenberg column
+    double* dnrm = dh + cycle + 1;
+    ck(c, cudaMemsetAsync(Xm.d.p, 0, sizeof(double) * L, st), "memset");
+    ck(c, cudaMemcpyAsync(R.d.p, Bs.d.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, st), "copy");  // X_0 = 0
+    timed(c, EV_EW, 0, 0, 8.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, nullptr, st); });
+    double r0 = 0.0;
+    read_back(c, dnrm, 1, &r0);
+    std::vector<double> H((size_t)(cycle + 1) * cycle), cs(cycle), sn(cycle), gv(cycle + 1), col(cycle + 1), y(cycle);
+    int steps = 0;
+    bool converged = r0 == 0.0;
+    double beta = r0;
+    while (steps < max_iter && !converged) {
+      if (beta / r0 <= tol) {
+        converged = true;
+        break;
+      }
+      // V_0 = R / beta
+      timed(c, EV_EW, 0, 0, 16.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, V, st); });
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = beta;
+      int k = 0;
+      for (int j = 0; j < cycle; j++) {
+        double* Vj = V + (size_t)j * L;
+        Planes<const double> vj{Vj, (long)m, (long)n * m};
+        Planes<double> w{Wm.d.p, (long)m, (long)n * m};
+        timed(c, EV_F64, 32.0 * n * n * m, 32.0 * n * n * m, 0,
+              [&] { return launch_qgemm_f64(n, n, m, dview(As), vj, w, st); });
+        double* hcol = dh + cycle + 2;  // Hessenberg column j (j + 2 entries) on the device
+        ck(c, cudaMemsetAsync(hcol, 0, sizeof(double) * (j + 2), st), "memset");
+        for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, applied twice
+          timed(c, EV_EW, 0, 0, 8.0 * L * (j + 2),
+                [&] { return launch_block_dot(V, j + 1, Wm.d.p, L, dh, st); });
+          timed(c, EV_EW, 0, 0, 8.0 * L * (j + 3),
+                [&] { return launch_block_sub(Wm.d.p, V, dh, j + 1, L, hcol, st); });
+        }
+        double* Vn = V + (size_t)(j + 1) * L;  // V_{j+1} = W / h_{j+1,j}
+        timed(c, EV_EW, 0, 0, 16.0 * L, [&] { return launch_norm_scale(Wm.d.p, L, hcol + j + 1, Vn, st); });
+        ck(c, cudaMemcpyAsync(col.data(), hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st), "read back");
+        ck(c, cudaStreamSynchronize(st), "stream sync");
+        H[(size_t)j * (cycle + 1) + j + 1] = col[j + 1];
+        k = j + 1;
+        steps++;
+        // Givens rotations: |g_{j+1}| is the GMRES residual, / |c_j| the FOM one
+        for (int i = 0; i < j; i++) {
+          const double a0 = cs[i] * col[i] + sn[i] * col[i + 1];
+          col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+          col[i] = a0;
+        }
+        const double rho = std::hypot(col[j], col[j + 1]);
+        cs[j] = rho > 0.0 ? col[j] / rho : 1.0;
+        sn[j] = rho > 0.0 ? col[j + 1] / rho : 0.0;
+        const double g_prev = gv[j];
+        gv[j + 1] = -sn[j] * g_prev;
+        gv[j] = cs[j] * g_prev;
+        col[j] = rho;
+        for (int i = 0; i <= j; i++) H[(size_t)j * (cycle + 1) + i] = col[i];  // column j of R
+        const double resid = kind == 0 ? std::fabs(gv[j + 1])
+                                       : (cs[j] != 0.0 ? std::fabs(gv[j + 1]) / std::fabs(cs[j]) : INFINITY);
+        if (resid / r0 <= tol || steps >= max_iter || col[j + 1] == 0.0 || H[(size_t)j * (cycle + 1) + j + 1] == 0.0)
+          break;
+      }
+      // y: GMRES R y = g (upper triangular); FOM H_k y = beta e_1, which is
+      // the same triangular system with the last rotation undone
+      // (last diagonal times c_k, last right-hand side divided by c_k).
+      for (int i = k - 1; i >= 0; i--) {
+        double d = H[(size_t)i * (cycle + 1) + i], rhs = gv[i];
+        if (kind == 1 && i == k - 1) {
+          d *= cs[k - 1];
+          rhs = cs[k - 1] != 0.0 ? rhs / cs[k - 1] : 0.0;
+        }
+        for (int l = i + 1; l < k; l++) rhs -= H[(size_t)l * (cycle + 1) + i] * y[l];
+        y[i] = d != 0.0 ? rhs / d : 0.0;
+      }
+      ck(c, cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "copy y");
+      timed(c, EV_EW, 0, 0, 8.0 * L * (k + 2), [&] { return launch_basis_add(Xm.d.p, V, dh, k, L, st); });
+      ck(c, cudaStreamSynchronize(st), "sync");  // y is pageable host memory read by the copy above
+      // explicit residual R = B' - A' X
+      f64(As, Xm, Wm);
+      timed(c, EV_EW, 0, 0, 24.0 * L, [&] { return launch_sub(R.d.p, Bs.d.p, Wm.d.p, L, st); });
+      timed(c, EV_EW, 0, 0, 8.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, nullptr, st); });
+      read_back(c, dnrm, 1, &beta);
+      converged = beta / r0 <= tol;
+    }
+    res.iters = steps;
+    res.converged = converged ? 1 : 0;
+    res.rel_res = r0 > 0.0 ? beta / r0 : 0.0;
+    // true residual ||B - A X|| / ||B||
+    f64(Ao, Xm, Wm);
+    timed(c, EV_EW, 0, 0, 24.0 * L, [&] { return launch_sub(R.d.p, Bo.d.p, Wm.d.p, L, st); });
+    double tn = 0.0, bn = 0.0;
+    timed(c, EV_EW, 0, 0, 8.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, nullptr, st); });
+    read_back(c, dnrm, 1, &tn);
+    timed(c, EV_EW, 0, 0, 8.0 * L, [&] { return launch_norm_scale(Bo.d.p, L, dnrm, nullptr, st); });
+    read_back(c, dnrm, 1, &bn);
+    res.true_rel_res = bn > 0.0 ? tn / bn : tn;
+    store_planes(c, Xm, X, ldx, n, m);
+    ck(c, cudaStreamSynchronize(st), "stream sync");
+  } catch (const QpError& e) {
+    cudaGetLastError();
+    return fail(c, e.code, e.msg);
+  }
+  res.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (out) *out = res;
+  return QPINV_OK;
+}
+
 int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, const int* n, const double* const* A,
                         const long* lda, qpinv_method method, double tol, int max_iter, double* const* X,
                         const long* ldx, qpinv_result* out) {

@@ -63,6 +63,11 @@ class qpinv_cur_result(ctypes.Structure):
                 ("pinv_max_E1_rel", ctypes.c_double), ("time_ms", ctypes.c_double)]
 
 
+class qpinv_krylov_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("true_rel_res", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
 PTR4 = ctypes.c_void_p * 4
 _lib = None
 
@@ -71,7 +76,7 @@ EXPORTS = ("qpinv_default_options", "qpinv_init", "qpinv_set_options", "qpinv_so
            "qpinv_free", "qpinv_last_error", "qpinv_qgemm", "qpinv_penrose", "qpinv_get_stats",
            "qpinv_reset_stats", "qpinv_qgemm_noalloc", "qpinv_alpha_features", "qpinv_alpha_train",
            "qpinv_alpha_predict", "qpinv_alpha_gradient", "qpinv_alpha_weights", "qpinv_cur_complete",
-           "qpinv_toeplitz_filter")
+           "qpinv_toeplitz_filter", "qpinv_global_krylov")
 ALPHA_NFEAT, ALPHA_NWEIGHTS, ALPHA_NTRAIN = 32, 6401, 6337
 
 
@@ -112,6 +117,8 @@ def lib():
                                          ctypes.POINTER(qpinv_cur_result)]
         L.qpinv_toeplitz_filter.argtypes = [vp, vp, i, PTR4, PTR4, i, i, i, d, i, PTR4, PTR4,
                                             ctypes.POINTER(qpinv_result), dp]
+        L.qpinv_global_krylov.argtypes = [vp, vp, i, i, PTR4, l, PTR4, l, i, i, i, d, i, PTR4, l,
+                                          ctypes.POINTER(qpinv_krylov_result)]
         _lib = L
     return _lib
 
@@ -322,6 +329,30 @@ class Context:
                                          float(tol), int(max_iter), ph, psh, ctypes.byref(res), ctypes.byref(err))
         _check(self.h, rc, "qpinv_toeplitz_filter")
         return h, sh, err.value, result_dict(res)
+
+    def global_krylov(self, A, B, kind="gmres", restart=0, precond_iters=0, tol=1e-6, max_iter=3000, X=None,
+                      stream=None):
+        """Gl-QGMRES / Gl-QFOM (qpinv_global_krylov) for A X = B; restart 0 =
+        none; precond_iters > 0: QSAI left preconditioner.  Returns (X, info)."""
+        n, m = A.shape[1], B.shape[2]
+        if X is None:
+            if _is_torch(B):
+                import torch
+                X = torch.empty((4, n, m), dtype=torch.float64, device=B.device)
+            else:
+                X = np.empty((4, n, m))
+        pa, lda, ka = _planes(A)
+        pb, ldb, kb = _planes(B)
+        px, ldx, kx = _planes(X)
+        res = qpinv_krylov_result()
+        rc = lib().qpinv_global_krylov(self.h, _stream_handle(stream), n, m, pa, lda, pb, ldb,
+                                       0 if kind == "gmres" else 1, int(restart), int(precond_iters), float(tol),
+                                       int(max_iter), px, ldx, ctypes.byref(res))
+        _check(self.h, rc, "qpinv_global_krylov")
+        if kx is not X:
+            X[...] = kx
+        return X, dict(iters=res.iters, converged=bool(res.converged), rel_res=res.rel_res,
+                       true_rel_res=res.true_rel_res, time_ms=res.time_ms)
 
     def solve_batched(self, As, method="qhpi19", tol=1e-6, max_iter=100, Xs=None, stream=None):
         import torch

@@ -72,7 +72,7 @@ def system_of(name):
 
 
 @pytest.mark.parametrize("kind", ["gmres", "fom"])
-@pytest.mark.parametrize("precond,restart,system", [(0, 0, "mild"), (2, 0, "mild"), (2, 8, "mild"),
+@pytest.mark.parametrize("precond,restart,system", [(0, 0, "mild"), (2, 0, "mild"), (2, 14, "mild"),
                                                     (0, 5, "gaussian"), (1, 4, "gaussian"),
                                                     (0, 0, "ill"), (2, 0, "ill")])
 def test_small_systems_match_oracle(ctx, kind, precond, restart, system):

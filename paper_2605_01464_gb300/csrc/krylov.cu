@@ -82,12 +82,64 @@ __global__ void k_sub(double* __restrict__ out, const double* __restrict__ a, co
     out[e] = a[e] - b[e];
 }
 
+// C = A B for a skinny right-hand side (m <= kSkinnyMax columns): block i
+// computes row i of C; its threads stride over k, accumulate the Hamilton
+// products for every column, and reduce across the block.  The general GEMM
+// kernels tile 64 x 64 outputs and leave almost every SM idle at m <= 16.
+constexpr int kSkinnyMax = 16;
+__global__ void __launch_bounds__(128) k_qgemm_skinny(Planes<const double> A, Planes<const double> B, int K, int m,
+                                                      Planes<double> C) {
+  __shared__ double sh[4 * kSkinnyMax][4];
+  const int i = blockIdx.x;
+  double acc[4 * kSkinnyMax];
+#pragma unroll
+  for (int t = 0; t < 4 * kSkinnyMax; t++) acc[t] = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const long ai = (long)i * A.ld + k;
+    const double as = A.p[ai], ax = A.p[A.ps + ai], ay = A.p[2 * A.ps + ai], az = A.p[3 * A.ps + ai];
+#pragma unroll
+    for (int l = 0; l < kSkinnyMax; l++) {
+      if (l < m) {
+        const long bi = (long)k * B.ld + l;
+        const double bs = B.p[bi], bx = B.p[B.ps + bi], by = B.p[2 * B.ps + bi], bz = B.p[3 * B.ps + bi];
+        acc[4 * l + 0] += as * bs - ax * bx - ay * by - az * bz;
+        acc[4 * l + 1] += as * bx + ax * bs + ay * bz - az * by;
+        acc[4 * l + 2] += as * by - ax * bz + ay * bs + az * bx;
+        acc[4 * l + 3] += as * bz + ax * by - ay * bx + az * bs;
+      }
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 4 * kSkinnyMax; t++) {
+    if (t < 4 * m) {
+      double v = acc[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[t][w] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * m) {
+    const int t = threadIdx.x, l = t >> 2, q = t & 3;
+    C.p[q * C.ps + (long)i * C.ld + l] = sh[t][0] + sh[t][1] + sh[t][2] + sh[t][3];
+  }
+}
+
 int grid_of(long L) {
   long b = (L + KT - 1) / KT;
   return (int)(b < 1 ? 1 : b > 4096 ? 4096 : b);
 }
 
 }  // namespace
+
+bool skinny_ok(int m) { return m >= 1 && m <= kSkinnyMax; }
+
+cudaError_t launch_qgemm_skinny(int M, int K, int m, const Planes<const double>& A, const Planes<const double>& B,
+                                const Planes<double>& C, cudaStream_t st) {
+  k_qgemm_skinny<<<M, 128, 0, st>>>(A, B, K, m, C);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_block_dot(const double* V, int c, const double* W, long L, double* h, cudaStream_t st) {
   k_block_dot<<<c, KT, 0, st>>>(V, c, W, L, h);

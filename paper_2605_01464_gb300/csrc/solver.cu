@@ -1758,8 +1758,11 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
     load_planes(c, B, ldb, n, m, Bo);
     QMat As = Ao, Bs = Bo;  // the system solved: A X = B, or M A X = M B
     auto f64 = [&](const QMat& P, const QMat& Q, const QMat& R) {
-      timed(c, EV_F64, 32.0 * P.rows * P.cols * Q.cols, 32.0 * P.rows * P.cols * Q.cols, 0,
-            [&] { return launch_qgemm_f64(P.rows, P.cols, Q.cols, dview(P), dview(Q), R.d, st); });
+      const double fl = 32.0 * P.rows * P.cols * Q.cols;
+      timed(c, EV_F64, fl, fl, 0, [&] {
+        return skinny_ok(Q.cols) ? launch_qgemm_skinny(P.rows, P.cols, Q.cols, dview(P), dview(Q), R.d, st)
+                                 : launch_qgemm_f64(P.rows, P.cols, Q.cols, dview(P), dview(Q), R.d, st);
+      });
     };
     if (precond_iters > 0) {
       // M = X_k of QSAI (Alg. 2) from X_0 = alpha A^H, safe alpha, FP64 products
@@ -1816,8 +1819,10 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
         double* Vj = V + (size_t)j * L;
         Planes<const double> vj{Vj, (long)m, (long)n * m};
         Planes<double> w{Wm.d.p, (long)m, (long)n * m};
-        timed(c, EV_F64, 32.0 * n * n * m, 32.0 * n * n * m, 0,
-              [&] { return launch_qgemm_f64(n, n, m, dview(As), vj, w, st); });
+        timed(c, EV_F64, 32.0 * n * n * m, 32.0 * n * n * m, 0, [&] {
+          return skinny_ok(m) ? launch_qgemm_skinny(n, n, m, dview(As), vj, w, st)
+                              : launch_qgemm_f64(n, n, m, dview(As), vj, w, st);
+        });
         double* hcol = dh + cycle + 2;  // Hessenberg column j (j + 2 entries) on the device
         ck(c, cudaMemsetAsync(hcol, 0, sizeof(double) * (j + 2), st), "memset");
         for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, applied twice

@@ -242,6 +242,8 @@ cudaError_t launch_block_sub(double* W, const double* V, const double* h, int c,
 cudaError_t launch_norm_scale(const double* W, long L, double* nrm, double* out, cudaStream_t st);
 cudaError_t launch_basis_add(double* X, const double* V, const double* y, int k, long L, cudaStream_t st);
 cudaError_t launch_sub(double* out, const double* a, const double* b, long L, cudaStream_t st);
+cudaError_t launch_givens(double* col, double* cs, double* sn, double* g, int j, int fom, double* res,
+                          cudaStream_t st);
 // C = A B (FP64) for B with 1..16 columns: one block per row of C.
 bool skinny_ok(int m);
 cudaError_t launch_qgemm_skinny(int M, int K, int m, const Planes<const double>& A, const Planes<const double>& B,

@@ -125,6 +125,31 @@ __global__ void __launch_bounds__(128) k_qgemm_skinny(Planes<const double> A, Pl
   }
 }
 
+// Givens step j of the GMRES / FOM least-squares update, on the device so
+// that the host need not read every Hessenberg column: applies the rotations
+// of steps 0..j-1 to column j (in place; h_{j+1,j} = col[j+1] is kept), forms
+// rotation j, updates g, and writes the residual estimate |g_{j+1}| (GMRES)
+// or |g_{j+1}| / |c_j| (FOM).  Sequential by nature: one thread.
+__global__ void k_givens(double* __restrict__ col, double* __restrict__ cs, double* __restrict__ sn,
+                         double* __restrict__ g, int j, int fom, double* __restrict__ res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < j; i++) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double rho = hypot(a, b);
+  const double c = rho > 0.0 ? a / rho : 1.0, s = rho > 0.0 ? b / rho : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  const double gp = g[j];
+  g[j + 1] = -s * gp;
+  g[j] = c * gp;
+  col[j] = rho;
+  res[j] = fom ? (c != 0.0 ? fabs(g[j + 1]) / fabs(c) : INFINITY) : fabs(g[j + 1]);
+}
+
 int grid_of(long L) {
   long b = (L + KT - 1) / KT;
   return (int)(b < 1 ? 1 : b > 4096 ? 4096 : b);
@@ -137,6 +162,13 @@ bool skinny_ok(int m) { return m >= 1 && m <= kSkinnyMax; }
 cudaError_t launch_qgemm_skinny(int M, int K, int m, const Planes<const double>& A, const Planes<const double>& B,
                                 const Planes<double>& C, cudaStream_t st) {
   k_qgemm_skinny<<<M, 128, 0, st>>>(A, B, K, m, C);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_givens(double* col, double* cs, double* sn, double* g, int j, int fom, double* res,
+                          cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(col, cs, sn, g, j, fom, res);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

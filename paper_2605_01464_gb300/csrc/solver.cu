@@ -1793,14 +1793,23 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
     double* V = (double*)buf(c, "kry.V", sizeof(double) * (size_t)(cycle + 1) * L + 64);
     QMat Xm = mat(c, "kry.X", n, m, MST_D, false, false), R = mat(c, "kry.R", n, m, MST_D, false, false);
     QMat Wm = mat(c, "kry.W", n, m, MST_D, false, false);
-    double* dh = (double*)buf(c, "kry.h", sizeof(double) * (size_t)(2 * cycle + 4) + 64);  // h | Hessenberg column
+    // device: h scratch | norm | Hessenberg columns (rotated in place) | c | s | g | residual estimates
+    const size_t hstride = (size_t)cycle + 1;
+    double* dh = (double*)buf(c, "kry.h", sizeof(double) * ((size_t)cycle + 2 + hstride * cycle + 4 * hstride) + 64);
     double* dnrm = dh + cycle + 1;
+    double* dH = dh + cycle + 2;
+    double* dcs = dH + hstride * cycle;
+    double* dsn = dcs + hstride;
+    double* dg = dsn + hstride;
+    double* dres = dg + hstride;
     ck(c, cudaMemsetAsync(Xm.d.p, 0, sizeof(double) * L, st), "memset");
     ck(c, cudaMemcpyAsync(R.d.p, Bs.d.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, st), "copy");  // X_0 = 0
     timed(c, EV_EW, 0, 0, 8.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, nullptr, st); });
     double r0 = 0.0;
     read_back(c, dnrm, 1, &r0);
-    std::vector<double> H((size_t)(cycle + 1) * cycle), cs(cycle), sn(cycle), gv(cycle + 1), col(cycle + 1), y(cycle);
+    // host copies: rotated columns (upper triangle), c, g, residual estimates
+    std::vector<double> H(hstride * cycle), cs(cycle), gv(hstride), rs(cycle), y(cycle);
+    constexpr int kCheck = 16;  // steps launched between host checks of the residual estimates
     int steps = 0;
     bool converged = r0 == 0.0;
     double beta = r0;
@@ -1809,64 +1818,67 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
         converged = true;
         break;
       }
-      // V_0 = R / beta
+      // V_0 = R / beta; g = beta e_1
       timed(c, EV_EW, 0, 0, 16.0 * L, [&] { return launch_norm_scale(R.d.p, L, dnrm, V, st); });
-      std::fill(H.begin(), H.end(), 0.0);
-      std::fill(gv.begin(), gv.end(), 0.0);
-      gv[0] = beta;
-      int k = 0;
-      for (int j = 0; j < cycle; j++) {
-        double* Vj = V + (size_t)j * L;
-        Planes<const double> vj{Vj, (long)m, (long)n * m};
-        Planes<double> w{Wm.d.p, (long)m, (long)n * m};
-        timed(c, EV_F64, 32.0 * n * n * m, 32.0 * n * n * m, 0, [&] {
-          return skinny_ok(m) ? launch_qgemm_skinny(n, n, m, dview(As), vj, w, st)
-                              : launch_qgemm_f64(n, n, m, dview(As), vj, w, st);
-        });
-        double* hcol = dh + cycle + 2;  // Hessenberg column j (j + 2 entries) on the device
-        ck(c, cudaMemsetAsync(hcol, 0, sizeof(double) * (j + 2), st), "memset");
-        for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, applied twice
-          timed(c, EV_EW, 0, 0, 8.0 * L * (j + 2),
-                [&] { return launch_block_dot(V, j + 1, Wm.d.p, L, dh, st); });
-          timed(c, EV_EW, 0, 0, 8.0 * L * (j + 3),
-                [&] { return launch_block_sub(Wm.d.p, V, dh, j + 1, L, hcol, st); });
+      ck(c, cudaMemsetAsync(dg, 0, sizeof(double) * hstride, st), "memset");
+      c->h_pin[0] = beta;
+      ck(c, cudaMemcpyAsync(dg, c->h_pin, sizeof(double), cudaMemcpyHostToDevice, st), "copy beta");
+      // Steps are launched kCheck at a time without host synchronisation; the
+      // host then finds the first step whose residual estimate meets the
+      // tolerance (or whose h_{j+1,j} is 0).  Steps launched beyond it are
+      // discarded: the GMRES / FOM iterate of step k uses columns 0..k-1 only.
+      int k = 0, j = 0;
+      bool done = false;
+      while (!done) {
+        const int j0 = j, nb = std::min({kCheck, cycle - j, max_iter - steps});  // >= 1: not done
+        for (int b = 0; b < nb; b++, j++) {
+          double* Vj = V + (size_t)j * L;
+          Planes<const double> vj{Vj, (long)m, (long)n * m};
+          Planes<double> w{Wm.d.p, (long)m, (long)n * m};
+          timed(c, EV_F64, 32.0 * n * n * m, 32.0 * n * n * m, 0, [&] {
+            return skinny_ok(m) ? launch_qgemm_skinny(n, n, m, dview(As), vj, w, st)
+                                : launch_qgemm_f64(n, n, m, dview(As), vj, w, st);
+          });
+          double* hcol = dH + hstride * j;  // Hessenberg column j (j + 2 entries)
+          ck(c, cudaMemsetAsync(hcol, 0, sizeof(double) * (j + 2), st), "memset");
+          for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, applied twice
+            timed(c, EV_EW, 0, 0, 8.0 * L * (j + 2), [&] { return launch_block_dot(V, j + 1, Wm.d.p, L, dh, st); });
+            timed(c, EV_EW, 0, 0, 8.0 * L * (j + 3),
+                  [&] { return launch_block_sub(Wm.d.p, V, dh, j + 1, L, hcol, st); });
+          }
+          double* Vn = V + (size_t)(j + 1) * L;  // V_{j+1} = W / h_{j+1,j}
+          timed(c, EV_EW, 0, 0, 16.0 * L, [&] { return launch_norm_scale(Wm.d.p, L, hcol + j + 1, Vn, st); });
+          timed(c, EV_EW, 0, 0, 8.0 * (3 * j + 8),
+                [&] { return launch_givens(hcol, dcs, dsn, dg, j, kind, dres, st); });
         }
-        double* Vn = V + (size_t)(j + 1) * L;  // V_{j+1} = W / h_{j+1,j}
-        timed(c, EV_EW, 0, 0, 16.0 * L, [&] { return launch_norm_scale(Wm.d.p, L, hcol + j + 1, Vn, st); });
-        ck(c, cudaMemcpyAsync(col.data(), hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st), "read back");
+        // the new columns' rows 0 .. j (rotated R and raw h_{j+1,j}), c, g, estimates
+        ck(c, cudaMemcpy2DAsync(H.data() + hstride * j0, sizeof(double) * hstride, dH + hstride * j0,
+                                sizeof(double) * hstride, sizeof(double) * (j + 1), nb, cudaMemcpyDeviceToHost, st),
+           "read columns");
+        ck(c, cudaMemcpyAsync(cs.data() + j0, dcs + j0, sizeof(double) * nb, cudaMemcpyDeviceToHost, st), "read c");
+        ck(c, cudaMemcpyAsync(rs.data() + j0, dres + j0, sizeof(double) * nb, cudaMemcpyDeviceToHost, st), "read r");
+        ck(c, cudaMemcpyAsync(gv.data(), dg, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st), "read g");
         ck(c, cudaStreamSynchronize(st), "stream sync");
-        H[(size_t)j * (cycle + 1) + j + 1] = col[j + 1];
-        k = j + 1;
-        steps++;
-        // Givens rotations: |g_{j+1}| is the GMRES residual, / |c_j| the FOM one
-        for (int i = 0; i < j; i++) {
-          const double a0 = cs[i] * col[i] + sn[i] * col[i + 1];
-          col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-          col[i] = a0;
+        for (int t = j0; t < j; t++) {
+          steps++;
+          k = t + 1;
+          if (rs[t] / r0 <= tol || steps >= max_iter || H[hstride * t + t + 1] == 0.0 || !(rs[t] == rs[t])) {
+            done = true;
+            break;
+          }
         }
-        const double rho = std::hypot(col[j], col[j + 1]);
-        cs[j] = rho > 0.0 ? col[j] / rho : 1.0;
-        sn[j] = rho > 0.0 ? col[j + 1] / rho : 0.0;
-        const double g_prev = gv[j];
-        gv[j + 1] = -sn[j] * g_prev;
-        gv[j] = cs[j] * g_prev;
-        col[j] = rho;
-        for (int i = 0; i <= j; i++) H[(size_t)j * (cycle + 1) + i] = col[i];  // column j of R
-        const double resid = kind == 0 ? std::fabs(gv[j + 1])
-                                       : (cs[j] != 0.0 ? std::fabs(gv[j + 1]) / std::fabs(cs[j]) : INFINITY);
-        if (resid / r0 <= tol || steps >= max_iter || col[j + 1] == 0.0 || H[(size_t)j * (cycle + 1) + j + 1] == 0.0)
-          break;
+        if (j >= cycle) done = true;
       }
       // y: GMRES R y = g (upper triangular); FOM H_k y = beta e_1, which is
       // the same triangular system with the last rotation undone
       // (last diagonal times c_k, last right-hand side divided by c_k).
       for (int i = k - 1; i >= 0; i--) {
-        double d = H[(size_t)i * (cycle + 1) + i], rhs = gv[i];
+        double d = H[hstride * i + i], rhs = gv[i];
         if (kind == 1 && i == k - 1) {
           d *= cs[k - 1];
           rhs = cs[k - 1] != 0.0 ? rhs / cs[k - 1] : 0.0;
         }
-        for (int l = i + 1; l < k; l++) rhs -= H[(size_t)l * (cycle + 1) + i] * y[l];
+        for (int l = i + 1; l < k; l++) rhs -= H[hstride * l + i] * y[l];
         y[i] = d != 0.0 ? rhs / d : 0.0;
       }
       ck(c, cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "copy y");

@@ -133,12 +133,15 @@ __global__ void __launch_bounds__(128) k_qgemm_skinny(Planes<const double> A, Pl
 __global__ void k_givens(double* __restrict__ col, double* __restrict__ cs, double* __restrict__ sn,
                          double* __restrict__ g, int j, int fom, double* __restrict__ res) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // the running entry stays in a register: every load is of an entry not yet
+  // written, so the loads pipeline and only the rotation chain is serial
+  double a = col[0];
   for (int i = 0; i < j; i++) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
+    const double b = col[i + 1], c = cs[i], s = sn[i];
+    col[i] = c * a + s * b;
+    a = -s * a + c * b;
   }
-  const double a = col[j], b = col[j + 1];
+  const double b = col[j + 1];
   const double rho = hypot(a, b);
   const double c = rho > 0.0 ? a / rho : 1.0, s = rho > 0.0 ? b / rho : 0.0;
   cs[j] = c;

@@ -36,13 +36,26 @@ __global__ void __launch_bounds__(KT) k_block_dot(const double* __restrict__ V, 
   if (threadIdx.x == 0) h[blockIdx.x] = s;
 }
 
-// W -= sum_{i<c} h[i] V_i; block 0 also adds h into the Hessenberg column.
-__global__ void k_block_sub(double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ h, int c,
-                            long L, double* __restrict__ hcol) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
-    double w = W[e];
-    for (int i = 0; i < c; i++) w -= h[i] * V[(long)i * L + e];
-    W[e] = w;
+// W += sign * sum_{i<c} h[i] V_i.  A block takes 32 consecutive elements
+// (one per lane, coalesced across the basis), its warps split the basis
+// index i, and the warps' partial sums are added in a fixed order.  Block 0
+// also adds h into the Hessenberg column when hcol is given.
+constexpr int kCombWarps = 16;
+__global__ void __launch_bounds__(32 * kCombWarps) k_block_combine(double* __restrict__ W, const double* __restrict__ V,
+                                                                   const double* __restrict__ h, int c, long L,
+                                                                   double sign, double* __restrict__ hcol) {
+  __shared__ double part[kCombWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long e = (long)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < L)
+    for (int i = w; i < c; i += kCombWarps) s += h[i] * V[(long)i * L + e];
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e < L) {
+    double t = 0.0;
+    for (int q = 0; q < kCombWarps; q++) t += part[q][lane];
+    W[e] += sign * t;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && hcol)
     for (int i = 0; i < c; i++) hcol[i] += h[i];
@@ -64,16 +77,6 @@ __global__ void __launch_bounds__(1024) k_norm_scale(const double* W, long L, do
   const double t = tot;
   if (out && t > 0.0)
     for (long e = threadIdx.x; e < L; e += blockDim.x) out[e] = W[e] / t;
-}
-
-// X += sum_{i<k} y[i] V_i
-__global__ void k_basis_add(double* __restrict__ X, const double* __restrict__ V, const double* __restrict__ y, int k,
-                            long L) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
-    double x = X[e];
-    for (int i = 0; i < k; i++) x += y[i] * V[(long)i * L + e];
-    X[e] = x;
-  }
 }
 
 // out = a - b
@@ -184,7 +187,7 @@ cudaError_t launch_block_dot(const double* V, int c, const double* W, long L, do
 
 cudaError_t launch_block_sub(double* W, const double* V, const double* h, int c, long L, double* hcol,
                              cudaStream_t st) {
-  k_block_sub<<<grid_of(L), KT, 0, st>>>(W, V, h, c, L, hcol);
+  k_block_combine<<<(int)((L + 31) / 32), 32 * kCombWarps, 0, st>>>(W, V, h, c, L, -1.0, hcol);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -196,7 +199,7 @@ cudaError_t launch_norm_scale(const double* W, long L, double* nrm, double* out,
 }
 
 cudaError_t launch_basis_add(double* X, const double* V, const double* y, int k, long L, cudaStream_t st) {
-  k_basis_add<<<grid_of(L), KT, 0, st>>>(X, V, y, k, L);
+  k_block_combine<<<(int)((L + 31) / 32), 32 * kCombWarps, 0, st>>>(X, V, y, k, L, 1.0, nullptr);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -372,9 +372,9 @@ def bench_cur(args, torch, qpinv):
     """CUR image completion (Sec. 5.1): a 512 x 768 synthetic colour image
     (seed 16) with 70 % of the pixels removed (seed 17), rank-60 CUR with
     U = C_J^+ C R_I^+, 25 iterations with fresh index sets (seed 18), Gaussian
-    filter sigma = 0.5, QHPI19 pseudoinverses (MIXED, rel. tol 1e-12).  One
-    step = one whole completion; the CPU baseline runs the FP64 oracle on the
-    same completion."""
+    filter sigma = 0.5, QHPI19 pseudoinverses (rel. tol 1e-12) in mixed and
+    in FP64 precision, the faster reported.  One step = one whole completion;
+    the CPU baseline runs the FP64 oracle on the same completion."""
     import numpy as np
     from paper_2605_01464_gb300 import inputs
     m, n, r, T = 512, 768, 60, 25
@@ -383,34 +383,48 @@ def bench_cur(args, torch, qpinv):
     Is, Js = inputs.cur_index_sets(m, n, r, T, 18)
     M = A * mask
     Md, maskd = torch.from_numpy(M).cuda(), torch.from_numpy(mask).cuda()
-    ctx = qpinv.Context(0, profile=True)
     stream = torch.cuda.current_stream()
-
-    def run(Mx, mx):
-        return ctx.cur_complete(Mx, mx, Is, Js, args.method, tol=1e-12, max_iter=200, sigma=0.5, stream=stream)
-
+    # The inner pseudoinverses are small (residual side 60): they are timed in
+    # the default mixed precision and in FP64 (CUDA-core products, fewer
+    # launches per product); the line reports the faster.  Timing runs have
+    # kernel profiling off; one extra profiled completion gives the kernel
+    # figures.
+    timing = {}
     with ClockSampler(0) as clk:
-        for _ in range(args.warmup):
+        for prec in ("mixed", "fp64"):
+            ctx = qpinv.Context(0, precision=prec)
+
+            def run(Mx, mx):
+                return ctx.cur_complete(Mx, mx, Is, Js, args.method, tol=1e-12, max_iter=200, sigma=0.5,
+                                        stream=stream)
+
+            for _ in range(args.warmup):
+                run(Md, maskd)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                C, info = run(Md, maskd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            # end to end: host image, mask and result (pinned), copies in the timed region
+            Mh = torch.from_numpy(M).pin_memory().numpy()
+            mh = torch.from_numpy(mask).pin_memory().numpy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                Ch, _ = run(Mh, mh)
+            torch.cuda.synchronize()
+            ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+            ctx.configure(profile=True)
+            ctx.reset_stats()
             run(Md, maskd)
-        ctx.reset_stats()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            C, info = run(Md, maskd)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        st = ctx.stats()
-        # end to end: host image, mask and result (pinned), copies in the timed region
-        Mh = torch.from_numpy(M).pin_memory().numpy()
-        mh = torch.from_numpy(mask).pin_memory().numpy()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            Ch, _ = run(Mh, mh)
-        torch.cuda.synchronize()
-        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+            st = ctx.stats()
+            ctx.close()
+            timing[prec] = (ms, ms_e2e, st, C, info)
+    best = min(timing, key=lambda k: timing[k][0])
+    ms, ms_e2e, st, C, info = timing[best]
     C = C.cpu().numpy()
     mse = np.mean((C[1:] - A[1:]) ** 2)
     psnr = 10 * math.log10(1.0 / mse)
@@ -426,15 +440,16 @@ def bench_cur(args, torch, qpinv):
     print(json.dumps({
         "metric": "CUR image completions/s (512x768, 70% missing, rank 60, 25 iterations)", "value": 1e3 / ms,
         "unit": "completions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (exact-slice products)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "512x768 synthetic colour image (pure quaternions), 70%% of pixels removed, CUR rank 60 "
                                "with U = C_J^+ C R_I^+, 25 impute-reconstruct iterations, Gaussian filter 0.5, "
-                               "%s pseudoinverses (mixed precision, rel. tol 1e-12)" % args.method.upper(),
+                               "%s pseudoinverses (%s precision, rel. tol 1e-12)" % (args.method.upper(), best),
+                   "precision_ms": {k: v[0] for k, v in timing.items()},
                    "l2": "working set of 19 MB per image plane set fits in L2; no flush"},
         "e2e": {"value": 1e3 / ms_e2e, "unit": "completions/s", "h2d_bytes_per_step": M.nbytes + mask.nbytes,
                 "d2h_bytes_per_step": C.nbytes},
-        "gpu_launches": st["kernel_launches"] // max(args.steps, 1),
+        "gpu_launches": st["kernel_launches"],
         "roofline": kernel_rooflines(st)[0], "cpu_baseline": base,
         "result": {"psnr_db": psnr, "psnr_masked_db": 10 * math.log10(1.0 / np.mean((M[1:] - A[1:]) ** 2)),
                    "ssim": _ssim(C, A), "pinv": info, "paper_kodim16": {"psnr_db": 27.91, "ssim": 0.8126,
@@ -541,7 +556,7 @@ def bench_krylov(args, torch, qpinv):
     m = 3 (the line's value); the rest are timed the same way and reported."""
     import numpy as np
     from paper_2605_01464_gb300 import inputs
-    ctx = qpinv.Context(0, profile=True)
+    ctx = qpinv.Context(0)  # timing with kernel profiling off; one profiled solve for the kernel figures
     stream = torch.cuda.current_stream()
     variants = (("fom", "fom", 0), ("gmres", "gmres", 0), ("prec_fom", "fom", 2), ("prec_gmres", "gmres", 2))
     out, line = {}, None
@@ -570,14 +585,21 @@ def bench_krylov(args, torch, qpinv):
                              "rel_res": info["rel_res"], "true_rel_res": info["true_rel_res"],
                              "gpu_launches": st["kernel_launches"] // steps}
                 if m == 3 and name == "prec_gmres":
+                    ctx.configure(profile=True)
+                    ctx.reset_stats()
+                    ctx.global_krylov(Ad, Bd, kind, precond_iters=pk, tol=1e-6, max_iter=3000, stream=stream)
+                    st = ctx.stats()
+                    ctx.configure(profile=False)
+                    steps_prof = 1
                     gbs = st["ew_bytes"] / (st["ew_ms"] * 1e-3) / 1e9 if st["ew_ms"] > 0 else None
                     roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                             "frac": gbs / hbm if gbs else None, "traffic": None,
                             "kernel": "global Gram-Schmidt / update kernels (k_block_dot, k_block_sub, "
                                       "k_norm_scale, k_basis_add; bytes counted per launch)",
-                            "ew_ms_per_solve": st["ew_ms"] / steps, "f64_gemm_ms_per_solve": st["f64_gemm_ms"] / steps,
+                            "ew_ms_per_solve": st["ew_ms"] / steps_prof,
+                            "f64_gemm_ms_per_solve": st["f64_gemm_ms"] / steps_prof,
                             "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % src}
-                    line = (ms, st["kernel_launches"] // steps, roof)
+                    line = (ms, st["kernel_launches"] // steps_prof, roof)
                     Ah = torch.from_numpy(A).pin_memory().numpy()
                     Bh = torch.from_numpy(B).pin_memory().numpy()
                     torch.cuda.synchronize()

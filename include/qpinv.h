@@ -332,7 +332,10 @@ int qpinv_toeplitz_filter(qpinv_ctx* ctx, void* stream, int N, const double* con
  *   - out (host, may be NULL): iterations, convergence, the relative residual
  *     of the system solved and the true one ||B - A X|| / ||B||.
  *   - Errors: QPINV_E_INVALID for bad sizes, kind, restart < 0,
- *     precond_iters outside [0, 100], max_iter outside [1, 100000]. */
+ *     precond_iters outside [0, 100], max_iter outside [1, 100000], or a
+ *     cycle (restart, or max_iter without restarts) above 10000 steps: one
+ *     cycle keeps (cycle + 1) basis blocks and a (cycle + 1) x cycle
+ *     Hessenberg matrix; QPINV_E_NOMEM when they do not fit. */
 typedef struct {
   int iters;           /* Arnoldi steps, over all restarts */
   int converged;       /* 1 if the stop tolerance was met */

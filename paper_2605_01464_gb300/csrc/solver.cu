@@ -40,6 +40,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -1665,6 +1666,9 @@ int qpinv_cur_complete(qpinv_ctx* c, void* stream, int m, int n, const double* c
     }
     store_planes(c, Cm, C, ldc, m, n);
     ck(c, cudaStreamSynchronize(st), "stream sync");
+  } catch (const std::bad_alloc&) {
+    cudaGetLastError();
+    return fail(c, QPINV_E_NOMEM, "host allocation failed");
   } catch (const QpError& e) {
     cudaGetLastError();
     return fail(c, e.code, e.msg);
@@ -1730,6 +1734,9 @@ int qpinv_toeplitz_filter(qpinv_ctx* c, void* stream, int N, const double* const
     ck(c, cudaStreamSynchronize(st), "stream sync");
     if (err) *err = den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
     if (pinv_out) *pinv_out = pr;
+  } catch (const std::bad_alloc&) {
+    cudaGetLastError();
+    return fail(c, QPINV_E_NOMEM, "host allocation failed");
   } catch (const QpError& e) {
     cudaGetLastError();
     return fail(c, e.code, e.msg);
@@ -1745,6 +1752,10 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
       !planes_ok((const double* const*)X) || (kind != 0 && kind != 1) || restart < 0 || precond_iters < 0 ||
       precond_iters > 100 || !(tol >= 0.0) || max_iter < 1 || max_iter > 100000)
     return fail(c, QPINV_E_INVALID, "invalid argument");
+  // the basis and the Hessenberg matrix of one cycle grow with its length:
+  // (cycle + 1) blocks and (cycle + 1) x cycle doubles, on the device and the host
+  if ((restart > 0 ? std::min(restart, max_iter) : max_iter) > 10000)
+    return fail(c, QPINV_E_INVALID, "cycle longer than 10000 steps: give restart <= 10000");
   const auto t_start = std::chrono::steady_clock::now();
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1905,6 +1916,9 @@ int qpinv_global_krylov(qpinv_ctx* c, void* stream, int n, int m, const double* 
     res.true_rel_res = bn > 0.0 ? tn / bn : tn;
     store_planes(c, Xm, X, ldx, n, m);
     ck(c, cudaStreamSynchronize(st), "stream sync");
+  } catch (const std::bad_alloc&) {
+    cudaGetLastError();
+    return fail(c, QPINV_E_NOMEM, "host allocation failed");
   } catch (const QpError& e) {
     cudaGetLastError();
     return fail(c, e.code, e.msg);

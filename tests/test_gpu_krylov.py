@@ -123,7 +123,7 @@ def test_host_pointers_match_device(ctx):
 
 def test_invalid_arguments(ctx, qp):
     A, B = small_system()
-    for kw in (dict(restart=-1), dict(precond_iters=101), dict(max_iter=0)):
+    for kw in (dict(restart=-1), dict(precond_iters=101), dict(max_iter=0), dict(max_iter=20000)):
         args = dict(kind="gmres", restart=0, precond_iters=0, tol=1e-6, max_iter=10)
         args.update(kw)
         with pytest.raises(qp.QpinvError) as e:

@@ -158,7 +158,7 @@ bool emu_fused_ok(int K, int S);
 cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st);
 bool tc_supported();
 
-// Batched solver (batched.cu).
+// Batched solver (batched_impl.cuh: host side in batched.cu, kernels in batched_tile<t>.cu).
 struct BatchResultHost {
   int status, iters, side, gemms;
   double alpha, delta, delta_rel;

@@ -123,3 +123,18 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(cur, "pinv", lambda A, *a: (oracle.adjoint(A), {}))
     with pytest.raises(AssertionError):
         check_exact_rank(3, 3)
+
+
+def test_optimal_form_improves_and_cross_form_diverges_on_smooth_image():
+    # The evidence behind using U = C_J^+ C R_I^+ for completion: with index
+    # sets drawn uniformly at random, the cross form's W^+ amplifies the
+    # missing-pixel error every iteration, while the optimal form (a pair of
+    # projections) improves on the masked image
+    A = I.synthetic_rgb_image(64, 96, 16)
+    mask = I.completion_mask(64, 96, 0.3, 17)
+    Is, Js = I.cur_index_sets(64, 96, 10, 8, 18)
+    M = A * mask
+    Cx, _ = cur.cur_complete(M, mask, Is, Js, sigma=0.0, cross=True)
+    Co, _ = cur.cur_complete(M, mask, Is, Js, sigma=0.0, cross=False)
+    assert cur.psnr(Co, A) > cur.psnr(M, A) + 10.0
+    assert cur.psnr(Cx, A) < cur.psnr(M, A)

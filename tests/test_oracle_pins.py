@@ -281,14 +281,14 @@ def test_unfactorized_order_one_is_identity_step():
     assert np.array_equal(X, X0)
 
 
-@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19"])
+@pytest.mark.parametrize("method", ["ns", "qsai", "qrapid", "qhpi19", "qhpim"])
 def test_left_and_right_forms_agree(method):
     A = I.gaussian_quaternion(10, 7, 21)
     X = oracle.init_x0(A, oracle.alpha(A, "safe"))
     Y = X.copy()
     for _ in range(3):
-        X = oracle.step(A, X, method, N=2, side="right")
-        Y = oracle.step(A, Y, method, N=2, side="left")
+        X = oracle.step(A, X, method, N=2, side="right", order=6)
+        Y = oracle.step(A, Y, method, N=2, side="left", order=6)
         assert rel(X, Y) <= 1e-12
 
 

@@ -190,7 +190,8 @@ int qpinv_init(qpinv_ctx** ctx, int device, const qpinv_options* opt);
 /* Replaces the options of an existing context. */
 int qpinv_set_options(qpinv_ctx* ctx, const qpinv_options* opt);
 
-/* Single solve (Algorithms 1-3 and Newton-Schulz; stop rules of Sec. 4 and
+/* Single solve (Algorithms 1-3, Newton-Schulz and the unfactorized iteration of
+ * Definition 1; stop rules of Sec. 4 and
  * the plateau rule).  A: four planes of an m x n matrix (lda >= n); X: four
  * planes of the n x m output (ldx >= m), caller-owned.  tol: stop tolerance
  * of the chosen rule; max_iter >= 1 bounds the X-updates.  out (host,
@@ -211,7 +212,8 @@ int qpinv_solve(qpinv_ctx* ctx, void* stream, int m, int n, const double* const 
  * E1..E4 for each, in double-FP32 arithmetic (an unevaluated sum of two
  * floats, ~2^-46: small blocks are often rank deficient, and null-space
  * noise grows by ~kappa^2 over a solve).  Options used: stop_rule, qrapid_N,
- * alpha_mode (SAFE, FRO or USER; SPECTRAL and LEARNED run as SAFE).
+ * hyper_order, batched_tile, alpha_mode (SAFE, FRO or USER; SPECTRAL and
+ * LEARNED run as SAFE).
  * out[b] (host array, may be NULL) receives each outcome; tc_iters and
  * polish_iters are 0; time_ms is the whole call.  Matrices are independent:
  * a non-finite A gives QPINV_NONFINITE_INPUT for that matrix only. */

@@ -420,3 +420,17 @@ def test_planted_mistakes_are_caught(mutation, check):
             check()
     finally:
         oracle.set_mutation(0)
+
+
+@pytest.mark.parametrize("method", ["ns", "qsai", "qhpi19", "qhpim"])
+def test_initialization_theorem_threshold(method):
+    # Thm. 1: X_0 = alpha A^H converges iff rho(R_0) = max |1 - alpha sigma_i^2| < 1,
+    # i.e. alpha < 2 / sigma_1^2 (sigma_1 from LAPACK on the complex representation)
+    A = I.gaussian_quaternion(12, 9, 43)
+    s1 = np.linalg.svd(I.chi(A), compute_uv=False)[0]
+    _, below = oracle.solve(A, method, tol=1e-13, max_iter=400, alpha_mode="user", alpha_user=1.9 / s1 ** 2,
+                            order=5)
+    assert below["status"] in ("converged", "plateau") and max(below["E_rel"]) <= 1e-12, below
+    _, above = oracle.solve(A, method, tol=1e-13, max_iter=400, alpha_mode="user", alpha_user=2.1 / s1 ** 2,
+                            order=5)
+    assert above["status"] == "diverged", above

@@ -138,3 +138,14 @@ def test_optimal_form_improves_and_cross_form_diverges_on_smooth_image():
     Co, _ = cur.cur_complete(M, mask, Is, Js, sigma=0.0, cross=False)
     assert cur.psnr(Co, A) > cur.psnr(M, A) + 10.0
     assert cur.psnr(Cx, A) < cur.psnr(M, A)
+
+
+def test_full_index_sets_reproduce_the_filled_matrix():
+    # r = min(m, n) with every column chosen: C_J C_J^+ C R_I^+ R_I = C when
+    # R_I has full column rank, so the loop returns its starting matrix
+    A = I.synthetic_rgb_image(12, 8, 16)
+    mask = I.completion_mask(12, 8, 0.5, 17)
+    Is = np.array([[0, 2, 3, 5, 6, 8, 9, 11]] * 3, dtype=np.int32)
+    Js = np.array([list(range(8))] * 3, dtype=np.int32)
+    C, _ = cur.cur_complete(A * mask, mask, Is, Js, sigma=0.0, tol=1e-14, max_iter=500)
+    assert rel(C, A * mask) <= 1e-10

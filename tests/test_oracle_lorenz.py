@@ -77,3 +77,14 @@ def test_planted_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(lorenz, "data_matrix", lambda x, p, t0: raw(x, p, t0).transpose(0, 2, 1).copy())
     with pytest.raises(AssertionError):
         check_structure()
+
+
+def test_single_tap_filter_is_the_quaternion_quotient():
+    # p = 0: X = [x(t0)], h_0 = x(t0)^-1 s(t0) and s_hat = s exactly
+    x = I.gaussian_quaternion(1, 5, 61)[:, 0, :]
+    s = I.gaussian_quaternion(1, 5, 62)[:, 0, :]
+    h, s_hat, eps, info = lorenz.design(x, s, 0, 2, "qsai", tol=1e-15)
+    q = x[:, 2]
+    qinv = np.array([q[0], -q[1], -q[2], -q[3]]) / np.dot(q, q)
+    assert np.allclose(h[:, 0, 0], oracle.qmul(qinv, s[:, 2]), rtol=0, atol=1e-14)
+    assert eps <= 1e-15

@@ -100,9 +100,24 @@ class ClockSampler:
 
 
 def make_workload(n, device):
+    """(A, U, sigma, V) of the square log-spaced workload."""
     from paper_2605_01464_gb300 import inputs
-    A, U, s, V = inputs.logspaced_square(n, 1e-6, seed_u=1, seed_v=2, device=device)
-    return A
+    return inputs.logspaced_square(n, 1e-6, seed_u=1, seed_v=2, device=device)
+
+
+def oracle_pinv_error(X, U, sigma, V):
+    """Relative Frobenius error of the GPU's X against the FP64 oracle's exact
+    pseudoinverse V Sigma^-1 U^H of the generator's factors (CPU-baseline leg:
+    runs on the host cores after the timed region)."""
+    import numpy as np
+
+    import oracle
+
+    t0 = time.perf_counter()
+    want = oracle.pinv_from_svd(U, sigma, V)
+    X = np.asarray(X)
+    err = float(np.linalg.norm(X - want) / np.linalg.norm(want))
+    return err, time.perf_counter() - t0
 
 
 def cpu_baseline_sample(A, iters, budget_s=30.0):
@@ -133,7 +148,7 @@ def run_reference(args, rank):
 
     from oracle import build as obuild
     obuild.build()
-    A = make_workload(args.n, "cpu")
+    A = make_workload(args.n, "cpu")[0]
     steps = []
     for k in range(args.warmup + args.steps):
         s = cpu_baseline_sample(A, WORKLOAD_ITERS)
@@ -186,11 +201,66 @@ def kernel_qgemm(args, torch, qpinv):
     return 0
 
 
+def gemm_target_records(torch, qpinv, local, sizes=(4096, 8192), warmup=2, reps=5):
+    """Roofline entries of the single-pass BF16 tensor-core quaternion GEMM
+    (k_qgemm_tc, one BF16 term per operand) at n x n x n, n >= 4096: the
+    kernel's own CUDA-event time per launch (library events on the launch
+    stream), 32 flops per quaternion multiply-add, against the measured BF16
+    burst peak (a kernel timed alone), with the clocks sampled meanwhile."""
+    bf16_burst, _, _, src = peaks()
+    out = []
+    gen = torch.Generator(device="cuda:%d" % local)
+    for n in sizes:
+        gen.manual_seed(7000 + n)
+        A = torch.randn((4, n, n), dtype=torch.float64, device="cuda:%d" % local, generator=gen)
+        B = torch.randn((4, n, n), dtype=torch.float64, device="cuda:%d" % local, generator=gen)
+        C = torch.empty_like(A)
+        ctx = qpinv.Context(local, profile=True)
+        for _ in range(warmup):
+            ctx.qgemm(A, B, precision="tc", split_level=1, C=C)
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        with ClockSampler(local) as clk:
+            for _ in range(reps):
+                ctx.qgemm(A, B, precision="tc", split_level=1, C=C)
+            torch.cuda.synchronize()
+        st = ctx.stats()
+        ctx.close()
+        launches = max(st["tc_gemm_launches"], 1)
+        ms = st["tc_gemm_ms"] / launches
+        alg = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
+        out.append({"bound": "tensor", "achieved": alg, "peak": bf16_burst, "unit": "TFLOP/s",
+                    "frac": alg / bf16_burst, "traffic": None,
+                    "kernel": "k_qgemm_tc (single-pass BF16 quaternion GEMM, %d x %d x %d)" % (n, n, n),
+                    "launches": launches, "ms_per_launch": ms, "achieved_issued": alg, "frac_issued": alg / bf16_burst,
+                    "peak_source": "%s bf16_tflops burst (MEASURED_PEAKS.json): the kernel is timed alone" % src,
+                    "clocks": clk.summary()})
+        del A, B, C
+        torch.cuda.empty_cache()
+    return out
+
+
+# CTA GEMM engines of qpinv_solve_batched by index (qpinv_options.batched_tile)
+BATCH_ENGINES = ["16x16", "32x32", "64x32", "32x64", "64x64", "tc (tensor-core exact slices)"]
+
+
+def batched_flops(m, n, method, steps):
+    """Algorithmic flops of one batched solve: 32 per quaternion multiply-add
+    of every product -- per iteration the method's products on the residual
+    side s = min(m, n) (QHPI19: 2 s^2 l + 5 s^3 with l = max(m, n); QSAI
+    2 s^2 l + 4 s^3; NS 2 s^2 l) -- plus the 4 Penrose products 2 m n (m + n)."""
+    s, l = min(m, n), max(m, n)
+    per = {"qhpi19": 2 * s * s * l + 5 * s ** 3, "qsai": 2 * s * s * l + 4 * s ** 3, "ns": 2 * s * s * l}
+    return 32.0 * (steps * per.get(method, per["qhpi19"]) + 2.0 * m * n * (m + n))
+
+
 def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     """4096 pure-quaternion blocks (m, n ~ U[16, 256], rank ~ U[4, min(m, n)])
     solved by qpinv_solve_batched in one persistent launch per step.  With N
     ranks each GPU solves its own 4096 blocks (weak scaling; no collective on
     the data path, only the timing reduction)."""
+    import numpy as np
+
     from paper_2605_01464_gb300 import inputs
     dist = None
     if world > 1:
@@ -220,15 +290,43 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     e1 = [i["E_rel"][0] for i in infos]
     its = [i["iters"] for i in infos]
     st = ctx.stats()
+    # steps computed per matrix: the returned iterations plus the rejected
+    # step of a plateau stop
+    flops = sum(batched_flops(a.shape[1], a.shape[2], args.method, i["iters"] + (i["status"] == "plateau"))
+                for a, i in zip(mats, infos))
+    bf16_burst, bf16_sust, _, src = peaks()
+    ach = flops / (dt / args.steps) / 1e12
+    roof = {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s", "frac": ach / bf16_sust,
+            "traffic": None, "kernel": "the persistent batched kernel (%s engine), whole call" %
+                                       BATCH_ENGINES[st["batched_tile"]],
+            "algorithmic_flops_per_step": flops,
+            "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sample = list(range(0, 4096, 256))  # 16 evenly spaced blocks
+        t0 = time.perf_counter()
+        errs = []
+        for b in sample:
+            xo, _ = oracle.solve(mats[b], args.method, tol=args.tol, max_iter=200)
+            errs.append(float(np.linalg.norm(Xs[b].cpu().numpy() - xo) / np.linalg.norm(xo)))
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": len(sample) / t_cpu, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the FP64 oracle's %s on 16 evenly spaced blocks of the batch (%.1f s); the GPU X of "
+                         "those blocks against the oracle's: max relative error %.2e"
+                         % (args.method, t_cpu, max(errs)),
+               "x_relerr_vs_oracle_max": max(errs)}
     print(json.dumps({"metric": "batched pinv solves/s", "value": solves / dt, "unit": "solves/s",
                       "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-                      "higher_is_better": True, "scaling": "weak", "dtype": "df32 (double-FP32)", "data": "synthetic",
+                      "higher_is_better": True, "scaling": "weak",
+                      "dtype": "df32 masters (double-FP32); tc engine: exact 7-bit BF16 slices",
+                      "data": "synthetic",
                       "config": {"workload": "4096 pure-quaternion blocks, m, n ~ U[16,256], rank ~ U[4,min(m,n)], "
                                              "seed 3, %s, rel. tol %g, one persistent kernel per step replayed as a "
                                              "captured CUDA graph, autotuned CTA GEMM tile" % (args.method, args.tol),
-                                 "tile": ["16x16", "32x32", "64x32", "32x64", "64x64"][st["batched_tile"]],
+                                 "tile": BATCH_ENGINES[st["batched_tile"]],
                                  "autotune_ms": tune_ms, "graph_replays": st["batched_graph_replays"]},
-                      "gpu_launches": st["kernel_launches"],
+                      "gpu_launches": st["kernel_launches"], "roofline": roof, "cpu_baseline": cpu,
                       "result": {"max_E1_rel": max(e1), "median_iters": sorted(its)[len(its) // 2],
                                  "statuses": sorted(set(i["status"] for i in infos))},
                       "clocks": clk.summary()}), flush=True)
@@ -249,27 +347,57 @@ def _timed_solve(ctx, torch, A, method, tol, max_iter=500):
 
 def bench_rankdef(args, torch, qpinv):
     """Rank-2048 8192 x 4096 A = QL diag(sigma) QR^H, sigma geometric 1..1e-4
-    (seeds 4, 5): QHPI19 and Newton-Schulz with FP64-accurate tensor-core
-    products (EMU) and the plateau stop; one step = one QHPI19 solve."""
+    (seeds 4, 5): QHPI19 and Newton-Schulz to the plateau stop, each with
+    FP64-accurate tensor-core products throughout (EMU) and in the default
+    mixed precision (BF16-split bulk with FP64-accurate polish; a result that
+    fails the Penrose check is repeated in EMU, and the line says which
+    precision produced X).  One step = one QHPI19 EMU solve.  Every X is
+    compared with the FP64 oracle's exact pseudoinverse QR Sigma^-1 QL^H of
+    the generator's factors (CPU-baseline leg, after the timed solves)."""
+    import numpy as np
+
     from paper_2605_01464_gb300 import inputs
     dev = "cuda" if args.gen_device == "cuda" else "cpu"
-    A = torch.from_numpy(inputs.rank_deficient(8192, 4096, 2048, 1e-4, 4, 5, device=dev)[0]).cuda()
+    A_host, QL, sig, QR = inputs.rank_deficient(8192, 4096, 2048, 1e-4, 4, 5, device=dev)
+    A = torch.from_numpy(A_host).cuda()
     ctx = qpinv.Context(0, precision="emu", profile=True)
-    out = {}
+    out, Xs = {}, {}
     with ClockSampler(0) as clk:
         for method in ("qhpi19", "ns"):
-            for _ in range(args.warmup):
-                _timed_solve(ctx, torch, A, method, args.tol)
-            ctx.reset_stats()
-            times, info = [], None
-            for _ in range(args.steps if method == "qhpi19" else 1):
-                ms, info = _timed_solve(ctx, torch, A, method, args.tol)
-                times.append(ms)
-            st = ctx.stats()
-            out[method] = {"ms_per_solve": statistics.mean(times), "iters": info["iters"], "status": info["status"],
-                           "E_rel": info["E_rel"], "gemms": info["gemms"], "gpu_launches": st["kernel_launches"],
-                           "roofline": kernel_rooflines(st)}
-    q = out["qhpi19"]
+            for prec in ("emu", "mixed"):
+                ctx.configure(precision=prec)
+                for _ in range(args.warmup if (method, prec) == ("qhpi19", "emu") else 0):
+                    _timed_solve(ctx, torch, A, method, args.tol)
+                ctx.reset_stats()
+                times, info = [], None
+                for _ in range(args.steps if (method, prec) == ("qhpi19", "emu") else 1):
+                    stream = torch.cuda.current_stream()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    X, info = ctx.solve(A, method, tol=args.tol, max_iter=500, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                st = ctx.stats()
+                key = "%s_%s" % (method, prec)
+                Xs[key] = X.cpu().numpy()
+                out[key] = {"ms_per_solve": statistics.mean(times), "iters": info["iters"],
+                            "status": info["status"], "precision_of_X": info["precision"],
+                            "E_rel": info["E_rel"], "gemms": info["gemms"], "gpu_launches": st["kernel_launches"],
+                            "roofline": kernel_rooflines(st)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        want = oracle.pinv_from_svd(QL, sig, QR)
+        t_ref = time.perf_counter() - t0
+        for key, X in Xs.items():
+            out[key]["x_relerr_vs_oracle"] = float(np.linalg.norm(X - want) / np.linalg.norm(want))
+        cpu = {"value": 1.0 / t_ref, "unit": "reference pseudoinverses/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the FP64 oracle's QR Sigma^-1 QL^H of the generator's factors (one 4096 x 2048 x 8192 "
+                         "quaternion product, %.1f s), the reference of x_relerr_vs_oracle" % t_ref}
+    q = out["qhpi19_emu"]
     print(json.dumps({
         "metric": "rank-deficient pinv solves/s to rel. Penrose res (FP64 floor)", "value": 1e3 / q["ms_per_solve"],
         "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q["ms_per_solve"],
@@ -277,9 +405,9 @@ def bench_rankdef(args, torch, qpinv):
         "data": "synthetic",
         "config": {"workload": "8192x4096 quaternion, rank 2048, A = QL diag(sigma) QR^H, sigma geometric 1..1e-4, "
                                "orthonormal factors from Gaussian quaternion matrices (seeds 4, 5); left residual "
-                               "(4096 side); EMU precision; rel. tol %g with plateau stop" % args.tol,
+                               "(4096 side); EMU and mixed precision; rel. tol %g with plateau stop" % args.tol,
                    "l2": "inputs exceed L2"},
-        "roofline": q["roofline"][0], "result": out, "clocks": clk.summary()}), flush=True)
+        "roofline": q["roofline"][0], "result": out, "cpu_baseline": cpu, "clocks": clk.summary()}), flush=True)
     return 0
 
 
@@ -766,6 +894,8 @@ def main():
     ap.add_argument("--polish", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-gemm-records", action="store_true",
+                    help="skip the single-pass GEMM records at n = 4096 and 8192 in the default line")
     ap.add_argument("--kernel", default=None, choices=["qgemm"],
                     help="time only the tensor-core quaternion GEMM (n x n x n) for kernel profiling")
     ap.add_argument("--split", type=int, default=1,
@@ -818,7 +948,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    A_host = make_workload(args.n, "cuda:%d" % local if args.gen_device == "cuda" else "cpu")
+    A_host, U_host, s_host, V_host = make_workload(args.n, "cuda:%d" % local if args.gen_device == "cuda" else "cpu")
     A = torch.from_numpy(A_host).cuda()
     stream = torch.cuda.current_stream()
     ctx = qpinv.Context(local, precision="mixed", polish_iters=args.polish, profile=True)
@@ -868,6 +998,8 @@ def main():
             dist.destroy_process_group()
         return 0
     roofs = kernel_rooflines(st)
+    if not args.no_gemm_records:
+        roofs += gemm_target_records(torch, qpinv, local)
     last = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -886,6 +1018,10 @@ def main():
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(A_host, last["iters"])
+        err, secs = oracle_pinv_error(X.cpu().numpy(), U_host, s_host, V_host)
+        line["result"]["x_relerr_vs_oracle"] = err
+        line["result"]["x_relerr_reference"] = ("FP64 oracle V Sigma^-1 U^H of the generator's factors "
+                                                "(%.1f s on the host cores)" % secs)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

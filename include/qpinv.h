@@ -133,6 +133,9 @@ typedef struct {
                         0 = 16x16, 1 = 32x32, 2 = 64x32, 3 = 32x64, 4 = 64x64 */
   int hyper_order;   /* QPINV_QHPIM order k, 2..64 (default 19; k = 2 is Newton-Schulz, and
                         k = 1, X_{j+1} = X_j, makes no progress and is rejected) */
+  int fuse_epilogue; /* 1 (default): the combine pass after a BF16 tensor-core product (residual
+                        R = I - A X, the polynomial blocks in R, the X update with its stop norms)
+                        runs in the GEMM's epilogue; 0: separate combine kernel (same arithmetic) */
 } qpinv_options;
 
 typedef struct {
@@ -153,6 +156,10 @@ typedef struct {
   double E_rel[4];   /* E divided by ||A||_F, ||X||_F, ||AX||_F, ||XA||_F */
   long long gemms;   /* quaternion matrix products issued */
   double time_ms;    /* wall time of the call */
+  int alpha_fallback; /* 1: QPINV_ALPHA_LEARNED was asked for and the safe alpha used instead --
+                         the prediction failed Thm. 1's condition before the solve, or the solve
+                         started from it did not contract (a residual norm that grew, a diverged
+                         or unconverged iteration) and was restarted from the safe alpha */
 } qpinv_result;
 
 typedef struct {
@@ -175,6 +182,7 @@ typedef struct {
   long long batched_tile;     /* CTA GEMM tile of the last batched call (see batched_tile) */
   double batched_tune_ms;     /* time spent autotuning batched tiles */
   long long batched_graph_replays; /* batched calls served by replaying a captured CUDA graph */
+  long long fused_epilogues;       /* tensor-core products whose combine pass ran in the GEMM epilogue */
 } qpinv_stats;
 
 typedef struct qpinv_ctx qpinv_ctx;
@@ -381,9 +389,11 @@ int qpinv_penrose(qpinv_ctx* ctx, void* stream, int m, int n, const double* cons
  *   - A (m x k), B (k x n), C (m x n): four FP64 planes each, DEVICE pointers
  *     only, row-major with leading dimensions lda >= k, ldb >= n, ldc >= n;
  *     1 <= m, k, n <= QPINV_NOALLOC_MAX_DIM, else QPINV_E_NOALLOC_LIMIT;
- *     host pointers give QPINV_E_INVALID.  C must not alias A or B.
- *   - Runs on the caller's current device and on `stream`; returns after the
- *     product is complete (it reads back the kernel's error word).
+ *     host pointers, and device pointers of a GPU other than the current
+ *     one, give QPINV_E_INVALID.  C must not alias A or B.
+ *   - Runs on the caller's current device and on `stream`; synchronous: it
+ *     reads the kernel's error word into host memory and waits for `stream`
+ *     before it returns.
  *   - The first call on each device looks up the array's device address; make
  *     that first call before any stream capture.
  *   - Every call shares the one array: calls whose work may overlap on the GPU

@@ -23,6 +23,8 @@
 // The iteration schedules are the small-correction forms of the single-matrix
 // solver (X_{j+1} = X + X t with t built from R, R^2, R^4), residual on the
 // smaller side.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -149,6 +151,12 @@ struct BatchParams {
   int method, mparam, stop_rule, max_iter, alpha_mode;  // mparam: QRAPID's N or QHPIM's order k
   double tol, alpha_user;
   double k[12];  // QHPI19 coefficients a1 a2 a3 b1 b2 c1 c2 d1 d2 d3 e1 e2
+  // tensor-core engine (batched_tc.cu): per-slot slice scratch and its TMA maps
+  const CUtensorMap* tc_maps;  // 2 per slot: A-form slices, B-form slices
+  char* tc_ws;
+  long tc_slot_bytes;
+  int tc_slices;  // exact 7-bit slices per operand
+  int* err;       // device error word (bounded-wait expiry)
 };
 
 // Per-tile entry points, defined in batched_tile<t>.cu.
@@ -157,19 +165,25 @@ cudaError_t batched_launch_t1(int slots, const BatchParams& P, cudaStream_t st);
 cudaError_t batched_launch_t2(int slots, const BatchParams& P, cudaStream_t st);
 cudaError_t batched_launch_t3(int slots, const BatchParams& P, cudaStream_t st);
 cudaError_t batched_launch_t4(int slots, const BatchParams& P, cudaStream_t st);
+cudaError_t batched_launch_tc(int slots, const BatchParams& P, cudaStream_t st);
 int batched_occupancy_t0();
 int batched_occupancy_t1();
 int batched_occupancy_t2();
 int batched_occupancy_t3();
 int batched_occupancy_t4();
+size_t batched_tc_slot_bytes();
+cudaError_t batched_tc_maps(char* tc_ws, int slots, CUtensorMap* host_maps, void* dev_maps, cudaStream_t st);
 
 namespace {
 
 struct Shared {
-  dfv a[4][BK][TMAX];
-  dfv b[4][BK][TMAX];
   double red[TPB / 32][2];
   double bc[4];
+};
+// operand tiles of the CUDA-core CTA GEMM
+struct SimtTiles {
+  dfv a[4][BK][TMAX];
+  dfv b[4][BK][TMAX];
 };
 
 __device__ double block_sum(double v, Shared& sh, int slot) {
@@ -186,7 +200,8 @@ __device__ double block_sum(double v, Shared& sh, int slot) {
 // C (P.rows x Q.cols) = epilogue(P Q), quaternion; every thread of the CTA calls it.
 // Returns (in every thread) the two norms of Epi::ref, if requested.
 template <int RM, int RN>
-__device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Shared& sh, double* norms) {
+__device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Shared& sh, SimtTiles& tl,
+                         double* norms) {
   constexpr int BM = 16 * RM, BN = 16 * RN;
   const int M = P.rows, K = P.cols, N = Q.cols;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -205,13 +220,13 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
           const int ii = t / BK, kk = t % BK, gi = i0 + ii, gk = k0 + kk;
           const bool ok = gi < M && gk < K;
 #pragma unroll
-          for (int c = 0; c < 4; c++) sh.a[c][kk][ii] = ok ? P.at(c, gi, gk) : dfv{0.f, 0.f};
+          for (int c = 0; c < 4; c++) tl.a[c][kk][ii] = ok ? P.at(c, gi, gk) : dfv{0.f, 0.f};
         }
         for (int t = threadIdx.x; t < BK * BN; t += TPB) {
           const int kk = t / BN, jj = t % BN, gk = k0 + kk, gj = j0 + jj;
           const bool ok = gk < K && gj < N;
 #pragma unroll
-          for (int c = 0; c < 4; c++) sh.b[c][kk][jj] = ok ? Q.at(c, gk, gj) : dfv{0.f, 0.f};
+          for (int c = 0; c < 4; c++) tl.b[c][kk][jj] = ok ? Q.at(c, gk, gj) : dfv{0.f, 0.f};
         }
         __syncthreads();
         const int kmax = min(BK, K - k0);
@@ -220,11 +235,11 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
 #pragma unroll
           for (int r = 0; r < RM; r++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) a[r][c] = sh.a[c][kk][ty + 16 * r];
+            for (int c = 0; c < 4; c++) a[r][c] = tl.a[c][kk][ty + 16 * r];
 #pragma unroll
           for (int q = 0; q < RN; q++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) b[q][c] = sh.b[c][kk][tx + 16 * q];
+            for (int c = 0; c < 4; c++) b[q][c] = tl.b[c][kk][tx + 16 * q];
 #pragma unroll
           for (int r = 0; r < RM; r++)
 #pragma unroll
@@ -349,18 +364,30 @@ struct Ctx {
 enum { B_A = 0, B_X0, B_X1, B_R, B_R2, B_R4, B_S, B_FA, B_FB, B_U, B_V, B_W, B_G, B_T, B_Z0, B_Z1, B_Z2, B_E, B_P1,
        B_P2, B_P3, B_P4 };
 
+// The CUDA-core CTA GEMM as a policy of Solve (the tensor-core engine in
+// batched_tc.cu provides another with the same call).
 template <int RM, int RN>
+struct SimtGemm {
+  Shared* sh;
+  SimtTiles* tl;
+  __device__ void operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms) {
+    cta_gemm<RM, RN>(P, Q, C, e, *sh, *tl, norms);
+  }
+};
+
+template <class G>
 struct Solve {
   Ctx& c;
+  G& g;
   DM A, X[2];
   int cur = 0;
   double nd = 0, nx = 0;
-  __device__ explicit Solve(Ctx& cc) : c(cc) {}
+  __device__ Solve(Ctx& cc, G& gg) : c(cc), g(gg) {}
 
   __device__ void gemm(const DM& P, const DM& Q, const DM& C, const Epi& e) {
     c.gemms++;
     double nrm[2] = {0, 0};
-    cta_gemm<RM, RN>(P, Q, C, e, *c.sh, nrm);
+    g(P, Q, C, e, nrm);
     if (e.ref) {
       nd = nrm[0];
       nx = nrm[1];
@@ -521,28 +548,18 @@ struct Solve {
   }
 };
 
-template <int RM, int RN, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_batched(BatchParams P) {
-  __shared__ Shared sh;
-  __shared__ int next;
-  Ctx c;
-  c.P = &P;
-  c.sh = &sh;
-  c.base = P.ws + (long)blockIdx.x * P.slot_elems;
-  for (;;) {
-    if (threadIdx.x == 0) next = atomicAdd(P.counter, 1);
-    __syncthreads();
-    const int slot = next;
-    __syncthreads();
-    if (slot >= P.count) break;
-    const int b = P.order[slot];
+// One matrix end to end (every thread of the CTA): alpha, X_0, the
+// iteration with its stop rule, E1..E4, X written to the caller.
+template <class G>
+__device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
+    Shared& sh = *c.sh;
     const BatchItem it = P.items[b];
     c.m = it.m;
     c.n = it.n;
     c.left = it.m > it.n;
     c.s = c.left ? it.n : it.m;
     c.gemms = 0;
-    Solve<RM, RN> S(c);
+    Solve<G> S(c, g);
     S.A = c.buf(B_A, it.m, it.n);
     S.X[0] = c.buf(B_X0, it.n, it.m);
     S.X[1] = c.buf(B_X1, it.n, it.m);
@@ -684,6 +701,25 @@ __global__ void __launch_bounds__(TPB, MINB) k_batched(BatchParams P) {
     res.gemms = c.gemms;
     if (threadIdx.x == 0) P.results[b] = res;
     __syncthreads();
+}
+
+template <int RM, int RN, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_batched(BatchParams P) {
+  __shared__ Shared sh;
+  __shared__ SimtTiles tl;
+  __shared__ int next;
+  Ctx c;
+  c.P = &P;
+  c.sh = &sh;
+  c.base = P.ws + (long)blockIdx.x * P.slot_elems;
+  SimtGemm<RM, RN> g{&sh, &tl};
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int slot = next;
+    __syncthreads();
+    if (slot >= P.count) break;
+    solve_item(P, c, g, P.order[slot]);
   }
 }
 
@@ -695,6 +731,7 @@ cudaError_t launch_batched(int tile, int slots, const BatchParams& P, cudaStream
     case 2: return batched_launch_t2(slots, P, st);
     case 3: return batched_launch_t3(slots, P, st);
     case 4: return batched_launch_t4(slots, P, st);
+    case 5: return batched_launch_tc(slots, P, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -707,7 +744,7 @@ unsigned long long mix(unsigned long long h, unsigned long long v) {
 
 }  // namespace
 
-#ifdef QP_BATCHED_TILE
+#if defined(QP_BATCHED_TILE) && !defined(QP_BATCHED_TC_UNIT)
 // One kernel instantiation: QP_TILE_RM x QP_TILE_RN outputs per thread,
 // QP_TILE_MINB resident CTAs per SM requested from the compiler.
 cudaError_t QP_TILE_LAUNCH(int slots, const BatchParams& P, cudaStream_t st) {
@@ -721,9 +758,9 @@ int QP_TILE_OCCUPANCY() {
     return 1;
   return nb > 0 ? nb : 1;
 }
-#else
+#elif !defined(QP_BATCHED_TILE)
 const char* batched_tile_name(int tile) {
-  static const char* names[BATCH_TILES] = {"16x16", "32x32", "64x32", "32x64", "64x64"};
+  static const char* names[BATCH_TILES] = {"16x16", "32x32", "64x32", "32x64", "64x64", "tc"};
   return tile >= 0 && tile < BATCH_TILES ? names[tile] : "?";
 }
 
@@ -734,6 +771,7 @@ int batched_slots_per_sm(int tile) {
     case 2: return batched_occupancy_t2();
     case 3: return batched_occupancy_t3();
     case 4: return batched_occupancy_t4();
+    case 5: return 1;  // tensor-core engine: one CTA (all of TMEM) per SM
     default: return 1;
   }
 }
@@ -780,6 +818,16 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
   P.tol = tol;
   P.alpha_user = alpha_user;
   for (int t = 0; t < 12; t++) P.k[t] = hpi19_k[t];
+  P.tc_maps = (const CUtensorMap*)r.tc_maps;
+  P.tc_ws = (char*)r.tc_ws;
+  P.tc_slot_bytes = (long)batched_tc_slot_bytes();
+  P.tc_slices = 7;
+  P.err = r.err;
+  if (r.tile == BATCH_TILE_TC) {
+    if (!r.tc_ws || !r.tc_maps || !r.host_maps || !r.err) return cudaErrorInvalidValue;
+    cudaError_t e = batched_tc_maps((char*)r.tc_ws, r.slots, (CUtensorMap*)r.host_maps, r.tc_maps, st);
+    if (e != cudaSuccess) return e;
+  }
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(r.dev_items, r.host_items, sizeof(BatchItem) * batch, cudaMemcpyHostToDevice, s)) !=

@@ -116,6 +116,33 @@ cudaError_t launch_qgemm_f64(int M, int K, int N, const Planes<const double>& A,
                              const Planes<const double>& B, const Planes<double>& C,
                              cudaStream_t st);
 
+// Combine pass fused into the epilogue of the tensor-core GEMM (FP32 phase):
+// the product never goes to HBM; each output o is
+//   out_o = cacc * (A B) + sum_t caux[t] * aux_t + diag * I   (diag on plane s)
+// written as an FP32 master and/or round-to-nearest BF16 splits (A-form
+// row-major, B-form transposed), with the stop-test partials of output 0
+// (||out0 - aux0||^2, ||out0||^2, non-finite count) per (CTA, epilogue warp).
+// Outputs must not alias the product's operand forms (other CTAs are still
+// reading them); an output may alias an aux plane (same element, same thread).
+struct EpiOut {
+  float* mp = nullptr;  // FP32 master planes (may be null)
+  long mld = 0, mps = 0;
+  bf16* a = nullptr;  // A-form splits [level][comp][rows][lda] (may be null)
+  long lda = 0, psa = 0;
+  bf16* b = nullptr;  // B-form splits [level][comp][cols][ldb] (may be null)
+  long ldb = 0, psb = 0;
+  int levels = 0;
+  float cacc = 0.f, caux[4] = {0.f, 0.f, 0.f, 0.f}, diag = 0.f;
+};
+struct EpiArgs {
+  int nout = 0;  // 0: plain FP32 store of the product into TcGemmArgs::C
+  EpiOut out[kMaxOut];
+  const float* aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  long ld_aux[4] = {0, 0, 0, 0}, ps_aux[4] = {0, 0, 0, 0};
+  double* partials = nullptr;  // 3 values per (CTA, epilogue warp): tc_partial_blocks(M, N) blocks
+};
+int tc_partial_blocks(int M, int N);
+
 // Tensor-core quaternion GEMM on BF16 split operands.  acc (FP32) = sum over
 // the listed (i, j) term pairs of A_i * B_j, restricted to k in [k0, k1).
 struct TcGemmArgs {
@@ -132,6 +159,7 @@ struct TcGemmArgs {
   int pair_i[16] = {0}, pair_j[16] = {0};
   int pair_acc[16] = {0};  // TMEM accumulator of each pair (1 only with C64: the two are summed)
   Planes<float> C;  // FP32 output
+  EpiArgs epi;      // epi.nout > 0: fused combine instead of the plain store (FP32 output only)
   int* err = nullptr;  // device error word (bounded-wait expiry)
 };
 cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);
@@ -167,14 +195,20 @@ struct BatchResultHost {
 }  // namespace qp
 #include <vector>
 namespace qp {
-// CTA GEMM tile shapes of the batched kernel (quaternion entries):
-// 0: 16x16, 1: 32x32, 2: 64x32, 3: 32x64, 4: 64x64.
-constexpr int BATCH_TILES = 5;
+// CTA GEMM engines of the batched kernel: CUDA-core double-FP32 tiles
+// (quaternion entries) 0: 16x16, 1: 32x32, 2: 64x32, 3: 32x64, 4: 64x64, and
+// 5: the tensor-core exact-slice engine (batched_tc.cu).
+constexpr int BATCH_TILES = 6;
+constexpr int BATCH_TILE_TC = 5;
 const char* batched_tile_name(int tile);
 // Device and pinned host buffers of one batched call (owned by the context).
 struct BatchRun {
   int tile = 1, slots = 0;
   void* ws = nullptr;  // slots * batched_slot_bytes()
+  void* tc_ws = nullptr;    // tensor-core engine: slots * batched_tc_slot_bytes()
+  void* tc_maps = nullptr;  // ... its TMA maps on the device (2 per slot)
+  void* host_maps = nullptr;  // pinned staging of the maps
+  int* err = nullptr;       // device error word
   void *dev_items = nullptr, *dev_order = nullptr, *dev_results = nullptr;
   int* dev_counter = nullptr;
   void *host_items = nullptr, *host_order = nullptr, *host_results = nullptr;  // pinned
@@ -192,6 +226,7 @@ cudaError_t run_batched(int batch, const int* m, const int* n, const double* con
                         int stop_rule, int alpha_mode, double alpha_user, const double* hpi19_k, const BatchRun& r,
                         BatchGraph* graph, std::vector<BatchResultHost>& out, cudaStream_t st);
 size_t batched_slot_bytes();
+size_t batched_tc_slot_bytes();  // slice scratch of one tensor-core engine slot
 // Learned alpha (alpha.cu).
 int alpha_nweights();
 int alpha_ntrain();

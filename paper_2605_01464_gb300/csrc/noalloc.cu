@@ -17,6 +17,9 @@
 // device current, looks the address up with cudaGetSymbolAddress and caches
 // it; make that first call before any stream capture.
 //
+// Each call is synchronous: it reads the kernel's error word back into host
+// memory and waits for its stream before it returns.
+//
 // Sharing: every call uses the same array and leaves its contents behind.
 // The error word is cleared at the start of each call; everything else that
 // is read is written first in the same call.  Calls whose work overlaps on
@@ -111,7 +114,10 @@ int blocks_for(long total) {
   return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
-bool all_device(const void* const* p, int n) {
+// True if every pointer is device (or managed) memory of device `dev`: the
+// kernels run on the current device, and memory of another GPU would be read
+// through a peer mapping that may not exist.
+bool all_device(const void* const* p, int n, int dev) {
   for (int t = 0; t < n; t++) {
     cudaPointerAttributes at;
     if (!p[t] || cudaPointerGetAttributes(&at, p[t]) != cudaSuccess) {
@@ -119,6 +125,7 @@ bool all_device(const void* const* p, int n) {
       return false;
     }
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+    if (at.device != dev) return false;
   }
   return true;
 }
@@ -135,12 +142,12 @@ extern "C" int qpinv_qgemm_noalloc(void* stream, int m, int k, int n, const doub
       !A || !B || !C)
     return QPINV_E_INVALID;
   if (m > NA_MAX || n > NA_MAX || k > NA_MAX) return QPINV_E_NOALLOC_LIMIT;
-  if (!all_device((const void* const*)A, 4) || !all_device((const void* const*)B, 4) ||
-      !all_device((const void* const*)C, 4))
-    return QPINV_E_INVALID;
-  if (!tc_supported()) return QPINV_E_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return QPINV_E_CUDA;
+  if (!all_device((const void* const*)A, 4, dev) || !all_device((const void* const*)B, 4, dev) ||
+      !all_device((const void* const*)C, 4, dev))
+    return QPINV_E_INVALID;
+  if (!tc_supported()) return QPINV_E_UNSUPPORTED;
   unsigned char* base = nullptr;
   if (scratch_address(dev, &base) != cudaSuccess) return QPINV_E_CUDA;
   cudaStream_t st = (cudaStream_t)stream;

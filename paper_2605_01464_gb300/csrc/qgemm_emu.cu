@@ -12,15 +12,22 @@
 // A persistent grid (one CTA per SM) walks work items (tile, level group):
 // the levels are split into two groups of equal cost, each summed into its
 // own int64 accumulator, so that 2 x tiles items balance over the SMs.  For
-// each level of its item the MMA warp accumulates a K-chunk into an FP32 TMEM
-// buffer (columns 0..255); the epilogue warps convert it exactly to int32 and
-// add it into an int32 TMEM accumulator of the level (columns 256..511), then
-// release the buffer for the next chunk.  At the end of a level the int32 sum
-// is shifted to the common 64-bit fixed point and added to the global int64
-// accumulator of its group through a shared-memory transpose (coalesced
-// rows).  Global traffic per product is one read-modify-write of an
-// accumulator per level instead of one per chunk, and there is a single
-// launch per product.
+// each level of its item the MMA warp accumulates K-chunks into two FP32 TMEM
+// buffers in turn (256 columns each), so the tensor core fills one while the
+// eight epilogue warps drain the other: each converts its 32 rows x 128
+// columns exactly to int32 and adds them into the level's sums, held in its
+// registers (128 per thread), then releases the buffer.  At the end of a
+// level the int32 sums are shifted to the common 64-bit fixed point and
+// added to the global int64 accumulator of the item's group (each thread its
+// own row segment, 16-byte accesses).  Global traffic per product is one
+// read-modify-write of an accumulator per level instead of one per chunk, and
+// there is a single launch per product.
+//
+// The kernel is bound by the tensor core's shared-memory operand reads (one
+// 128 x 16 A tile and one 64 x 16 B tile per MMA of N = 64: ncu shows the
+// tensor core's shared-memory wavefronts at 1.5 times its pipe activity);
+// staging A in tensor memory with tcgen05.cp instead was measured slower
+// (10.7 against 9.2 ms for the 8-slice 2048^3 product).
 //
 // int32 range: a level-d sum is bounded by 4K 2^12 (d + 3) (2^14 for d = 0)
 // level units; launch_qgemm_emu refuses K beyond what keeps this below 2^31.
@@ -39,15 +46,19 @@ constexpr int ESTAGES = 4;
 constexpr int EA_PLANE = EBM * EBK * 2;                    // 8 KB
 constexpr int EB_PLANE = EBN * EBK * 2;                    // 4 KB
 constexpr int ESTAGE = 4 * (EA_PLANE + EB_PLANE);          // 48 KB
-constexpr int ESTAGING = 4 * 32 * 33 * 8;                  // epilogue transpose, 4 warps
-constexpr int ESMEM = ESTAGES * ESTAGE + ESTAGING + 1024;  // + alignment slack
-constexpr int ETHREADS = 192;
+constexpr int ESMEM = ESTAGES * ESTAGE + 1024;             // + alignment slack
+constexpr int EEPI_WARPS = 8;                              // two per TMEM lane quarter
+constexpr int ETHREADS = 64 + 32 * EEPI_WARPS;             // TMA warp, MMA warp, epilogue warps
 constexpr int EGROUP_M = 16;
+// TMEM columns: two FP32 chunk accumulators of 256 columns (component c at
+// c * EBN): the MMAs of chunk w fill buffer w % 2 while the epilogue drains
+// the other.
+constexpr uint32_t ECHUNK_COLS = 4 * EBN;
 static_assert(ESMEM <= 227 * 1024, "shared memory per CTA");
+static_assert(2 * ECHUNK_COLS == 512, "TMEM columns");
 
 constexpr uint32_t EIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EBN >> 3) << 17) |
                             ((uint32_t)(EBM >> 4) << 24);
-constexpr uint32_t EIDESC_NEG_A = EIDESC | (1u << 13);
 
 struct EParams {
   int M, N, K, S;
@@ -73,10 +84,23 @@ __device__ __forceinline__ void tile_origin(const EParams& P, int t, int& m0, in
   n0 = (local / gm) * EBN;
 }
 
+// int64 += v (two columns when both exist and the address is 16-byte aligned).
+__device__ __forceinline__ void add64_pair(long long* dst, long long v0, long long v1, bool two) {
+  if (two && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    longlong2 g = *reinterpret_cast<longlong2*>(dst);
+    g.x += v0;
+    g.y += v1;
+    *reinterpret_cast<longlong2*>(dst) = g;
+  } else {
+    dst[0] += v0;
+    if (two) dst[1] += v1;
+  }
+}
+
 __global__ void __launch_bounds__(ETHREADS, 1)
     k_qgemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EParams P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_full[ESTAGES], bar_empty[ESTAGES], bar_acc_full, bar_acc_empty;
+  __shared__ uint64_t bar_full[ESTAGES], bar_empty[ESTAGES], bar_acc_full[2], bar_acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -89,8 +113,10 @@ __global__ void __launch_bounds__(ETHREADS, 1)
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_acc_full), 1);
-    mbar_init(smem_u32(&bar_acc_empty), 4);  // one arrival per epilogue warp
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), EEPI_WARPS);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -152,12 +178,14 @@ __global__ void __launch_bounds__(ETHREADS, 1)
        for (int li = 0; li < P.nlv[g] && ok; li++) {
         const int d = P.lv[g][li];
         for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
-          // the FP32 buffer is free once the epilogue has read chunk w - 1
-          if (w > 0 && !mbar_wait(smem_u32(&bar_acc_empty), (w - 1) & 1, &abort_flag, P.err, 12)) {
+          // buffer w % 2 is free once the epilogue has read chunk w - 2
+          const int b = w & 1;
+          if (w >= 2 && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((w >> 1) - 1) & 1, &abort_flag, P.err, 12)) {
             ok = false;
             break;
           }
           fence_after();
+          const uint32_t dacc = tmem + b * ECHUNK_COLS;
           const int kb0 = k0 / EBK, kb1 = (min(P.K, k0 + P.kc[d]) + EBK - 1) / EBK;
           bool first = true;
           for (int kb = kb0; kb < kb1 && ok; kb++) {
@@ -171,51 +199,42 @@ __global__ void __launch_bounds__(ETHREADS, 1)
               uint8_t* sp = smem + (size_t)st * ESTAGE;
               const uint32_t a_base = smem_u32(sp), b_base = smem_u32(sp + 4 * EA_PLANE);
 #pragma unroll
-              for (int kk = 0; kk < EBK / 16; kk++) {
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                  const uint64_t ad = smem_desc_sw<ESWB>(a_base + r * EA_PLANE + kk * 32);
-#pragma unroll
-                  for (int c = 0; c < 4; c++) {
-                    const int bp = r ^ c;
-                    const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
-                                     (r == 3 && (c == 0 || c == 1));
-                    const uint64_t bd = smem_desc_sw<ESWB>(b_base + bp * EB_PLANE + kk * 32);
-                    const uint32_t acc = (!first || kk > 0 || r > 0) ? 1u : 0u;
-                    mma_bf16(tmem + c * EBN, ad, bd, neg ? EIDESC_NEG_A : EIDESC, acc);
-                  }
-                }
-              }
+              for (int kk = 0; kk < EBK / 16; kk++)
+                qmma_k16<ESWB>(dacc, EBN, a_base + kk * 32, EA_PLANE, b_base + kk * 32, EB_PLANE, EIDESC,
+                               first && kk == 0);
               first = false;
               mma_commit(smem_u32(&bar_empty[st]));
             }
           }
-          if (ok) mma_commit(smem_u32(&bar_acc_full));
+          if (ok) mma_commit(smem_u32(&bar_acc_full[b]));
         }
        }
       }
     }
   } else {
-    // ---------------- epilogue: exact FP32 -> int32 per chunk, int64 per level ----------------
-    const int quarter = warp & 3;
-    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
-    long long* st64 = reinterpret_cast<long long*>(smem + ESTAGES * ESTAGE) + (warp - 2) * (32 * 33);
+    // ---------------- epilogue: exact FP32 -> int32 per chunk (registers), int64 per level ----------------
+    // Warp e = warp - 2 reads TMEM lane quarter warp % 4 (its 32 rows) and the
+    // column half e / 4 (components 2h, 2h + 1): 128 int32 level sums per thread.
+    const int e = warp - 2, quarter = warp & 3, half = e >> 2;
+    const uint32_t tb0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * 128;
     int w = 0;
     bool ok = true;
+    int acc[128];
     for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
      const int g = item % P.ngroups;
      int m0, n0;
      tile_origin(P, item / P.ngroups, m0, n0);
-     const int row0 = m0 + quarter * 32;
-     const int nrow = min(32, P.M - row0);
+     const int row = m0 + quarter * 32 + lane;
      long long* const C64 = P.C64g[g];
      for (int li = 0; li < P.nlv[g] && ok; li++) {
       const int d = P.lv[g][li];
       const float scale = ldexpf(1.0f, 7 * (d + 2));  // level unit -> integer (a power of two: exact)
       const int sh = P.shift - 7 * (d + 2);
       for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
+        const int b = w & 1;
+        const uint32_t tb = tb0 + b * ECHUNK_COLS;
         int have = 1;
-        if (lane == 0) have = mbar_wait(smem_u32(&bar_acc_full), w & 1, &abort_flag, P.err, 14) ? 1 : 0;
+        if (lane == 0) have = mbar_wait(smem_u32(&bar_acc_full[b]), (w >> 1) & 1, &abort_flag, P.err, 14) ? 1 : 0;
         have = __shfl_sync(0xffffffffu, have, 0);
         if (!have) {
           ok = false;
@@ -223,44 +242,37 @@ __global__ void __launch_bounds__(ETHREADS, 1)
         }
         fence_after();
         const bool first = k0 == 0;
-#pragma unroll 1
+#pragma unroll
         for (int p = 0; p < 8; p++) {
-          uint32_t f[32], a[32];
-          tmem_ld32u(tb + p * 32, f);
-          if (!first) tmem_ld32u(tb + 256 + p * 32, a);
+          uint32_t f[16];
+          tmem_ld16u(tb + p * 16, f);
           tmem_wait_ld();
 #pragma unroll
-          for (int t = 0; t < 32; t++) {
+          for (int t = 0; t < 16; t++) {
             const int x = __float2int_rn(__uint_as_float(f[t]) * scale);
-            a[t] = first ? (uint32_t)x : (uint32_t)((int)a[t] + x);
+            acc[p * 16 + t] = first ? x : acc[p * 16 + t] + x;
           }
-          tmem_st32u(tb + 256 + p * 32, a);
         }
         // every FP32 value of the chunk is in registers: release the buffer
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));
-        tmem_wait_st();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty[b]));
         const bool last = k0 + P.kc[d] >= P.K;
-        if (!last) continue;
-        // level done: int64 += int32 * 2^sh (rounded shift when sh < 0)
-#pragma unroll 1
-        for (int p = 0; p < 8; p++) {
-          uint32_t a[32];
-          tmem_ld32u(tb + 256 + p * 32, a);
-          tmem_wait_ld();
+        if (!last || row >= P.M) continue;
+        // level done: int64 += int32 * 2^sh (rounded shift when sh < 0), this
+        // thread's row, components 2 half and 2 half + 1
 #pragma unroll
-          for (int t = 0; t < 32; t++) {
-            const long long x = (long long)(int)a[t];
-            st64[lane * 33 + t] = sh >= 0 ? (x << sh) : ((x + (1LL << (-sh - 1))) >> (-sh));
+        for (int p = 0; p < 4; p++) {
+          const int c = 2 * half + (p >> 1), j0 = n0 + (p & 1) * 32;
+          long long* dst = C64 + c * P.ps64 + (long)row * P.ld64 + j0;
+#pragma unroll
+          for (int t = 0; t < 32; t += 2) {
+            if (j0 + t >= P.N) break;
+            const long long x0 = (long long)acc[p * 32 + t], x1 = (long long)acc[p * 32 + t + 1];
+            const long long y0 = sh >= 0 ? (x0 << sh) : ((x0 + (1LL << (-sh - 1))) >> (-sh));
+            const long long y1 = sh >= 0 ? (x1 << sh) : ((x1 + (1LL << (-sh - 1))) >> (-sh));
+            add64_pair(dst + t, y0, y1, j0 + t + 1 < P.N);
           }
-          __syncwarp();
-          const int c = p >> 1, col = n0 + (p & 1) * 32 + lane;
-          if (col < P.N) {
-            long long* dst = C64 + c * P.ps64 + (long)row0 * P.ld64 + col;
-            rmw_rows64(dst, P.ld64, nrow, st64 + lane);
-          }
-          __syncwarp();
         }
       }
      }
@@ -319,17 +331,14 @@ cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st) {
   P.ps64 = a.ps64;
   P.shift = a.shift;
   P.err = a.err;
+
   P.Mt = (a.M + EBM - 1) / EBM;
   P.Nt = (a.N + EBN - 1) / EBN;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, EBM, EBK)) return cudaErrorInvalidValue;
   if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, EBN, EBK)) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_qgemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, ESMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k_qgemm_emu, ESMEM, attr_done)) return e;
   P.items = P.Mt * P.Nt * P.ngroups;
   static int nsm[64] = {0};
   int dev = 0;

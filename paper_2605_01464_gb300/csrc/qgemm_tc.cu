@@ -65,7 +65,6 @@ static_assert(ACC_COLS == 256, "TMEM allocations must be powers of two (256 or 5
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
-constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
 
 struct KParams {
   int M, N;
@@ -77,11 +76,112 @@ struct KParams {
   int pfirst[16]; // 1 if the pair is the first of its accumulator
   int nacc;       // 1 or 2 accumulators (2 only with int64 output)
   Planes<float> C;
+  EpiArgs E;       // E.nout > 0: fused combine epilogue (FP32 output only)
   long long* C64;  // non-null: int64 fixed-point accumulation
   long ld64, ps64;
   float scale;     // 2^shift
   int* err;
 };
+
+__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Fused combine for 16 consecutive columns j0.. of row i (this lane), plane c:
+// v = the product's values; see EpiArgs.  nc = valid columns (1..16).
+__device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0, int nc, const float* v,
+                                          float& sdx, float& sx, int& bad) {
+#pragma unroll 1
+  for (int o = 0; o < E.nout; o++) {
+    const EpiOut& O = E.out[o];
+    float w[16];
+#pragma unroll
+    for (int t = 0; t < 16; t++) w[t] = O.cacc != 0.f ? O.cacc * v[t] : 0.f;
+#pragma unroll 1
+    for (int a = 0; a < 4; a++) {
+      if (!E.aux[a] || O.caux[a] == 0.f) continue;
+      const float* ap = E.aux[a] + c * E.ps_aux[a] + (long)i * E.ld_aux[a] + j0;
+      const float ca = O.caux[a];
+      if (nc == 16 && al16(ap)) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const float4 u = reinterpret_cast<const float4*>(ap)[q];
+          w[4 * q] += ca * u.x;
+          w[4 * q + 1] += ca * u.y;
+          w[4 * q + 2] += ca * u.z;
+          w[4 * q + 3] += ca * u.w;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; t++)
+          if (t < nc) w[t] += ca * ap[t];
+      }
+    }
+    if (c == 0 && O.diag != 0.f) {
+#pragma unroll
+      for (int t = 0; t < 16; t++)
+        if (i == j0 + t) w[t] += O.diag;
+    }
+    if (o == 0 && E.partials) {
+      const float* xp = E.aux[0] ? E.aux[0] + c * E.ps_aux[0] + (long)i * E.ld_aux[0] + j0 : nullptr;
+#pragma unroll
+      for (int t = 0; t < 16; t++)
+        if (t < nc) {
+          const float x0 = xp ? xp[t] : 0.f;
+          sdx += (w[t] - x0) * (w[t] - x0);
+          sx += w[t] * w[t];
+          bad += isfinite(w[t]) ? 0 : 1;
+        }
+    }
+    if (O.mp) {
+      float* dst = O.mp + c * O.mps + (long)i * O.mld + j0;
+      if (nc == 16 && al16(dst)) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          reinterpret_cast<float4*>(dst)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; t++)
+          if (t < nc) dst[t] = w[t];
+      }
+    }
+    if (O.a || O.b) {
+      float r[16];
+#pragma unroll
+      for (int t = 0; t < 16; t++) r[t] = w[t];
+#pragma unroll 1
+      for (int l = 0; l < O.levels; l++) {
+        bf16 h[16];
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+          h[t] = __float2bfloat16_rn(r[t]);
+          r[t] -= __bfloat162float(h[t]);
+        }
+        if (O.a) {
+          bf16* dst = O.a + (long)l * 4 * O.psa + c * O.psa + (long)i * O.lda + j0;
+          if (nc == 16 && al16(dst)) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+              pk[q] = (uint32_t)__bfloat16_as_ushort(h[2 * q]) | ((uint32_t)__bfloat16_as_ushort(h[2 * q + 1]) << 16);
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; t++)
+              if (t < nc) dst[t] = h[t];
+          }
+        }
+        if (O.b) {
+          // B-form row j holds column j of the output: lanes (rows i) of one
+          // warp write consecutive entries of it
+          bf16* dst = O.b + (long)l * 4 * O.psb + c * O.psb + (long)j0 * O.ldb + i;
+#pragma unroll
+          for (int t = 0; t < 16; t++)
+            if (t < nc) dst[(long)t * O.ldb] = h[t];
+        }
+      }
+    }
+  }
+}
 
 template <class C>
 __global__ void __launch_bounds__(THREADS, C::MINB)
@@ -157,21 +257,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
         const uint32_t dacc = tmem + (uint32_t)(P.pacc[pr] * ACC_COLS);
         const bool fresh = u < P.npairs && P.pfirst[pr];  // first K block of this accumulator
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; kk++) {
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const uint64_t ad = smem_desc_sw<C::SWB>(a_base + r * A_PLANE_BYTES + kk * 32);
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-              const int bp = r ^ c;
-              const bool neg = (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) ||
-                               (r == 3 && (c == 0 || c == 1));
-              const uint64_t bd = smem_desc_sw<C::SWB>(b_base + bp * B_PLANE_BYTES + kk * 32);
-              const uint32_t acc = (!fresh || kk > 0 || r > 0) ? 1u : 0u;
-              mma_bf16(dacc + c * BN, ad, bd, neg ? IDESC_NEG_A : IDESC, acc);
-            }
-          }
-        }
+        for (int kk = 0; kk < BK / 16; kk++)
+          qmma_k16<C::SWB>(dacc, BN, a_base + kk * 32, A_PLANE_BYTES, b_base + kk * 32, B_PLANE_BYTES, IDESC,
+                           fresh && kk == 0);
         mma_commit(smem_u32(&bar_empty[s]));
         if (u == nunits - 1) mma_commit(smem_u32(&bar_acc));
       }
@@ -192,7 +280,42 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
       have = __shfl_sync(0xffffffffu, have, 0);
       fence_after();
     }
-    if (have) {
+    if (have && P.E.nout > 0) {
+      // fused combine: one row per lane, 16 columns at a time, straight from TMEM
+      const int i = row0 + lane;
+      float sdx = 0.f, sx = 0.f;
+      int bad = 0;
+#pragma unroll 1
+      for (int c = 0; c < 4; c++) {
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 16; ch++) {
+          float v[16];
+          if (nunits > 0) {
+            tmem_ld16(tbase + c * BN + ch * 16, v);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; t++) v[t] = 0.f;
+          }
+          const int j0 = n0 + ch * 16;
+          const int nc = min(16, P.N - j0);
+          if (i < P.M && nc > 0) epi_piece(P.E, c, i, j0, nc, v, sdx, sx, bad);
+        }
+      }
+      if (P.E.partials) {
+        double d0 = sdx, d1 = sx, d2 = bad;
+        for (int o = 16; o > 0; o >>= 1) {
+          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+          d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        }
+        if (lane == 0) {
+          double* pp = P.E.partials + 3 * ((long)blockIdx.x * 4 + quarter);
+          pp[0] = d0;
+          pp[1] = d1;
+          pp[2] = d2;
+        }
+      }
+    } else if (have) {
       long long* st64 = reinterpret_cast<long long*>(smem) + (warp - 2) * (32 * 33);
       float* st32 = reinterpret_cast<float*>(st64);
 #pragma unroll 1
@@ -261,12 +384,8 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM, BK)) return cudaErrorInvalidValue;
   if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, BN, BK)) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_qgemm_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k_qgemm_tc<C>, C::SMEM, attr_done)) return e;
   P.kb0 = a.k0 / BK;
   P.kb1 = (a.k1 + BK - 1) / BK;
   P.Mt = (a.M + BM - 1) / BM;
@@ -277,6 +396,8 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
 }
 
 }  // namespace
+
+int tc_partial_blocks(int M, int N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * 4; }
 
 bool tc_supported() {
   int dev = 0;
@@ -315,6 +436,8 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   }
   P.nacc = nacc;
   P.C = a.C;
+  P.E = a.epi;
+  if (P.E.nout < 0 || P.E.nout > kMaxOut || (P.E.nout > 0 && (a.C64 || nacc == 2))) return cudaErrorInvalidValue;
   P.C64 = a.C64;
   P.ld64 = a.ld64;
   P.ps64 = a.ps64;

@@ -33,6 +33,8 @@
 //     slices, 56 bits); R-products stay on BF16 splits.
 // Penrose residuals use FP64-accurate products (exact slices, or the
 // CUDA-core FP64 kernel in the FP64 form).
+#include <cuda.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -86,6 +88,7 @@ struct qpinv_ctx {
   size_t bh_cap[3] = {0, 0, 0};
   qp::BatchGraph bgraph;
   std::map<unsigned long long, int> tile_of;  // batch signature -> tuned tile
+  void* bmaps_host = nullptr;                 // pinned TMA maps of the batched tensor-core engine
 };
 
 namespace {
@@ -296,11 +299,6 @@ struct Solver {
     const long long* p2 = nullptr;  // ACC_I64: second accumulator of the same layout, summed
   };
 
-  Acc rprod(const QMat& P, const QMat& Q) {
-    Lcur = Lr;
-    return prod(P, Q, rmode >= 0 ? rmode : (L == 0 ? PM_F64 : PM_TC));
-  }
-
   // acc(rows x cols) = P (rows x K) * Q (K x cols) in one of three modes:
   //   PM_TC  - tcgen05 on BF16 splits (L terms), FP32 accumulation;
   //   PM_F64 - CUDA-core FP64 on the FP64 masters;
@@ -324,12 +322,21 @@ struct Solver {
     C.ld = rup8(N);
     C.ps = (long)M * C.ld;
     C.p = (float*)buf(c, "acc32", sizeof(float) * 4 * (size_t)C.ps + 64);
+    TcGemmArgs g = tc_args(P, Q);
+    g.C = C;
+    timed(c, EV_TC, flops, flops * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
+    return Acc{C.p, ACC_F32, C.ld, C.ps, nullptr, nullptr, 0};
+  }
+
+  // Tensor-core GEMM arguments of P Q on BF16 splits of Lcur terms
+  // (1 pair, 3 pairs with i + j <= 1, 6 pairs with i + j <= 2).
+  TcGemmArgs tc_args(const QMat& P, const QMat& Q) const {
     TcGemmArgs g;
-    g.M = M;
-    g.N = N;
-    g.K = K;
+    g.M = P.rows;
+    g.N = Q.cols;
+    g.K = P.cols;
     g.k0 = 0;
-    g.k1 = K;
+    g.k1 = P.cols;
     g.A = &P.s16;
     g.B = &Q.s16;
     static const int pi3[6] = {2, 1, 0, 1, 0, 0}, pj3[6] = {0, 1, 2, 0, 1, 0};
@@ -343,10 +350,92 @@ struct Solver {
     } else {
       g.npairs = 1;
     }
-    g.C = C;
     g.err = c->d_err;
-    timed(c, EV_TC, flops, flops * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
-    return Acc{C.p, ACC_F32, C.ld, C.ps, nullptr, nullptr, 0};
+    return g;
+  }
+
+  static void set_acc(CombineArgs& a, const Acc& acc) {
+    a.acc = acc.p;
+    a.acc_kind = acc.kind;
+    a.ld_acc = acc.ld;
+    a.ps_acc = acc.ps;
+    a.acc_erow = acc.erow;
+    a.acc_ecol = acc.ecol;
+    a.acc_shift = acc.shift;
+    a.acc2 = acc.p2;
+  }
+
+  // Whether the combine pass `a` (no accumulator set yet) can run in the
+  // epilogue of the tensor-core product P Q: FP32 phase, round-to-nearest
+  // splits only, and no output that overwrites an operand form the product
+  // is still reading.
+  bool epi_fusable(const CombineArgs& a, const QMat& P, const QMat& Q) const {
+    if (!c->opt.fuse_epilogue || dbl || a.f64 || a.acc || a.nout < 1 || a.nout > kMaxOut) return false;
+    for (int o = 0; o < a.nout; o++) {
+      const OutSpec& O = a.out[o];
+      if (O.exp_a || O.exp_b) return false;
+      if ((O.s16.a || O.s16.b) && O.s16.levels < 1) return false;
+      const void* forms[4] = {P.s16.a, P.s16.b, Q.s16.a, Q.s16.b};
+      for (const void* f : forms)
+        if (f && (O.s16.a == f || O.s16.b == f)) return false;
+    }
+    return true;
+  }
+
+  // The product P Q in `mode` followed by the combine pass `a` (accumulator
+  // unset): one tensor-core launch with the pass in its epilogue when
+  // possible, else the product and the combine kernel.
+  void prod_run(const QMat& P, const QMat& Q, int mode, CombineArgs a, bool with_partials = false,
+                int red_slot = 0) {
+    if (mode == PM_TC && epi_fusable(a, P, Q)) {
+      const int M = P.rows, K = P.cols, N = Q.cols;
+      gemms++;
+      const double flops = 32.0 * M * (double)K * N;
+      TcGemmArgs g = tc_args(P, Q);
+      EpiArgs& e = g.epi;
+      e.nout = a.nout;
+      for (int o = 0; o < a.nout; o++) {
+        const OutSpec& O = a.out[o];
+        EpiOut& d = e.out[o];
+        d.mp = (float*)O.mp;
+        d.mld = O.mld;
+        d.mps = O.mps;
+        d.a = O.s16.a;
+        d.lda = O.s16.lda;
+        d.psa = O.s16.psa;
+        d.b = O.s16.b;
+        d.ldb = O.s16.ldb;
+        d.psb = O.s16.psb;
+        d.levels = O.s16.levels;
+        d.cacc = (float)O.cacc;
+        for (int t = 0; t < 4; t++) d.caux[t] = (float)O.caux[t];
+        d.diag = (float)O.diag;
+      }
+      for (int t = 0; t < 4; t++) {
+        e.aux[t] = (const float*)a.aux[t];
+        e.ld_aux[t] = a.ld_aux[t];
+        e.ps_aux[t] = a.ps_aux[t];
+      }
+      const int blocks = tc_partial_blocks(M, N);
+      if (with_partials) {
+        if (blocks > partial_cap) {
+          partials = (double*)buf(c, "partials", sizeof(double) * 3 * (size_t)blocks + 64);
+          partial_cap = blocks;
+        }
+        e.partials = partials;
+      }
+      timed(c, EV_TC, flops, flops * g.npairs, 0, [&] { return launch_qgemm_tc(g, c->st); });
+      c->stats.fused_epilogues++;
+      if (with_partials) {
+        double* red = (double*)buf(c, "red", sizeof(double) * 8);
+        timed(c, EV_EW, 0, 0, 24.0 * blocks,
+              [&] { return launch_reduce_partials(partials, blocks, 3, red + red_slot, c->st); });
+      }
+      return;
+    }
+    Acc acc = prod(P, Q, mode);
+    set_acc(a, acc);
+    run(a, with_partials, red_slot);
   }
 
   Acc prod_emu(const QMat& P, const QMat& Q, int S, double flops) {
@@ -563,21 +652,29 @@ struct Solver {
   }
 
   // ---------------- shape helpers ----------------
+  // Each product is followed by its combine pass `a` (built with no
+  // accumulator): prod_run fuses the two when it can.
+  // R-products (polynomials in R) take rmode and Lr split terms.
+  void rprod_run(const QMat& P, const QMat& Q, const CombineArgs& a) {
+    Lcur = Lr;
+    prod_run(P, Q, rmode >= 0 ? rmode : (L == 0 ? PM_F64 : PM_TC), a);
+  }
   // X-products take the mode of the phase (xmode).
   // Residual product: right A*Y (m x m), left Y*A (n x n).
-  Acc res_prod(const QMat& Y) {
+  void res_run(const QMat& Y, const CombineArgs& a, bool with_partials, int red_slot) {
     Lcur = Lx;
-    return left ? prod(Y, A, xmode) : prod(A, Y, xmode);
+    if (left) prod_run(Y, A, xmode, a, with_partials, red_slot);
+    else prod_run(A, Y, xmode, a, with_partials, red_slot);
   }
   // Apply a side polynomial T (s x s) to Y (n x m): right Y*T, left T*Y.
-  Acc apply(const QMat& Y, const QMat& T) {
+  void apply_run(const QMat& Y, const QMat& T, const CombineArgs& a, bool with_partials = false) {
     Lcur = Lx;
     const int save = xS;
     if (xmode == PM_EMU && !dbl) xS = xSu;
     else if (xmode == PM_EMU && dbl && xSp > 0) xS = xSp;
-    Acc r = left ? prod(T, Y, xmode) : prod(Y, T, xmode);
+    if (left) prod_run(T, Y, xmode, a, with_partials);
+    else prod_run(Y, T, xmode, a, with_partials);
     xS = save;
-    return r;
   }
   const char* tform() const { return left ? "fa" : "fb"; }
   QMat sq(const char* name, bool a, bool b) { return mat(c, name, s, s, MST_F | MST_D, a, b); }
@@ -590,104 +687,95 @@ struct Solver {
       pre_res = false;
       return pre_R;
     }
-    Acc acc = res_prod(Y);
     QMat R = sq(name, strchr(forms, 'a') != nullptr, strchr(forms, 'b') != nullptr);
-    CombineArgs a = base_args(s, s, &acc);
+    CombineArgs a = base_args(s, s, nullptr);
     out(a, R, forms, -1.0, 1.0);
-    run(a, norm, 4);
+    res_run(Y, a, norm, 4);
     return R;
   }
 
-  // Xn = base + acc (master + both forms) with the stop-test partials vs X[cur].
-  void update(const QMat& base, const Acc& acc) {
+  // X_{j+1} = base + (Y T | T Y) (master + both forms) with the stop-test
+  // partials against X[cur].
+  void apply_update(const QMat& Y, const QMat& T, const QMat& base) {
     QMat& Xn = X[cur ^ 1];
-    CombineArgs a = base_args(n, m, &acc);
+    CombineArgs a = base_args(n, m, nullptr);
     aux(a, 0, X[cur]);
     aux(a, 1, base);
     OutSpec& o = out(a, Xn, "fab", 1.0);
     o.caux[1] = 1.0;  // + base (aux 0 = X_j is only the reference of the norm)
-    run(a, true);
+    apply_run(Y, T, a, true);
   }
 
   // ---------------- one iteration of each method ----------------
   void step_ns() {
     QMat R = residual(X[cur], "R", tform(), true);
-    Acc acc = apply(X[cur], R);
-    update(X[cur], acc);
+    apply_update(X[cur], R, X[cur]);
   }
 
   void step_qsai(double b1, double b2) {
     QMat R = residual(X[cur], "R", "fab", true);
-    Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", true, true);
     {
-      CombineArgs a = base_args(s, s, &a2);
+      CombineArgs a = base_args(s, s, nullptr);
       out(a, R2, "fab", 1.0);
-      run(a);
+      rprod_run(R, R, a);
     }
-    Acc a4 = rprod(R2, R2);
     QMat R4 = sq("R4", false, false), Fa = sq("Fa", true, false), Fb = sq("Fb", false, true);
     {
-      CombineArgs a = base_args(s, s, &a4);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R2);
       out(a, R4, "f", 1.0);
       out(a, Fa, "fa", 1.0).caux[0] = b1;
       out(a, Fb, "fb", 1.0).caux[0] = b2;
-      run(a);
+      rprod_run(R2, R2, a);
     }
-    Acc ab = rprod(Fa, Fb);
     QMat q = sq("q", false, true);
     {
-      CombineArgs a = base_args(s, s, &ab);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R2);
       aux(a, 1, R4);
       OutSpec& o = out(a, q, "fb", 1.0);
       o.caux[0] = b1 + b2;
       o.caux[1] = 2.0;
-      run(a);
+      rprod_run(Fa, Fb, a);
     }
-    Acc rq = rprod(R, q);
     QMat t = sq("t", left, !left);
     {
-      CombineArgs a = base_args(s, s, &rq);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R);
       aux(a, 1, q);
       OutSpec& o = out(a, t, tform(), 1.0);
       o.caux[0] = 1.0;
       o.caux[1] = 1.0;
-      run(a);
+      rprod_run(R, q, a);
     }
-    Acc xt = apply(X[cur], t);
-    update(X[cur], xt);
+    apply_update(X[cur], t, X[cur]);
   }
 
   void step_qhpi19(const double* k) {
     // k: a1 a2 a3 b1 b2 c1 c2 d1 d2 d3 e1 e2
     const double c1 = k[5], c2 = k[6], d1 = k[7], d2 = k[8], d3 = k[9], e1 = k[10], e2 = k[11];
     QMat R = residual(X[cur], "R", "fab", true);
-    Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", true, true), S = sq("S", true, false);
     {
-      CombineArgs a = base_args(s, s, &a2);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R);
       out(a, R2, "fab", 1.0);
       out(a, S, "fa", 1.0).caux[0] = 1.0;
-      run(a);
+      rprod_run(R, R, a);
     }
-    Acc a4 = rprod(R2, R2);
     QMat R4 = sq("R4", false, false), Fa = sq("Fa", true, false), Fb = sq("Fb", false, true);
     {
-      CombineArgs a = base_args(s, s, &a4);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R2);
       out(a, R4, "f", 1.0);
       out(a, Fa, "fa", 1.0).caux[0] = d1;
       out(a, Fb, "fb", 1.0).caux[0] = d2;
-      run(a);
+      rprod_run(R2, R2, a);
     }
-    Acc ab = rprod(Fa, Fb);
     QMat u = sq("u", false, false), v = sq("v", true, false), w = sq("w", false, true);
     {
-      CombineArgs a = base_args(s, s, &ab);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R2);
       aux(a, 1, R4);
       OutSpec& ou = out(a, u, "f", 1.0);
@@ -699,12 +787,11 @@ struct Solver {
       OutSpec& ow = out(a, w, "fb", 1.0);
       ow.caux[0] = d1 + d2 + e1;
       ow.caux[1] = 2.0 + e2;
-      run(a);
+      rprod_run(Fa, Fb, a);
     }
-    Acc vw = rprod(v, w);
     QMat g = sq("g", false, true);
     {
-      CombineArgs a = base_args(s, s, &vw);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, u);
       aux(a, 1, R2);
       aux(a, 2, R4);
@@ -712,18 +799,16 @@ struct Solver {
       o.caux[0] = 2.0;
       o.caux[1] = d3 + e1 + c1;
       o.caux[2] = e2 + c2;
-      run(a);
+      rprod_run(v, w, a);
     }
-    Acc sg = rprod(S, g);
     QMat t = sq("t", left, !left);
     {
-      CombineArgs a = base_args(s, s, &sg);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, S);
       out(a, t, tform(), 1.0).caux[0] = 1.0;
-      run(a);
+      rprod_run(S, g, a);
     }
-    Acc xt = apply(X[cur], t);
-    update(X[cur], xt);
+    apply_update(X[cur], t, X[cur]);
   }
 
   // Unfactorized hyperpower iteration of order k (Definition 1):
@@ -735,59 +820,53 @@ struct Solver {
     QMat H[2] = {sq("h0", true, true), sq("h1", true, true)};
     const QMat* h = &R;
     for (int i = 2; i < k; i++) {
-      Acc acc = rprod(R, *h);
       QMat& hn = H[i & 1];
-      CombineArgs a = base_args(s, s, &acc);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R);
       out(a, hn, i == k - 1 ? tform() : "fb", 1.0).caux[0] = 1.0;
-      run(a);
+      rprod_run(R, *h, a);
       h = &hn;
     }
-    Acc xt = apply(X[cur], *h);
-    update(X[cur], xt);
+    apply_update(X[cur], *h, X[cur]);
   }
 
   // QRAPID correction  W + Y (I - A W)  (right) / W + (I - W A) Y (left) into Z.
   void rapid_correct(const QMat& W, const QMat& Y, QMat& Z, bool is_final) {
     QMat E = residual(W, "E", tform());
-    Acc acc = apply(Y, E);
     if (is_final) {
-      update(W, acc);
+      apply_update(Y, E, W);
       return;
     }
-    CombineArgs a = base_args(n, m, &acc);
+    CombineArgs a = base_args(n, m, nullptr);
     aux(a, 0, W);
     out(a, Z, "fab", 1.0).caux[0] = 1.0;
-    run(a);
+    apply_run(Y, E, a);
   }
 
   void step_qrapid(int N) {
     QMat R = residual(X[cur], "R", "fab", true);
-    Acc a2 = rprod(R, R);
     QMat R2 = sq("R2", false, true);
     {
-      CombineArgs a = base_args(s, s, &a2);
+      CombineArgs a = base_args(s, s, nullptr);
       out(a, R2, "fb", 1.0);
-      run(a);
+      rprod_run(R, R, a);
     }
-    Acc a3 = rprod(R, R2);
     QMat tU = sq("t", left, !left);
     {
-      CombineArgs a = base_args(s, s, &a3);
+      CombineArgs a = base_args(s, s, nullptr);
       aux(a, 0, R);
       aux(a, 1, R2);
       OutSpec& o = out(a, tU, tform(), 0.25);
       o.caux[0] = 1.0;
       o.caux[1] = 1.0;
-      run(a);
+      rprod_run(R, R2, a);
     }
     QMat Zb[3] = {big("Z0"), big("Z1"), big("Z2")};
-    Acc xt = apply(X[cur], tU);
     {  // U = X + X tU
-      CombineArgs a = base_args(n, m, &xt);
+      CombineArgs a = base_args(n, m, nullptr);
       aux(a, 0, X[cur]);
       out(a, Zb[0], "fab", 1.0).caux[0] = 1.0;
-      run(a);
+      apply_run(X[cur], tU, a);
     }
     rapid_correct(Zb[0], X[cur], Zb[1], false);  // V = U + X (I - A U)
     int y = 0, w = 1;                             // Y_0 = U, W_0 = V
@@ -1047,6 +1126,7 @@ void qpinv_default_options(qpinv_options* o) {
   o->profile = 0;
   o->batched_tile = -1;
   o->hyper_order = 19;
+  o->fuse_epilogue = 1;
 }
 
 static int check_opts(const qpinv_options* o) {
@@ -1059,6 +1139,7 @@ static int check_opts(const qpinv_options* o) {
   if (o->side < 0 || o->side > 2 || o->stop_rule < 0 || o->stop_rule > 1) return 0;
   if (o->batched_tile < -1 || o->batched_tile >= qp::BATCH_TILES) return 0;
   if (o->hyper_order < 2 || o->hyper_order > 64) return 0;
+  if (o->fuse_epilogue < 0 || o->fuse_epilogue > 1) return 0;
   return 1;
 }
 
@@ -1108,6 +1189,7 @@ void qpinv_free(qpinv_ctx* c) {
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (void* p : c->bh_buf)
     if (p) cudaFreeHost(p);
+  if (c->bmaps_host) cudaFreeHost(c->bmaps_host);
   if (c->bgraph.exec) cudaGraphExecDestroy(c->bgraph.exec);
   if (c->bgraph.stream) cudaStreamDestroy(c->bgraph.stream);
   delete c;
@@ -1160,6 +1242,11 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     bool emu = o.precision == QPINV_PREC_EMU || (!fp64 && wrong_side);
     if (!fp64 && !tc_supported()) return fail(c, QPINV_E_UNSUPPORTED, "tcgen05 path needs an sm_103 device");
     long long gemms_before = 0;
+    // A solve started from a learned alpha that does not contract is
+    // restarted once from the safe alpha (north of Thm. 1's bound the
+    // iteration diverges along the top singular direction, which the
+    // features' Lanczos estimate theta_1 <= sigma_1^2 may have missed).
+    bool force_safe = false;
     // A MIXED solve whose result fails the Penrose check is repeated with
     // FP64-accurate products: rank-deficient A (and A beyond the tensor-core
     // phase's conditioning reach) amplifies BF16 rounding in the complement of
@@ -1195,8 +1282,10 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       // Network prediction, accepted only if it passes Thm. 1's contraction
       // condition alpha sigma_1^2 < 2 with a 5% margin for the Lanczos
       // estimate theta_1 <= sigma_1^2; otherwise the safe alpha is used.
+      // The solve itself then checks that the residual contracts.
       amode = QPINV_ALPHA_SAFE;
-      if (!c->alpha_w.empty() && a_f2 > 0.0) {
+      res.alpha_fallback = 1;
+      if (!force_safe && !c->alpha_w.empty() && a_f2 > 0.0) {
         ck(c, launch_f64_to_f32(a, m, n, S.A.f, c->st), "A to fp32");
         float feat[32];
         double theta1 = 0.0;
@@ -1206,6 +1295,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
         if (std::isfinite(al) && al > 0.0 && al * theta1 * 1.05 < 2.0) {
           alpha = al;
           amode = QPINV_ALPHA_LEARNED;
+          res.alpha_fallback = 0;
         }
       }
     }
@@ -1286,6 +1376,8 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     }
     int polish_done = 0, tc_done = 0;
     double prev_rel = INFINITY, xnorm = std::sqrt(a_f2) * alpha;
+    double prev_rnorm = INFINITY;  // ||R_{j-1}||_F (contraction check of a learned alpha)
+    bool learned_failed = false;
     res.status = QPINV_NOT_CONVERGED;
     res.iters = 0;
     for (int j = 0; j < max_iter; j++) {
@@ -1350,6 +1442,18 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       if (h[2] > 0.0 || !std::isfinite(d) || !std::isfinite(nx)) {
         res.status = QPINV_DIVERGED;
         break;  // X[cur] is the last finite iterate
+      }
+      if (amode == QPINV_ALPHA_LEARNED) {
+        // First-step contraction check (and the next few steps): in exact
+        // arithmetic R_{j+1} = R_j^p with the spectrum of R_0 in (-1, 1] when
+        // alpha sigma_1^2 < 2, so ||R_j||_F cannot grow; a growth beyond
+        // rounding (5 %) while the residual is still O(1)-ish means
+        // alpha sigma_1^2 > 2.  Later divergence shows up as DIVERGED.
+        if (j <= 4 && rnorm > 1.05 * prev_rnorm && prev_rnorm > 1e-4) {
+          learned_failed = true;
+          break;
+        }
+        prev_rnorm = rnorm;
       }
       const double drel = nx > 0 ? d / nx : d;
       res.delta = d;
@@ -1452,6 +1556,13 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
       }
       prev_rel = drel;
     }
+    if (amode == QPINV_ALPHA_LEARNED && !force_safe &&
+        (learned_failed || res.status == QPINV_DIVERGED || res.status == QPINV_NOT_CONVERGED)) {
+      if (c->trace) fprintf(stderr, "qpinv: learned alpha %.6e did not contract; restart from the safe alpha\n", alpha);
+      gemms_before += S.gemms;
+      force_safe = true;
+      continue;
+    }
     res.tc_iters = tc_done;
     res.polish_iters = polish_done;
     if (!S.dbl) {
@@ -1469,7 +1580,7 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     if (c->trace)
       fprintf(stderr, "qpinv: attempt %d precision %d status %d iters %d E1_rel %.3e\n", attempt, res.precision,
               res.status, res.iters, res.E_rel[0]);
-    if (attempt == 0 && o.precision == QPINV_PREC_MIXED && !emu && o.penrose && !(res.E_rel[0] <= 1e-6)) {
+    if (o.precision == QPINV_PREC_MIXED && !emu && o.penrose && !(res.E_rel[0] <= 1e-6)) {
       gemms_before = res.gemms;
       emu = true;
       continue;
@@ -1958,6 +2069,12 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
     run.dev_order = buf(c, "batch.order", sizeof(int) * (size_t)batch + 64);
     run.dev_results = buf(c, "batch.results", batched_result_bytes() * (size_t)batch + 64);
     run.dev_counter = (int*)buf(c, "batch.counter", 64);
+    // tensor-core engine: slice scratch and TMA maps for one slot per SM
+    run.tc_ws = buf(c, "batch.tcws", batched_tc_slot_bytes() * (size_t)nsm);
+    run.tc_maps = buf(c, "batch.tcmaps", sizeof(CUtensorMap) * 2 * (size_t)nsm + 64);
+    if (!c->bmaps_host) ck(c, cudaMallocHost(&c->bmaps_host, sizeof(CUtensorMap) * 2 * (size_t)nsm + 64), "pinned maps");
+    run.host_maps = c->bmaps_host;
+    run.err = c->d_err;
     const size_t need[3] = {batched_item_bytes() * (size_t)batch, sizeof(int) * (size_t)batch,
                             batched_result_bytes() * (size_t)batch};
     for (int t = 0; t < 3; t++)
@@ -2024,6 +2141,7 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
           // three iterations per matrix: the tiles' relative speed, not a converged solve
           solve_with(t, cnt, sm.data(), sn.data(), sa.data(), sla.data(), sx.data(), slx.data(), nullptr,
                      std::min(max_iter, 3));
+          check_kernel_error(c);
           const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a0).count();
           if (c->trace)
             fprintf(stderr, "qpinv batched tile %s: %.2f ms on %d sampled matrices\n", batched_tile_name(t), ms, cnt);
@@ -2043,6 +2161,7 @@ int qpinv_solve_batched(qpinv_ctx* c, void* stream, int batch, const int* m, con
       solve_with(tile, batch, m, n, A, lda, X, ldx, &c->bgraph, max_iter);
       return cudaSuccess;
     });
+    check_kernel_error(c);  // bounded waits of the tensor-core engine
     if (c->bgraph.replays > replays && c->bgraph.replays > 1) c->stats.batched_graph_replays++;
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();

@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace qp {
@@ -79,6 +81,28 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// Sign pattern of the real form of the Hamilton product: block (r, c) of
+// M(B) is -B_{r xor c} for these (r, c), +B_{r xor c} otherwise.
+__host__ __device__ constexpr bool qsign_neg(int r, int c) {
+  return (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) || (r == 3 && (c == 0 || c == 1));
+}
+// The 16 signed (r, c) MMAs of one K = 16 step: A plane r times B plane
+// r xor c into component c's accumulator (d_tmem + c * ncols), the sign from
+// the instruction descriptor's negate-A bit (bit 13).
+template <int SWB>
+__device__ __forceinline__ void qmma_k16(uint32_t d_tmem, uint32_t ncols, uint32_t a_base, uint32_t a_plane,
+                                         uint32_t b_base, uint32_t b_plane, uint32_t idesc, bool fresh) {
+  constexpr uint32_t NEG_A = 1u << 13;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const uint64_t ad = smem_desc_sw<SWB>(a_base + r * a_plane);
+    const uint32_t acc = (fresh && r == 0) ? 0u : 1u;
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+      mma_bf16(d_tmem + c * ncols, ad, smem_desc_sw<SWB>(b_base + (r ^ c) * b_plane),
+               qsign_neg(r, c) ? idesc | NEG_A : idesc, acc);
+  }
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -124,6 +148,27 @@ __device__ __forceinline__ void tmem_st32u(uint32_t taddr, const uint32_t* r) {
         "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
 }
+// 32 lanes x 16 consecutive columns (one row of 16 values per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int t = 0; t < 16; t++) v[t] = __uint_as_float(r[t]);
+}
+__device__ __forceinline__ void tmem_ld16u(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Epilogue row writers: lane j handles column j of up to 32 consecutive rows
@@ -154,6 +199,22 @@ __device__ __forceinline__ void store_rows32(float* __restrict__ dst, long ld, i
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (bit d of `done`; a repeated call from a racing
+// thread is harmless).  The attribute is per device: a flag shared by all
+// devices would skip the call on the second one.
+template <typename Kern>
+cudaError_t ensure_smem_attr(Kern kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -35,7 +35,8 @@ class qpinv_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("split_level", ctypes.c_int), ("polish_iters", ctypes.c_int),
                 ("alpha_mode", ctypes.c_int), ("alpha_user", ctypes.c_double), ("qrapid_N", ctypes.c_int),
                 ("side", ctypes.c_int), ("stop_rule", ctypes.c_int), ("penrose", ctypes.c_int),
-                ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int), ("hyper_order", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int), ("hyper_order", ctypes.c_int),
+                ("fuse_epilogue", ctypes.c_int)]
 
 
 class qpinv_result(ctypes.Structure):
@@ -43,7 +44,7 @@ class qpinv_result(ctypes.Structure):
                 ("polish_iters", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_source", ctypes.c_int),
                 ("side", ctypes.c_int), ("precision", ctypes.c_int), ("delta", ctypes.c_double),
                 ("delta_rel", ctypes.c_double), ("E", ctypes.c_double * 4), ("E_rel", ctypes.c_double * 4),
-                ("gemms", ctypes.c_longlong), ("time_ms", ctypes.c_double)]
+                ("gemms", ctypes.c_longlong), ("time_ms", ctypes.c_double), ("alpha_fallback", ctypes.c_int)]
 
 
 class qpinv_stats(ctypes.Structure):
@@ -55,7 +56,7 @@ class qpinv_stats(ctypes.Structure):
                 ("emu_gemm_launches", ctypes.c_longlong), ("emu_gemm_ms", ctypes.c_double),
                 ("emu_gemm_flops", ctypes.c_double), ("emu_gemm_flops_issued", ctypes.c_double),
                 ("batched_tile", ctypes.c_longlong), ("batched_tune_ms", ctypes.c_double),
-                ("batched_graph_replays", ctypes.c_longlong)]
+                ("batched_graph_replays", ctypes.c_longlong), ("fused_epilogues", ctypes.c_longlong)]
 
 
 class qpinv_cur_result(ctypes.Structure):
@@ -223,7 +224,7 @@ class Context:
 
     def configure(self, precision=None, split_level=None, polish_iters=None, alpha=None, alpha_user=None,
                   qrapid_N=None, side=None, stop=None, penrose=None, profile=None, batched_tile=None,
-                  hyper_order=None, _apply=True):
+                  hyper_order=None, fuse_epilogue=None, _apply=True):
         o = self.options
         if precision is not None: o.precision = PRECISION[precision]
         if split_level is not None: o.split_level = int(split_level)
@@ -237,6 +238,7 @@ class Context:
         if profile is not None: o.profile = int(bool(profile))
         if batched_tile is not None: o.batched_tile = int(batched_tile)
         if hyper_order is not None: o.hyper_order = int(hyper_order)
+        if fuse_epilogue is not None: o.fuse_epilogue = int(bool(fuse_epilogue))
         if _apply:
             _check(self.h, lib().qpinv_set_options(self.h, ctypes.byref(o)), "qpinv_set_options")
 
@@ -467,4 +469,5 @@ def result_dict(r):
                 polish_iters=r.polish_iters, alpha=r.alpha, alpha_source=r.alpha_source,
                 side="left" if r.side == 2 else "right", precision=PRECISION_NAME.get(r.precision, r.precision),
                 delta=r.delta, delta_rel=r.delta_rel,
-                E=list(r.E), E_rel=list(r.E_rel), gemms=r.gemms, time_ms=r.time_ms)
+                E=list(r.E), E_rel=list(r.E_rel), gemms=r.gemms, time_ms=r.time_ms,
+                alpha_fallback=r.alpha_fallback)

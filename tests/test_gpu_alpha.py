@@ -6,6 +6,7 @@ accuracy (E1/||A|| within 10x of the safe-alpha solve's, or <= 1e-10)."""
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mlp
 from paper_2605_01464_gb300 import inputs as I
 
@@ -96,3 +97,72 @@ def test_learned_alpha_saves_iterations(trained, method):
     assert all(r[3] <= max(1e-10, 10.0 * r[2]) and r[2] <= 1e-7 for r in rows), rows
     assert all(r[5] == r[6] for r in rows), rows
     assert sum(r[4] == 4 for r in rows) >= len(rows) // 2, rows  # prediction accepted (QPINV_ALPHA_LEARNED)
+
+
+def _constant_network(value):
+    """Weights whose prediction is y = log(alpha theta_1) = log(value) for any input."""
+    w = np.zeros(mlp.NWEIGHTS, dtype=np.float32)
+    w[mlp.OFF_SD:] = 1.0
+    w[mlp.OFF_B3] = np.log(value)
+    return w
+
+
+def _hidden_top_direction(n, seed):
+    """Real A = Q diag(s) Q^T (zero imaginary planes), s = 1, 0.96, then
+    0.9 .. 0.05, whose top singular vector u1 is orthogonal to the four
+    component vectors of the features' Lanczos start vector
+    q_i = 1 / (1 + 0.37 (i mod 7) + 0.11 i) (i over interleaved quaternion
+    components).  The Krylov space of A^H A from q then holds u1 only through
+    rounding, so theta_1 is close to s_2^2 = 0.9216, below sigma_1^2 = 1 by
+    more than the 5 % margin of the acceptance test."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(4 * n)
+    q = (1.0 / (1.0 + 0.37 * (i % 7) + 0.11 * i)).reshape(n, 4)  # columns: component vectors
+    Qq, _ = np.linalg.qr(q)
+    g = rng.normal(size=n)
+    u1 = g - Qq @ (Qq.T @ g)
+    u1 /= np.linalg.norm(u1)
+    Q, _ = np.linalg.qr(np.column_stack([u1, rng.normal(size=(n, n - 1))]))
+    Q[:, 0] *= np.sign(Q[:, 0] @ u1)
+    s = np.concatenate([[1.0, 0.96], np.geomspace(0.9, 0.05, n - 2)])
+    A = np.zeros((4, n, n))
+    A[0] = (Q * s) @ Q.T
+    return A, u1, q
+
+
+def test_learned_alpha_that_does_not_contract_falls_back_to_safe(qp):
+    """The acceptance test alpha theta_1 * 1.05 < 2 trusts theta_1 ~ sigma_1^2;
+    here theta_1 misses the top direction, so a network predicting
+    alpha theta_1 = 1.9 gives alpha sigma_1^2 ~ 2.06 > 2 (Thm. 1's bound):
+    the residual grows on u1 and the solve must restart from the safe alpha."""
+    A, u1, q = _hidden_top_direction(40, 3)
+    assert np.abs(q.T @ u1).max() <= 1e-12
+    ctx = qp.Context(0)
+    try:
+        ctx.alpha_weights(_constant_network(1.9))
+        f, theta1 = ctx.alpha_features(cuda(A))
+        assert theta1 <= 0.95, theta1  # the estimate misses sigma_1^2 = 1
+        ctx.configure(alpha="learned")
+        X, info = ctx.solve(cuda(A), "qhpi19", tol=1e-12, max_iter=200)
+        assert info["alpha_fallback"] == 1 and info["alpha_source"] == 0, info
+        assert info["status"] in ("converged", "plateau"), info
+        assert abs(info["alpha"] - oracle_alpha_safe(A)) <= 1e-12 * info["alpha"], info
+        Xo, _ = oracle.solve(A, "qhpi19", tol=1e-12, max_iter=200)
+        assert rel(X.cpu().numpy(), Xo) <= 1e-10, (rel(X.cpu().numpy(), Xo), info)
+        # positive control: on a Gaussian matrix theta_1 is accurate and the
+        # same prediction (alpha sigma_1^2 ~ 1.9) is kept
+        G = I.gaussian_quaternion(48, 40, 5)
+        X, info = ctx.solve(cuda(G), "qhpi19", tol=1e-12, max_iter=200)
+        assert info["alpha_fallback"] == 0 and info["alpha_source"] == 4, info
+        assert info["status"] in ("converged", "plateau"), info
+        assert info["alpha"] * oracle.sigma_max(G) ** 2 < 2.0
+    finally:
+        ctx.close()
+
+
+def oracle_alpha_safe(A):
+    return oracle.alpha(A, "safe")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)

@@ -56,11 +56,14 @@ def test_batched_matches_exact_pinv(qp, method):
     ctx.close()
 
 
-def test_batched_agrees_with_oracle_iteration(qp):
-    """Full-rank odd shapes: the batched X equals the FP64 oracle's X."""
-    shapes = [(5, 4), (17, 31), (40, 24), (64, 64)]
+@pytest.mark.parametrize("tile", [-1, 5])
+def test_batched_agrees_with_oracle_iteration(qp, tile):
+    """Full-rank odd shapes: the batched X equals the FP64 oracle's X (autotuned
+    engine, and the tensor-core engine with its 128 x 64 tiles spanning
+    two row tiles and four column tiles at 256 x 200)."""
+    shapes = [(5, 4), (17, 31), (40, 24), (64, 64), (256, 200), (130, 256)]
     mats = [I.gaussian_quaternion(m, n, 70 + m) for (m, n) in shapes]
-    ctx = qp.Context(0)
+    ctx = qp.Context(0, batched_tile=tile)
     Xs, infos = ctx.solve_batched([torch.from_numpy(a).cuda() for a in mats], "qhpi19", tol=1e-13)
     for a, x in zip(mats, Xs):
         xo, _ = oracle.solve(a, "qhpi19", tol=1e-13)
@@ -88,9 +91,10 @@ def test_batched_rejects_oversize(qp):
     ctx.close()
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 def test_batched_every_tile_shape(qp, tile):
-    """Each CTA GEMM tile shape (16x16 .. 64x64) gives the same accuracy."""
+    """Each CTA GEMM engine -- the CUDA-core tile shapes 16x16 .. 64x64 and the
+    tensor-core exact-slice engine (5) -- gives the same accuracy."""
     mats = batch_inputs()[:12] + [I.gaussian_quaternion(70, 130, 91), I.gaussian_quaternion(200, 90, 92)]
     ctx = qp.Context(0, batched_tile=tile)
     As = [torch.from_numpy(a).cuda() for a in mats]
@@ -112,7 +116,7 @@ def test_batched_autotune_and_graph_replay(qp):
     Xs1, _ = ctx.solve_batched(As, "qhpi19", tol=1e-12, max_iter=200)
     X1 = [x.clone() for x in Xs1]
     st1 = ctx.stats()
-    assert 0 <= st1["batched_tile"] < 5 and st1["batched_tune_ms"] > 0
+    assert 0 <= st1["batched_tile"] < 6 and st1["batched_tune_ms"] > 0
     Xs2, _ = ctx.solve_batched(As, "qhpi19", tol=1e-12, max_iter=200, Xs=Xs1)
     st2 = ctx.stats()
     assert st2["batched_tune_ms"] == st1["batched_tune_ms"]  # signature cached

@@ -1,0 +1,136 @@
+"""GPU parity at the workloads' full sizes, in the launch configurations the
+bench times, against the FP64 oracle.
+
+* The quaternion GEMM kernels at M, N, K >= 2048: the exact-slice kernel's
+  persistent grid then gives every CTA several (tile, level group) work items
+  (1024 items on 152 SMs at 2048^2), and the 16-row-tile rasterization of
+  both kernels covers full groups; the ragged case (M = 2176 = 17 row tiles,
+  N = 2100, K = 2056) adds a partial raster group and ragged tails in every
+  dimension.  Reference: the oracle's FP64 product, element by element
+  (relative Frobenius error).
+* The 2048^2 QHPI19 mixed-precision solve of the bench (sigma log-spaced
+  1..1e-6) and a rank-deficient 2560 x 2048 solve (rank 1024, sigma
+  geometric 1..1e-4), each against the exact pseudoinverse V Sigma^-1 U^H of
+  the generator's factors, formed by the oracle.
+
+Tolerances (relative Frobenius error):
+  * BF16-split GEMM with FP32 tensor-core accumulation: 1 term 1e-2,
+    2 terms 3e-4, 3 terms 5e-5 x max(1, K / 1000) -- the accumulation error
+    grows about linearly with K (2.6e-5 measured at K = 1000);
+  * exact-slice GEMM: 4 slices 1e-7, 8 slices 1e-14 (FP64 level; the
+    oracle's own k-ordered sum carries about sqrt(K) u);
+  * solves: E1/||A||_F <= 1e-10 (the stated FP64-polished tolerance) and X
+    within 1e-8 of V Sigma^-1 U^H for kappa = 1e6 -- the reference itself is
+    the pseudoinverse of A before A was rounded to FP64, which moves A^dagger
+    by about kappa u relative (1e-10) and the iteration adds its own kappa u
+    rounding; for the rank-deficient case the iteration also multiplies
+    null-space rounding by its order every step (about kappa^2 u over a
+    solve, 1e-8 at kappa = 1e4), bound 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_01464_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def tol_tc(L, K):
+    return {1: 1e-2, 2: 3e-4}.get(L, 5e-5 * max(1.0, K / 1000.0))
+
+
+EMU_TOL = {4: 1e-7, 8: 1e-14}
+
+
+@pytest.fixture(scope="module")
+def qp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_01464_gb300 import build, qpinv
+    build.build()
+    return qpinv
+
+
+@pytest.fixture(scope="module")
+def ctx(qp):
+    c = qp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SHAPES = {"square2048": (2048, 2048, 2048), "ragged2176": (2176, 2056, 2100)}
+
+
+@pytest.fixture(scope="module")
+def products():
+    out = {}
+    for name, (m, k, n) in SHAPES.items():
+        A = I.gaussian_quaternion(m, k, 41)
+        B = I.gaussian_quaternion(k, n, 42)
+        out[name] = (A, B, oracle.matmul(A, B))
+    return out
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_qgemm_tc_full_size(ctx, products, shape, L):
+    A, B, Co = products[shape]
+    C = ctx.qgemm(dev(A), dev(B), precision="tc", split_level=L).cpu().numpy()
+    err = rel(C, Co)
+    assert err <= tol_tc(L, A.shape[2]), (shape, L, err)
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("S", [4, 8])
+def test_qgemm_exact_slices_full_size(ctx, products, shape, S):
+    A, B, Co = products[shape]
+    C = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=S).cpu().numpy()
+    err = rel(C, Co)
+    assert err <= EMU_TOL[S], (shape, S, err)
+    if S == 8:
+        # element by element as well: every entry within 1e-13 of the row/column scale
+        scale = np.sqrt((A ** 2).sum(axis=(0, 2)))[:, None] * np.sqrt((B ** 2).sum(axis=(0, 1)))[None, :]
+        assert np.max(np.abs(C - Co) / scale[None]) <= 1e-13
+
+
+def test_solve_logspaced_2048_mixed_against_exact_pinv(ctx):
+    """The bench's workload: 2048^2, sigma log-spaced 1..1e-6, QHPI19, mixed
+    precision, safe alpha, relative tolerance 1e-12."""
+    A, U, s, V = I.logspaced_square(2048, 1e-6, seed_u=1, seed_v=2, device="cuda")
+    ctx.configure(precision="mixed", alpha="safe", side="auto", polish_iters=2)
+    X, info = ctx.solve(dev(A), "qhpi19", tol=1e-12, max_iter=200)
+    want = oracle.pinv_from_svd(U, s, V)
+    err = rel(X.cpu().numpy(), want)
+    print("2048^2 logspaced qhpi19 mixed: X rel err %.3e, E_rel %s, iters %d, status %s"
+          % (err, info["E_rel"], info["iters"], info["status"]))
+    assert info["status"] in ("converged", "plateau"), info
+    assert info["precision"] == "mixed", info
+    assert info["E_rel"][0] <= 1e-10, info
+    assert err <= 1e-8, (err, info)
+
+
+@pytest.mark.parametrize("method", ["qhpi19", "ns"])
+def test_solve_rank_deficient_2560x2048_against_exact_pinv(ctx, method):
+    """Rank 1024 of 2048 columns, sigma geometric 1..1e-4 (the rank-deficient
+    workload's structure at a quarter of its size): the mixed-precision solve
+    fails its Penrose check and is repeated with FP64-accurate products."""
+    A, QL, s, QR = I.rank_deficient(2560, 2048, 1024, 1e-4, seed_l=4, seed_r=5, device="cuda")
+    ctx.configure(precision="mixed", alpha="safe", side="auto", polish_iters=2)
+    X, info = ctx.solve(dev(A), method, tol=1e-12, max_iter=300)
+    want = oracle.pinv_from_svd(QL, s, QR)
+    err = rel(X.cpu().numpy(), want)
+    print("2560x2048 rank 1024 %s: X rel err %.3e, E_rel %s, iters %d, status %s, precision %s"
+          % (method, err, info["E_rel"], info["iters"], info["status"], info["precision"]))
+    assert info["status"] in ("converged", "plateau"), info
+    assert info["E_rel"][0] <= 1e-10, info
+    assert err <= 1e-6, (err, info)

@@ -277,3 +277,26 @@ def test_solve_logspaced_kappa_1e6(ctx, method):
     assert rel(X.cpu().numpy(), want) <= 1e-8, (rel(X.cpu().numpy(), want), info)
     Eo, Ro = oracle.penrose(A, X.cpu().numpy())
     assert Ro[0] <= 1e-10  # the oracle's own FP64 evaluation of E1 agrees with the bound
+
+
+@pytest.mark.parametrize("method,N", [("qhpi19", 5), ("qsai", 5), ("qrapid", 2), ("ns", 5), ("qhpim", 5)])
+def test_fused_epilogue_matches_separate_combine(ctx, method, N):
+    """The combine pass run in the tensor-core GEMM's epilogue and the same
+    pass as its own kernel give the same iterates (same FP32 arithmetic in
+    the same order; only the FMA contraction of two compilations may
+    differ), on ragged shapes (200 x 136: partial row and column tiles)."""
+    A = I.gaussian_quaternion(200, 136, 17)
+    got = {}
+    for fuse in (True, False):
+        ctx.configure(precision="tc", qrapid_N=N, hyper_order=7, fuse_epilogue=fuse)
+        ctx.reset_stats()
+        X, info = ctx.solve(dev(A), method, tol=1e-6, max_iter=60)
+        st = ctx.stats()
+        assert (st["fused_epilogues"] > 0) == fuse, st
+        got[fuse] = (X.cpu().numpy(), info)
+    ctx.configure(precision="mixed", fuse_epilogue=True, hyper_order=19)
+    (X1, i1), (X2, i2) = got[True], got[False]
+    assert i1["iters"] == i2["iters"], (i1, i2)
+    assert rel(X1, X2) <= 1e-6, rel(X1, X2)
+    Xo, _ = oracle.solve(A, method, tol=1e-6, max_iter=60, N=N, order=7)
+    assert rel(X1, Xo) <= 1e-5

@@ -777,18 +777,18 @@ def bench_learned(args, torch, qpinv):
 
     ctx = qpinv.Context(0)
     t0 = time.perf_counter()
-    feats, labels, _ = LA.make_dataset(ctx, args.train_count, 32, 256, seed=11, device="cuda", to_device=cuda)
+    feats, labels, _ = LA.make_dataset_gpu(ctx, torch, args.train_count, 32, 512, seed=11)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     loss = ctx.alpha_train(feats, labels, epochs=300, batch=100, lr=3e-3, seed=5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     rows = []
-    shapes = [(1024, 1024), (2048, 1024)]
+    shapes = [(1024, 1024), (2048, 1024), (2048, 2048), (4096, 4096), (4096, 2048)]
     with ClockSampler(0) as clk:
         for k, fam in enumerate(("logspaced", "geometric", "clustered")):
             for (m, n) in shapes:
-                A = cuda(LA.heldout_matrix(fam, m, n, 700 + 10 * k + m // 1024, device="cuda")[0])
+                A = cuda(LA.heldout_matrix(fam, m, n, 700 + 10 * k + m // 1024 + n // 512, device="cuda")[0])
                 res = {}
                 for mode in ("safe", "learned"):
                     ctx.configure(alpha=mode)
@@ -810,8 +810,9 @@ def bench_learned(args, torch, qpinv):
         "metric": "held-out solve time, safe alpha / learned alpha (QHPI19, mixed, equal accuracy)",
         "value": safe_ms / learned_ms, "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 1,
         "higher_is_better": True, "dtype": "bf16-split/f32-acc + exact-slice f64", "data": "synthetic",
-        "config": {"workload": "MLP 32-64-64-1 trained on %d generator-family matrices (32..256); held-out "
-                               "1024^2 and 2048x1024, kappa = 10^U[1,5]" % args.train_count},
+        "config": {"workload": "MLP 32-64-64-1 trained on %d generator-family matrices (32..512, drawn on the GPU "
+                               "in groups of one shape); held-out 1024^2, 2048x1024, 2048^2, 4096^2, 4096x2048 with "
+                               "log-uniform / geometric / clustered spectra, kappa = 10^U[1,5]" % args.train_count},
         "training": {"samples": args.train_count, "final_loss": loss, "data_s": t_data, "train_s": t_train},
         "iters": {"safe": sum(r["safe"]["iters"] for r in rows), "learned": sum(r["learned"]["iters"] for r in rows)},
         "rows": rows,
@@ -908,7 +909,7 @@ def main():
                          "and held-out evaluation; hyper: factorized vs unfactorized hyperpower (Example 3); "
                          "cur: CUR image completion (Sec. 5.1); filter: Lorenz signal filtering (Sec. 5.2); "
                          "krylov: QSAI-preconditioned global Krylov solvers (Sec. 3.5)")
-    ap.add_argument("--train-count", type=int, default=1500, help="--workload learned: training matrices")
+    ap.add_argument("--train-count", type=int, default=20000, help="--workload learned: training matrices")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
     args = ap.parse_args()

@@ -100,6 +100,36 @@ __device__ __forceinline__ void slice_df(bf16* base, long lstride, int S, dfv v,
   base[0] = __float2bfloat16_rn(ldexpf((float)F, -7));
 }
 
+// The same for 8 consecutive entries of one row (one exponent), written as
+// 16-byte stores per slice plane (base 16-byte aligned).
+__device__ __forceinline__ void slice_df8(bf16* base, long lstride, int S, const dfv* v, int e) {
+  const int sh = 7 * S - e;
+  long long F[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) F[q] = ffixed(v[q].hi, sh) + ffixed(v[q].lo, sh);
+  for (int l = S - 1; l >= 0; l--) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      float x[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (l > 0) {
+          int d = (int)(F[q + h] & 127);
+          if (d >= 64) d -= 128;
+          F[q + h] = (F[q + h] - d) >> 7;
+          x[h] = ldexpf((float)d, -7 * (l + 1));
+        } else {
+          x[h] = ldexpf((float)F[q + h], -7);
+        }
+      }
+      pk[q >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
+    }
+    *reinterpret_cast<uint4*>(base + l * lstride) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
 __device__ __forceinline__ void store_rows64(long long* __restrict__ dst, long ld, int nrow,
                                              const long long* __restrict__ st) {
 #pragma unroll 4
@@ -137,23 +167,40 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
     for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
     if (lane == 0) ts->eP[i] = ex;
   }
-  for (int j = tid; j < N; j += TPB) {
-    int ex = -100000;
-    for (int k = 0; k < K; k++)
+  {
+    // columns of Q: lanes walk 32 consecutive columns, warps split the rows;
+    // per-warp maxima meet in the shared staging area
+    int* part = reinterpret_cast<int*>(smem + TSTAGES * TSTAGE);  // [8][MAXD]
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      const int j = j0 + lane;
+      int ex = -100000;
+      if (j < N)
+        for (int k = warp; k < K; k += TPB / 32)
 #pragma unroll
-      for (int c = 0; c < 4; c++) ex = max(ex, fexp(Q.at(c, k, j).hi));
-    ts->eQ[j] = ex;
+          for (int c = 0; c < 4; c++) ex = max(ex, fexp(Q.at(c, k, j).hi));
+      part[warp * MAXD + j] = ex;  // j < j0 + 32 <= MAXD
+    }
+    __syncthreads();
+    for (int j = tid; j < N; j += TPB) {
+      int ex = part[j];
+#pragma unroll
+      for (int w = 1; w < TPB / 32; w++) ex = max(ex, part[w * MAXD + j]);
+      ts->eQ[j] = ex;
+    }
   }
   __syncthreads();
   // ---- 2. exact slices (zero padded in K to a multiple of TBK) ----
   const int KP = (K + TBK - 1) / TBK * TBK;
   const long lstride = 4L * MAXD * TKP;
-  for (long t = tid; t < (long)M * KP; t += TPB) {
-    const int i = (int)(t / KP), k = (int)(t % KP);
+  const int KP8 = KP / 8;
+  for (long t = tid; t < (long)M * KP8; t += TPB) {
+    const int i = (int)(t / KP8), k = (int)(t % KP8) * 8;
 #pragma unroll 1
     for (int c = 0; c < 4; c++) {
-      const dfv v = k < K ? P.at(c, i, k) : dfv{0.f, 0.f};
-      slice_df(sa + ((long)c * MAXD + i) * TKP + k, lstride, S, v, ts->eP[i]);
+      dfv v[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) v[q] = k + q < K ? P.at(c, i, k + q) : dfv{0.f, 0.f};
+      slice_df8(sa + ((long)c * MAXD + i) * TKP + k, lstride, S, v, ts->eP[i]);
     }
   }
   {
@@ -169,13 +216,18 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
           for (int c = 0; c < 4; c++) st[c][ty + 8 * q][tx] = (k < K && j < N) ? Q.at(c, k, j) : dfv{0.f, 0.f};
         }
         __syncthreads();
-#pragma unroll 1
-        for (int q = 0; q < 4; q++) {
-          const int j = j0 + ty + 8 * q, k = k0 + tx;
+        {
+          // 32 columns x 4 groups of 8 k: thread (jl, g) = (tid / 4 % 32, tid % 4), one plane pass each
+          const int jl = (tid >> 2) & 31, g = tid & 3, j = j0 + jl, k = k0 + 8 * g;
           if (j < N)
 #pragma unroll 1
-            for (int c = 0; c < 4; c++)
-              slice_df(sb + ((long)c * MAXD + j) * TKP + k, lstride, S, st[c][tx][ty + 8 * q], ts->eQ[j]);
+            for (int c = 0; c < 4; c++) {
+              if ((tid >> 7) != (c & 1)) continue;  // threads 0..127 planes 0, 2; 128..255 planes 1, 3
+              dfv v[8];
+#pragma unroll
+              for (int q = 0; q < 8; q++) v[q] = st[c][8 * g + q][jl];
+              slice_df8(sb + ((long)c * MAXD + j) * TKP + k, lstride, S, v, ts->eQ[j]);
+            }
         }
         __syncthreads();
       }
@@ -255,11 +307,11 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
                   }
                   fence_after();
                   uint8_t* sp = smem + (size_t)st * TSTAGE;
-                  const uint32_t a_base = smem_u32(sp), b_base = smem_u32(sp + 4 * TA_PLANE);
+                  const uint64_t ad0 = smem_desc_sw<TSWB>(smem_u32(sp)),
+                                 bd0 = smem_desc_sw<TSWB>(smem_u32(sp + 4 * TA_PLANE));
 #pragma unroll
                   for (int kk = 0; kk < TBK / 16; kk++)
-                    qmma_k16<TSWB>(ts->tmem, TBN, a_base + kk * 32, TA_PLANE, b_base + kk * 32, TB_PLANE, TIDESC,
-                                   first && kk == 0);
+                    qmma_k16<TA_PLANE, TB_PLANE>(ts->tmem, TBN, ad0 + kk * 2, bd0 + kk * 2, TIDESC, first && kk == 0);
                   first = false;
                   mma_commit(smem_u32(&ts->empty[st]));
                 }

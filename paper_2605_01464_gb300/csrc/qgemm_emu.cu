@@ -197,11 +197,11 @@ __global__ void __launch_bounds__(ETHREADS, 1)
               }
               fence_after();
               uint8_t* sp = smem + (size_t)st * ESTAGE;
-              const uint32_t a_base = smem_u32(sp), b_base = smem_u32(sp + 4 * EA_PLANE);
+              const uint64_t ad0 = smem_desc_sw<ESWB>(smem_u32(sp)),
+                             bd0 = smem_desc_sw<ESWB>(smem_u32(sp + 4 * EA_PLANE));
 #pragma unroll
               for (int kk = 0; kk < EBK / 16; kk++)
-                qmma_k16<ESWB>(dacc, EBN, a_base + kk * 32, EA_PLANE, b_base + kk * 32, EB_PLANE, EIDESC,
-                               first && kk == 0);
+                qmma_k16<EA_PLANE, EB_PLANE>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
               first = false;
               mma_commit(smem_u32(&bar_empty[st]));
             }

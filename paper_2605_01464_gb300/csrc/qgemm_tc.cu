@@ -252,14 +252,14 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
         if (!mbar_wait(smem_u32(&bar_full[s]), (u / STAGES) & 1, &abort_flag, P.err, 2)) break;
         fence_after();
         uint8_t* st = smem + (size_t)s * STAGE_BYTES;
-        const uint32_t a_base = smem_u32(st), b_base = smem_u32(st + 4 * A_PLANE_BYTES);
+        const uint64_t ad0 = smem_desc_sw<C::SWB>(smem_u32(st)),
+                       bd0 = smem_desc_sw<C::SWB>(smem_u32(st + 4 * A_PLANE_BYTES));
         const int pr = u % P.npairs;
         const uint32_t dacc = tmem + (uint32_t)(P.pacc[pr] * ACC_COLS);
         const bool fresh = u < P.npairs && P.pfirst[pr];  // first K block of this accumulator
 #pragma unroll
         for (int kk = 0; kk < BK / 16; kk++)
-          qmma_k16<C::SWB>(dacc, BN, a_base + kk * 32, A_PLANE_BYTES, b_base + kk * 32, B_PLANE_BYTES, IDESC,
-                           fresh && kk == 0);
+          qmma_k16<A_PLANE_BYTES, B_PLANE_BYTES>(dacc, BN, ad0 + kk * 2, bd0 + kk * 2, IDESC, fresh && kk == 0);
         mma_commit(smem_u32(&bar_empty[s]));
         if (u == nunits - 1) mma_commit(smem_u32(&bar_acc));
       }

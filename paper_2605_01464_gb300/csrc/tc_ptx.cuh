@@ -88,19 +88,24 @@ __host__ __device__ constexpr bool qsign_neg(int r, int c) {
 }
 // The 16 signed (r, c) MMAs of one K = 16 step: A plane r times B plane
 // r xor c into component c's accumulator (d_tmem + c * ncols), the sign from
-// the instruction descriptor's negate-A bit (bit 13).
-template <int SWB>
-__device__ __forceinline__ void qmma_k16(uint32_t d_tmem, uint32_t ncols, uint32_t a_base, uint32_t a_plane,
-                                         uint32_t b_base, uint32_t b_plane, uint32_t idesc, bool fresh) {
+// the instruction descriptor's negate-A bit (bit 13).  ad0 / bd0 are the
+// descriptors of the step's first A and B planes; a plane's descriptor is
+// ad0 plus its byte offset / 16 (the address field is the low 14 bits and
+// every operand lies below 256 KB, so the add never carries out of it).
+// The issuing thread feeds the tensor core one MMA per few dozen cycles, so
+// the loop is kept to one add per descriptor.
+template <uint32_t A_PLANE, uint32_t B_PLANE>
+__device__ __forceinline__ void qmma_k16(uint32_t d_tmem, uint32_t ncols, uint64_t ad0, uint64_t bd0, uint32_t idesc,
+                                         bool fresh) {
   constexpr uint32_t NEG_A = 1u << 13;
 #pragma unroll
   for (int r = 0; r < 4; r++) {
-    const uint64_t ad = smem_desc_sw<SWB>(a_base + r * a_plane);
+    const uint64_t ad = ad0 + ((r * A_PLANE) >> 4);
     const uint32_t acc = (fresh && r == 0) ? 0u : 1u;
 #pragma unroll
     for (int c = 0; c < 4; c++)
-      mma_bf16(d_tmem + c * ncols, ad, smem_desc_sw<SWB>(b_base + (r ^ c) * b_plane),
-               qsign_neg(r, c) ? idesc | NEG_A : idesc, acc);
+      mma_bf16(d_tmem + c * ncols, ad, bd0 + (((r ^ c) * B_PLANE) >> 4), qsign_neg(r, c) ? idesc | NEG_A : idesc,
+               acc);
   }
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {

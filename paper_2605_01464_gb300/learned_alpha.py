@@ -118,3 +118,86 @@ def compare_iterations(ctx, mats, method="qhpi19", tol=1e-12, to_device=None):
                     l["precision"]))
     ctx.configure(alpha="safe")
     return out
+
+
+# ------------------------------------------------- GPU batch generator (training sets)
+# Training sets of tens of thousands of matrices are drawn in groups of one
+# shape on the GPU (torch's seeded generator, complex64 chi form): Haar-like
+# orthonormal factors by CholeskyQR2, A = U diag(sigma) V^H.  Their spectra
+# are exact to FP32 (about 1e-6 relative), ample for labels whose target is
+# alpha to a few per cent; the held-out matrices keep the seeded FP64
+# generators above.
+
+def _chi_t(torch, Q):
+    """(b, 4, m, n) real planes -> (b, 2m, 2n) complex chi form."""
+    s, x, y, z = Q.unbind(1)
+    b, m, n = s.shape
+    C = torch.empty((b, 2 * m, 2 * n), dtype=torch.complex64, device=Q.device)
+    C[:, 0::2, 0::2] = torch.complex(s, x)
+    C[:, 0::2, 1::2] = torch.complex(y, z)
+    C[:, 1::2, 0::2] = torch.complex(-y, z)
+    C[:, 1::2, 1::2] = torch.complex(s, -x)
+    return C
+
+
+def _unchi_t(torch, C):
+    a, b = C[:, 0::2, 0::2], C[:, 0::2, 1::2]
+    return torch.stack([a.real, a.imag, b.real, b.imag], dim=1)
+
+
+def _orth_t(torch, b, m, r, gen):
+    C = _chi_t(torch, torch.randn((b, 4, m, r), generator=gen, device=gen.device, dtype=torch.float32))
+    for _ in range(2):
+        H = C.mH @ C
+        H = 0.5 * (H + H.mH)
+        L = torch.linalg.cholesky(H)
+        C = torch.linalg.solve_triangular(L, C.mH, upper=False).mH
+    return C
+
+
+def sample_group_gpu(torch, family, m, n, count, gen):
+    """`count` matrices of one shape: ((count, 4, m, n) float64 planes on the
+    GPU, list of nonzero singular values per matrix, descending)."""
+    import numpy as np
+    k = min(m, n)
+    if family == "dense":
+        A = torch.randn((count, 4, m, n), generator=gen, device=gen.device, dtype=torch.float32)
+        C = _chi_t(torch, A)
+        G = C.mH @ C if n <= m else C @ C.mH
+        ev = torch.linalg.eigvalsh(0.5 * (G + G.mH)).flip(-1)[:, ::2].clamp_min(0).sqrt()
+        return A.double(), [e.cpu().numpy().astype(np.float64) for e in ev]
+    rng = np.random.default_rng(int(torch.randint(0, 2 ** 31 - 1, (1,), generator=gen, device=gen.device).item()))
+    r = k if family != "geometric" else int(rng.integers(max(1, k // 4), max(2, k // 2) + 1))
+    sig = np.stack([_spectrum(family, r, rng) * 10.0 ** rng.uniform(-2, 2) for _ in range(count)])
+    U = _orth_t(torch, count, m, r, gen)
+    V = _orth_t(torch, count, n, r, gen)
+    s2 = torch.as_tensor(np.repeat(sig, 2, axis=1), dtype=torch.float32, device=gen.device)
+    A = _unchi_t(torch, (U * s2[:, None, :].to(torch.complex64)) @ V.mH)
+    return A.double(), list(sig)
+
+
+def make_dataset_gpu(ctx, torch, count, lo, hi, seed, families=TRAIN_FAMILIES, group=32):
+    """Features (count x 32), labels (count) and per-sample (family, m, n,
+    theta_1) for `count` matrices in groups of one shape; features by the
+    library's kernels, labels as make_dataset."""
+    import numpy as np
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    rng = np.random.default_rng(seed)
+    feats, labels, meta = [], [], []
+    g = 0
+    while len(feats) < count:
+        fam = families[g % len(families)]
+        g += 1
+        m = int(rng.integers(lo, hi + 1))
+        n = int(rng.integers(lo, hi + 1)) if rng.uniform() < 0.5 else m
+        if fam == "dense":  # spectra from a Gram eigensolve: kept to the smaller sizes
+            m, n = min(m, 256), min(n, 256)
+        cnt = min(group, count - len(feats))
+        A, sigs = sample_group_gpu(torch, fam, m, n, cnt, gen)
+        for b in range(cnt):
+            f, theta1 = ctx.alpha_features(A[b].contiguous())
+            feats.append(f)
+            labels.append(math.log(optimal_alpha(sigs[b]) * theta1 / MARGIN))
+            meta.append((fam, m, n, theta1))
+    return np.array(feats, dtype=np.float32), np.array(labels, dtype=np.float32), meta

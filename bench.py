@@ -804,8 +804,10 @@ def bench_learned(args, torch, qpinv):
         ctx.configure(precision="mixed", alpha="learned")
         msl, infol = _timed_solve(ctx, torch, A, "qhpi19", args.tol)
         ctx.configure(alpha="safe")
-    safe_ms = sum(r["safe"]["ms"] for r in rows)
-    learned_ms = sum(r["learned"]["ms"] for r in rows)
+    # equal accuracy: rows where both solves reach the stated tolerance
+    eq = [r for r in rows if r["safe"]["E1_rel"] <= 1e-10 and r["learned"]["E1_rel"] <= 1e-10]
+    safe_ms = sum(r["safe"]["ms"] for r in eq)
+    learned_ms = sum(r["learned"]["ms"] for r in eq)
     print(json.dumps({
         "metric": "held-out solve time, safe alpha / learned alpha (QHPI19, mixed, equal accuracy)",
         "value": safe_ms / learned_ms, "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -815,6 +817,7 @@ def bench_learned(args, torch, qpinv):
                                "log-uniform / geometric / clustered spectra, kappa = 10^U[1,5]" % args.train_count},
         "training": {"samples": args.train_count, "final_loss": loss, "data_s": t_data, "train_s": t_train},
         "iters": {"safe": sum(r["safe"]["iters"] for r in rows), "learned": sum(r["learned"]["iters"] for r in rows)},
+        "equal_accuracy_rows": len(eq), "rows_total": len(rows),
         "rows": rows,
         "vs_fp64_fixed_alpha": {"matrix": "logspaced 1024^2 (seed 700)", "fp64_safe_ms": ms64,
                                 "fp64_E1_rel": info64["E_rel"][0], "mixed_learned_ms": msl,

@@ -147,7 +147,7 @@ typedef struct {
   int alpha_source;  /* QPINV_ALPHA_* actually used */
   int side;          /* QPINV_SIDE_RIGHT or QPINV_SIDE_LEFT actually used */
   int precision;     /* precision that produced X: a MIXED solve with penrose = 1 that diverges or
-                        whose E_rel[0] exceeds 1e-6 (typically rank-deficient A) is repeated in
+                        whose E_rel[0] exceeds 1e-9 (typically rank-deficient A) is repeated in
                         QPINV_PREC_EMU and reports EMU here, gemms then counting both attempts;
                         batched solves report QPINV_PREC_DF32 */
   double delta;      /* ||X_{j+1} - X_j||_F of the last computed step */

@@ -37,7 +37,8 @@ namespace {
 
 constexpr int MAXD = 256;
 constexpr int NBUF = 22;  // workspace matrices per slot
-constexpr int TPB = 256;
+constexpr int TPB = 256;      // threads of the CUDA-core engine's CTA
+constexpr int TPB_MAX = 352;  // largest CTA of any engine (the per-matrix code uses blockDim.x)
 // CTA GEMM: a 16 x 16 thread grid, each thread RM x RN outputs 16 apart, so
 // the CTA tile is 16 RM x 16 RN quaternion entries; BK = K step.  The tile
 // shape is a template parameter of the kernel, chosen per batch by the
@@ -177,7 +178,7 @@ cudaError_t batched_tc_maps(char* tc_ws, int slots, CUtensorMap* host_maps, void
 namespace {
 
 struct Shared {
-  double red[TPB / 32][2];
+  double red[TPB_MAX / 32][2];
   double bc[4];
 };
 // operand tiles of the CUDA-core CTA GEMM
@@ -192,7 +193,7 @@ __device__ double block_sum(double v, Shared& sh, int slot) {
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5][slot] = v;
   __syncthreads();
   double r = 0.0;
-  for (int w = 0; w < TPB / 32; w++) r += sh.red[w][slot];
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) r += sh.red[w][slot];
   __syncthreads();
   return r;  // valid in every thread
 }
@@ -308,7 +309,7 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
 // out = ca * X + sum ct * aux + diag I  (elementwise; no product).
 __device__ void cta_axpy(const DM& X, const DM& out, dfv ca, const DM* aux, dfv ct, dfv diag) {
   const long total = (long)X.rows * X.cols;
-  for (long t = threadIdx.x; t < total; t += TPB) {
+  for (long t = threadIdx.x; t < total; t += blockDim.x) {
     const int i = (int)(t / X.cols), j = (int)(t % X.cols);
     for (int c = 0; c < 4; c++) {
       dfv v = df_mul(ca, X.at(c, i, j));
@@ -324,7 +325,7 @@ __device__ void cta_axpy(const DM& X, const DM& out, dfv ca, const DM* aux, dfv 
 __device__ double cta_antiherm2(const DM& M, Shared& sh) {
   float s = 0.f;
   const long total = (long)M.rows * M.cols;
-  for (long t = threadIdx.x; t < total; t += TPB) {
+  for (long t = threadIdx.x; t < total; t += blockDim.x) {
     const int i = (int)(t / M.cols), j = (int)(t % M.cols);
     for (int c = 0; c < 4; c++) {
       const dfv mji = M.at(c, j, i), mij = M.at(c, i, j);
@@ -338,7 +339,7 @@ __device__ double cta_antiherm2(const DM& M, Shared& sh) {
 __device__ double cta_fro2(const DM& M, Shared& sh) {
   float s = 0.f;
   const long total = 4L * M.rows * M.cols;
-  for (long t = threadIdx.x; t < total; t += TPB) s += M.p[t].hi * M.p[t].hi;
+  for (long t = threadIdx.x; t < total; t += blockDim.x) s += M.p[t].hi * M.p[t].hi;
   return block_sum((double)s, sh, 0);
 }
 
@@ -566,7 +567,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
     // load A; row / column sums of moduli; ||A||_F^2
     float fro = 0.f;
     int bad = 0;
-    for (long t = threadIdx.x; t < (long)it.m * it.n; t += TPB) {
+    for (long t = threadIdx.x; t < (long)it.m * it.n; t += blockDim.x) {
       const int i = (int)(t / it.n), j = (int)(t % it.n);
       for (int q = 0; q < 4; q++) {
         const double a = it.A[q][(long)i * it.lda + j];
@@ -579,7 +580,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
     const double a_f2 = block_sum((double)fro, sh, 0);
     const double nbad = block_sum((double)bad, sh, 1);
     float rmax = 0.f, cmax = 0.f;
-    for (int i = threadIdx.x; i < it.m; i += TPB) {
+    for (int i = threadIdx.x; i < it.m; i += blockDim.x) {
       float r = 0.f;
       for (int j = 0; j < it.n; j++) {
         float q2 = 0.f;
@@ -588,7 +589,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
       }
       rmax = fmaxf(rmax, r);
     }
-    for (int j = threadIdx.x; j < it.n; j += TPB) {
+    for (int j = threadIdx.x; j < it.n; j += blockDim.x) {
       float r = 0.f;
       for (int i = 0; i < it.m; i++) {
         float q2 = 0.f;
@@ -607,7 +608,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
     }
     __syncthreads();
     double nrm_inf = 0, nrm_1 = 0;
-    for (int w = 0; w < TPB / 32; w++) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
       nrm_inf = fmax(nrm_inf, sh.red[w][0]);
       nrm_1 = fmax(nrm_1, sh.red[w][1]);
     }
@@ -627,7 +628,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
     } else {
       // X_0 = alpha A^H
       const dfv al = df_from(alpha);
-      for (long t = threadIdx.x; t < (long)it.m * it.n; t += TPB) {
+      for (long t = threadIdx.x; t < (long)it.m * it.n; t += blockDim.x) {
         const int i = (int)(t / it.n), j = (int)(t % it.n);
         for (int q = 0; q < 4; q++) {
           const dfv a = S.A.at(q, i, j);
@@ -693,7 +694,7 @@ __device__ void solve_item(const BatchParams& P, Ctx& c, G& g, int b) {
       const double nr[4] = {sqrt(a_f2), sqrt(cta_fro2(Xf, sh)), sqrt(cta_fro2(Rr, sh)), sqrt(cta_fro2(Rl, sh))};
       for (int q = 0; q < 4; q++) res.E_rel[q] = nr[q] > 0 ? res.E[q] / nr[q] : res.E[q];
       // write X
-      for (long t = threadIdx.x; t < (long)it.n * it.m; t += TPB) {
+      for (long t = threadIdx.x; t < (long)it.n * it.m; t += blockDim.x) {
         const int i = (int)(t / it.m), j = (int)(t % it.m);
         for (int q = 0; q < 4; q++) it.X[q][(long)i * it.ldx + j] = df_to(Xf.at(q, i, j));
       }

@@ -41,18 +41,22 @@ namespace qp {
 namespace {
 
 constexpr int TBM = 128, TBN = 64, TBK = 32, TSWB = 64;
-constexpr int TSTAGES = 3;
+constexpr int TSTAGES = 4;
 constexpr int TA_PLANE = TBM * TBK * 2;            // 8 KB
 constexpr int TB_PLANE = TBN * TBK * 2;            // 4 KB
 constexpr int TSTAGE = 4 * (TA_PLANE + TB_PLANE);  // 48 KB
-constexpr int TSTAGING = 4 * 32 * 33 * 8;          // epilogue transpose / slicing transpose
-constexpr int TSMEM = TSTAGES * TSTAGE + TSTAGING + 1024;
+constexpr int TSTAGING = 4 * 32 * 33 * 8;          // slicing transpose, aliased with stage 0
+constexpr int TSMEM = TSTAGES * TSTAGE + 1024;
+static_assert(TSTAGING <= TSTAGE, "the slicing staging fits in one idle stage");
 constexpr int TKP = MAXD;   // K pitch of the slice scratch (elements)
 constexpr int TMAXS = 8;    // slice planes reserved per operand
 constexpr uint32_t TIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
                             ((uint32_t)(TBM >> 4) << 24);
 static_assert(TSMEM + 4096 <= 227 * 1024, "shared memory per CTA");
-static_assert(TPB == 256, "warp roles assume 8 warps");
+constexpr int TMMA_WARPS = 2;               // MMA issuers: components 0-1 and 2-3
+constexpr int TEPI0 = 1 + TMMA_WARPS;        // first of the 8 epilogue warps (two per TMEM lane quarter)
+constexpr int TTHREADS = 32 * (TEPI0 + 8);   // 352
+static_assert(TTHREADS <= TPB_MAX, "shared per-matrix state sized for the block");
 
 // slice scratch per slot: A-form and B-form [TMAXS][4][MAXD][TKP] BF16, then
 // the int64 accumulator [4][MAXD][MAXD]
@@ -61,7 +65,7 @@ constexpr size_t TC_C64_BYTES = (size_t)4 * MAXD * MAXD * sizeof(long long);
 constexpr size_t TC_SLOT_BYTES = 2 * TC_SLICE_BYTES + TC_C64_BYTES;
 
 struct TcShared {
-  uint64_t full[TSTAGES], empty[TSTAGES], acc_full, acc_empty;
+  uint64_t full[TSTAGES], empty[TSTAGES], acc_full[2], acc_empty[2];
   uint32_t tmem;
   int abort_flag;
   int u, w, issued;  // stage uses and chunks so far (mbarrier phases); loads issued
@@ -130,18 +134,11 @@ __device__ __forceinline__ void slice_df8(bf16* base, long lstride, int S, const
   }
 }
 
-__device__ __forceinline__ void store_rows64(long long* __restrict__ dst, long ld, int nrow,
-                                             const long long* __restrict__ st) {
-#pragma unroll 4
-  for (int r = 0; r < 32; r++)
-    if (r < nrow) dst[(long)r * ld] = st[r * 33];
-}
-
 // The tensor-core CTA GEMM: C = epilogue(P Q) for df matrices (P M x K, Q K x N).
 struct TcGemm {
   Shared* sh;
   TcShared* ts;
-  uint8_t* smem;  // 1024-aligned: TSTAGES stages, then TSTAGING bytes of staging
+  uint8_t* smem;  // 1024-aligned: TSTAGES stages (the first doubles as staging outside the tensor-core phase)
   const CUtensorMap* mapA;
   const CUtensorMap* mapB;
   bf16* sa;  // A-form slices [TMAXS][4][MAXD][TKP]
@@ -151,15 +148,20 @@ struct TcGemm {
   int* err;
 
   __device__ void operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms);
+  // the phases, each its own function (own register allocation)
+  __device__ void exponents(const DM& P, const DM& Q);
+  __device__ void slices(const DM& P, const DM& Q);
+  __device__ void products(int M, int N, int K, int shift, int u0, int w0);
+  __device__ void combine(int M, int N, int K, int shift, const DM& C, const Epi& e, double* norms);
 };
 
-__device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms) {
-  const int M = P.rows, K = P.cols, N = Q.cols;
+__device__ __noinline__ void TcGemm::exponents(const DM& P, const DM& Q) {
+  const int K = P.cols, M = P.rows, N = Q.cols;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int u0 = ts->u, w0 = ts->w;  // read before this product's first barrier
-  const bool aborted = ts->abort_flag != 0;
+  (void)warp;
+  (void)lane;
   // ---- 1. exponents ----
-  for (int i = warp; i < M; i += TPB / 32) {
+  for (int i = warp; i < M; i += TTHREADS / 32) {
     int ex = -100000;
     for (int k = lane; k < K; k += 32)
 #pragma unroll
@@ -170,53 +172,69 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
   {
     // columns of Q: lanes walk 32 consecutive columns, warps split the rows;
     // per-warp maxima meet in the shared staging area
-    int* part = reinterpret_cast<int*>(smem + TSTAGES * TSTAGE);  // [8][MAXD]
+    int* part = reinterpret_cast<int*>(smem);  // [warps][MAXD], in the idle stage ring
     for (int j0 = 0; j0 < N; j0 += 32) {
       const int j = j0 + lane;
       int ex = -100000;
       if (j < N)
-        for (int k = warp; k < K; k += TPB / 32)
+        for (int k = warp; k < K; k += TTHREADS / 32)
 #pragma unroll
           for (int c = 0; c < 4; c++) ex = max(ex, fexp(Q.at(c, k, j).hi));
       part[warp * MAXD + j] = ex;  // j < j0 + 32 <= MAXD
     }
     __syncthreads();
-    for (int j = tid; j < N; j += TPB) {
+    for (int j = tid; j < N; j += TTHREADS) {
       int ex = part[j];
 #pragma unroll
-      for (int w = 1; w < TPB / 32; w++) ex = max(ex, part[w * MAXD + j]);
+      for (int w = 1; w < TTHREADS / 32; w++) ex = max(ex, part[w * MAXD + j]);
       ts->eQ[j] = ex;
     }
   }
   __syncthreads();
+}
+
+__device__ __noinline__ void TcGemm::slices(const DM& P, const DM& Q) {
+  const int K = P.cols, M = P.rows, N = Q.cols;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  (void)warp;
+  (void)lane;
   // ---- 2. exact slices (zero padded in K to a multiple of TBK) ----
   const int KP = (K + TBK - 1) / TBK * TBK;
   const long lstride = 4L * MAXD * TKP;
   const int KP8 = KP / 8;
-  for (long t = tid; t < (long)M * KP8; t += TPB) {
+  for (long t = tid; t < (long)M * KP8; t += TTHREADS) {
     const int i = (int)(t / KP8), k = (int)(t % KP8) * 8;
-#pragma unroll 1
-    for (int c = 0; c < 4; c++) {
-      dfv v[8];
+    // two planes' 16 loads in flight before any is used (the slot's
+    // matrices live in L2 / HBM and one CTA per SM has few warps to hide it)
+    const int e = ts->eP[i];
 #pragma unroll
-      for (int q = 0; q < 8; q++) v[q] = k + q < K ? P.at(c, i, k + q) : dfv{0.f, 0.f};
-      slice_df8(sa + ((long)c * MAXD + i) * TKP + k, lstride, S, v, ts->eP[i]);
+    for (int c0 = 0; c0 < 4; c0 += 2) {
+      dfv v[2][8];
+#pragma unroll
+      for (int c = 0; c < 2; c++)
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[c][q] = k + q < K ? P.at(c0 + c, i, k + q) : dfv{0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 2; c++) slice_df8(sa + ((long)(c0 + c) * MAXD + i) * TKP + k, lstride, S, v[c], e);
     }
   }
   {
-    // Q transposed through shared memory: reads along j, writes along k
-    dfv(*st)[32][33] = reinterpret_cast<dfv(*)[32][33]>(smem + TSTAGES * TSTAGE);
+    // Q transposed through shared memory: reads along j, writes along k (the
+    // first 256 threads: 8 rows of 32 per pass)
+    dfv(*st)[32][33] = reinterpret_cast<dfv(*)[32][33]>(smem);  // the idle stage ring
     const int tx = tid & 31, ty = tid >> 5;
     for (int k0 = 0; k0 < KP; k0 += 32)
       for (int j0 = 0; j0 < N; j0 += 32) {
+        if (tid < 256) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int k = k0 + ty + 8 * q, j = j0 + tx;
+          for (int q = 0; q < 4; q++) {
+            const int k = k0 + ty + 8 * q, j = j0 + tx;
 #pragma unroll
-          for (int c = 0; c < 4; c++) st[c][ty + 8 * q][tx] = (k < K && j < N) ? Q.at(c, k, j) : dfv{0.f, 0.f};
+            for (int c = 0; c < 4; c++) st[c][ty + 8 * q][tx] = (k < K && j < N) ? Q.at(c, k, j) : dfv{0.f, 0.f};
+          }
         }
         __syncthreads();
-        {
+        if (tid < 256) {
           // 32 columns x 4 groups of 8 k: thread (jl, g) = (tid / 4 % 32, tid % 4), one plane pass each
           const int jl = (tid >> 2) & 31, g = tid & 3, j = j0 + jl, k = k0 + 8 * g;
           if (j < N)
@@ -236,6 +254,13 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
 
+}
+
+__device__ __noinline__ void TcGemm::products(int M, int N, int K, int shift, int u0, int w0) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  (void)warp;
+  (void)lane;
+  const bool aborted = false;
   // ---- 3. tensor-core phase ----
   int kc[TMAXS];
 #pragma unroll
@@ -248,11 +273,9 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
     kc[d] = c0 < K ? c0 : K;
   }
   const int Mt = (M + TBM - 1) / TBM, Nt = (N + TBN - 1) / TBN;
-  int lg = 0;
-  while ((1L << lg) < 4L * K) lg++;
-  const int shift = 61 - lg;  // |sum| < 4K in normalized units
   if (!aborted) {
     if (warp == 0) {
+      // ---------------- TMA producer ----------------
       if (lane == 0) {
         int u = u0;
         bool ok = true;
@@ -284,18 +307,22 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
         }
         if (ok) ts->u = u;
       }
-    } else if (warp == 1) {
+    } else if (warp < TEPI0) {
+      // ---------------- MMA issuers: warp 1 components 0, 1; warp 2 components 2, 3 ----------------
       if (lane == 0) {
+        const bool lo = warp == 1;
         int u = u0, w = w0;
         bool ok = true;
         for (int tile = 0; tile < Mt * Nt && ok; tile++) {
           for (int d = S - 1; d >= 0 && ok; d--) {
             for (int k0 = 0; k0 < K && ok; k0 += kc[d], w++) {
-              if (w > 0 && !mbar_wait(smem_u32(&ts->acc_empty), (w - 1) & 1, &ts->abort_flag, err, 22)) {
+              const int b = w & 1;  // FP32 buffer of this chunk, free once chunk w - 2 was drained
+              if (w >= 2 && !mbar_wait(smem_u32(&ts->acc_empty[b]), ((w >> 1) - 1) & 1, &ts->abort_flag, err, 22)) {
                 ok = false;
                 break;
               }
               fence_after();
+              const uint32_t dacc = ts->tmem + b * 256;
               const int kb0 = k0 / TBK, kb1 = (min(K, k0 + kc[d]) + TBK - 1) / TBK;
               bool first = true;
               for (int kb = kb0; kb < kb1 && ok; kb++) {
@@ -310,35 +337,45 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
                   const uint64_t ad0 = smem_desc_sw<TSWB>(smem_u32(sp)),
                                  bd0 = smem_desc_sw<TSWB>(smem_u32(sp + 4 * TA_PLANE));
 #pragma unroll
-                  for (int kk = 0; kk < TBK / 16; kk++)
-                    qmma_k16<TA_PLANE, TB_PLANE>(ts->tmem, TBN, ad0 + kk * 2, bd0 + kk * 2, TIDESC, first && kk == 0);
+                  for (int kk = 0; kk < TBK / 16; kk++) {
+                    if (lo)
+                      qmma_k16_half<TA_PLANE, TB_PLANE, 0>(dacc, TBN, ad0 + kk * 2, bd0 + kk * 2, TIDESC,
+                                                          first && kk == 0);
+                    else
+                      qmma_k16_half<TA_PLANE, TB_PLANE, 2>(dacc, TBN, ad0 + kk * 2, bd0 + kk * 2, TIDESC,
+                                                          first && kk == 0);
+                  }
                   first = false;
                   mma_commit(smem_u32(&ts->empty[st]));
                 }
               }
-              if (ok) mma_commit(smem_u32(&ts->acc_full));
+              if (ok) mma_commit(smem_u32(&ts->acc_full[b]));
             }
           }
         }
-        if (ok) ts->w = w;
+        if (ok && lo) ts->w = w;
       }
-    } else if (warp >= 4) {
-      // epilogue: FP32 chunk -> int32 level sum (TMEM) -> int64 (global) per level
-      const int quarter = warp & 3;
-      const uint32_t tb = ts->tmem + ((uint32_t)(quarter * 32) << 16);
-      long long* st64 = reinterpret_cast<long long*>(smem + TSTAGES * TSTAGE) + quarter * (32 * 33);
+    } else {
+      // ---------------- epilogue: FP32 chunk -> int32 level sums (registers) -> int64 (global) ----------------
+      // Warp e = warp - TEPI0 reads TMEM lane quarter warp % 4 and column half e / 4
+      // (components 2h, 2h + 1): 128 int32 level sums per thread.
+      const int e8 = warp - TEPI0, quarter = warp & 3, half = e8 >> 2;
+      const uint32_t tb0 = ts->tmem + ((uint32_t)(quarter * 32) << 16) + half * 128;
       int w = w0;
       bool ok = true;
+      int acc[128];
       for (int tile = 0; tile < Mt * Nt && ok; tile++) {
         const int m0 = (tile % Mt) * TBM, n0 = (tile / Mt) * TBN;
-        const int row0 = m0 + quarter * 32;
-        const int nrow = max(0, min(32, M - row0));
+        const int row = m0 + quarter * 32 + lane;
         for (int d = S - 1; d >= 0 && ok; d--) {
           const float scale = ldexpf(1.0f, 7 * (d + 2));
           const int shd = shift - 7 * (d + 2);
           for (int k0 = 0; k0 < K && ok; k0 += kc[d], w++) {
+            const int b = w & 1;
+            const uint32_t tb = tb0 + b * 256;
             int have = 1;
-            if (lane == 0) have = mbar_wait(smem_u32(&ts->acc_full), w & 1, &ts->abort_flag, err, 24) ? 1 : 0;
+            if (lane == 0)
+              have = mbar_wait(smem_u32(&ts->acc_full[b]), (w >> 1) & 1, &ts->abort_flag, err, 24) ? 1 : 0;
             have = __shfl_sync(0xffffffffu, have, 0);
             if (!have) {
               ok = false;
@@ -346,69 +383,89 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
             }
             fence_after();
             const bool first = k0 == 0;
-#pragma unroll 1
+#pragma unroll
             for (int p = 0; p < 8; p++) {
-              uint32_t f[32], a[32];
-              tmem_ld32u(tb + p * 32, f);
-              if (!first) tmem_ld32u(tb + 256 + p * 32, a);
+              uint32_t f[16];
+              tmem_ld16u(tb + p * 16, f);
               tmem_wait_ld();
 #pragma unroll
-              for (int t = 0; t < 32; t++) {
+              for (int t = 0; t < 16; t++) {
                 const int x = __float2int_rn(__uint_as_float(f[t]) * scale);
-                a[t] = first ? (uint32_t)x : (uint32_t)((int)a[t] + x);
+                acc[p * 16 + t] = first ? x : acc[p * 16 + t] + x;
               }
-              tmem_st32u(tb + 256 + p * 32, a);
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ts->acc_empty));
-            tmem_wait_st();
-            if (k0 + kc[d] < K) continue;
-            // level done: int64 accumulator (+)= int32 sum * 2^shd
-#pragma unroll 1
-            for (int p = 0; p < 8; p++) {
-              uint32_t a[32];
-              tmem_ld32u(tb + 256 + p * 32, a);
-              tmem_wait_ld();
+            if (lane == 0) mbar_arrive(smem_u32(&ts->acc_empty[b]));
+            if (k0 + kc[d] < K || row >= M) continue;
+            // level done: int64 accumulator (+)= int32 sum * 2^shd, this
+            // thread's row, components 2 half and 2 half + 1 (16-byte accesses;
+            // a column past N in a pair lands in the row's padding, never read)
 #pragma unroll
-              for (int t = 0; t < 32; t++) {
-                const long long x = (long long)(int)a[t];
-                st64[lane * 33 + t] = shd >= 0 ? (x << shd) : ((x + (1LL << (-shd - 1))) >> (-shd));
+            for (int p = 0; p < 4; p++) {
+              const int c = 2 * half + (p >> 1), j0 = n0 + (p & 1) * 32;
+              long long* dst = c64 + ((long)c * MAXD + row) * MAXD + j0;
+#pragma unroll
+              for (int t = 0; t < 32; t += 2) {
+                if (j0 + t >= N) break;
+                const long long x0 = (long long)acc[p * 32 + t], x1 = (long long)acc[p * 32 + t + 1];
+                longlong2 y;
+                y.x = shd >= 0 ? (x0 << shd) : ((x0 + (1LL << (-shd - 1))) >> (-shd));
+                y.y = shd >= 0 ? (x1 << shd) : ((x1 + (1LL << (-shd - 1))) >> (-shd));
+                longlong2* dp = reinterpret_cast<longlong2*>(dst + t);
+                if (d != S - 1) {
+                  const longlong2 g0 = *dp;
+                  y.x += g0.x;
+                  y.y += g0.y;
+                }
+                *dp = y;
               }
-              __syncwarp();
-              const int c = p >> 1, col = n0 + (p & 1) * 32 + lane;
-              if (col < N && nrow > 0) {
-                long long* dst = c64 + ((long)c * MAXD + row0) * MAXD + col;
-                if (d == S - 1) store_rows64(dst, MAXD, nrow, st64 + lane);
-                else rmw_rows64(dst, MAXD, nrow, st64 + lane);
-              }
-              __syncwarp();
             }
           }
         }
       }
     }
   }
+}
+
+__device__ __noinline__ void TcGemm::combine(int M, int N, int K, int shift, const DM& C, const Epi& e,
+                                             double* norms) {
+  (void)K;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  (void)warp;
+  (void)lane;
   fence_before();
   __syncthreads();
   fence_after();
 
   // ---- 4. int64 -> df, the pass's epilogue ----
   float nd = 0.f, nx = 0.f;
-  for (long t = tid; t < (long)M * N; t += TPB) {
+  for (long t = tid; t < (long)M * N; t += TTHREADS) {
     const int i = (int)(t / N), j = (int)(t % N);
     const int ex = ts->eP[i] + ts->eQ[j] - shift;
+    // loads first (the stores to C may alias an aux plane at this very entry only)
+    long long q[4];
+    dfv ax[3][4], rf[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) q[c] = c64[((long)c * MAXD + i) * MAXD + j];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) ax[a][c] = e.aux[a] ? e.aux[a]->at(c, i, j) : dfv{0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 4; c++) rf[c] = e.ref ? e.ref->at(c, i, j) : dfv{0.f, 0.f};
+#pragma unroll
     for (int c = 0; c < 4; c++) {
-      const long long q = c64[((long)c * MAXD + i) * MAXD + j];
-      const float h = __ll2float_rn(q);
-      const float l = __ll2float_rn(q - (long long)h);
+      const float h = __ll2float_rn(q[c]);
+      const float l = __ll2float_rn(q[c] - (long long)h);
       dfv v = df_quick(ldexpf(h, ex), ldexpf(l, ex));
       v = df_mul(e.ca, v);
+#pragma unroll
       for (int a = 0; a < 3; a++)
-        if (e.aux[a]) v = df_fma(e.ct[a], e.aux[a]->at(c, i, j), v);
+        if (e.aux[a]) v = df_fma(e.ct[a], ax[a][c], v);
       if (c == 0 && i == j) v = df_add(v, e.diag);
       if (e.ref) {
-        const dfv dd = df_add(v, df_neg(e.ref->at(c, i, j)));
+        const dfv dd = df_add(v, df_neg(rf[c]));
         nd += dd.hi * dd.hi;
         nx += v.hi * v.hi;
       }
@@ -423,7 +480,21 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
   }
 }
 
-__global__ void __launch_bounds__(TPB, 1) k_batched_tc(BatchParams P) {
+
+__device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms) {
+  const int M = P.rows, K = P.cols, N = Q.cols;
+  const int u0 = ts->u, w0 = ts->w;  // read before this product's first barrier
+  const bool aborted = ts->abort_flag != 0;
+  int lg = 0;
+  while ((1L << lg) < 4L * K) lg++;
+  const int shift = 61 - lg;  // |sum| < 4K in normalized units
+  exponents(P, Q);
+  slices(P, Q);
+  if (!aborted) products(M, N, K, shift, u0, w0);
+  combine(M, N, K, shift, C, e, norms);
+}
+
+__global__ void __launch_bounds__(TTHREADS, 1) k_batched_tc(BatchParams P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ Shared sh;
   __shared__ TcShared ts;
@@ -435,10 +506,12 @@ __global__ void __launch_bounds__(TPB, 1) k_batched_tc(BatchParams P) {
     ts.u = ts.w = ts.issued = 0;
     for (int s = 0; s < TSTAGES; s++) {
       mbar_init(smem_u32(&ts.full[s]), 1);
-      mbar_init(smem_u32(&ts.empty[s]), 1);
+      mbar_init(smem_u32(&ts.empty[s]), TMMA_WARPS);  // one commit per MMA issuer
     }
-    mbar_init(smem_u32(&ts.acc_full), 1);
-    mbar_init(smem_u32(&ts.acc_empty), 4);  // one arrival per epilogue warp
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&ts.acc_full[b]), TMMA_WARPS);
+      mbar_init(smem_u32(&ts.acc_empty[b]), 8);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -501,7 +574,7 @@ cudaError_t batched_launch_tc(int slots, const BatchParams& P, cudaStream_t st) 
   if (P.tc_slices < 2 || P.tc_slices > TMAXS || !P.tc_maps || !P.tc_ws || !P.err) return cudaErrorInvalidValue;
   static std::atomic<unsigned long long> attr_done{0};
   if (cudaError_t e = ensure_smem_attr(k_batched_tc, TSMEM, attr_done)) return e;
-  k_batched_tc<<<slots, TPB, TSMEM, st>>>(P);
+  k_batched_tc<<<slots, TTHREADS, TSMEM, st>>>(P);
   return cudaGetLastError();
 }
 

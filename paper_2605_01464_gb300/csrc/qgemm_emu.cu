@@ -14,7 +14,9 @@
 // own int64 accumulator, so that 2 x tiles items balance over the SMs.  For
 // each level of its item the MMA warp accumulates K-chunks into two FP32 TMEM
 // buffers in turn (256 columns each), so the tensor core fills one while the
-// eight epilogue warps drain the other: each converts its 32 rows x 128
+// eight epilogue warps drain the other (two MMA-issuing warps share each K
+// step, components 0-1 and 2-3, so that one thread's issue rate does not
+// bound the tensor core): each converts its 32 rows x 128
 // columns exactly to int32 and adds them into the level's sums, held in its
 // registers (128 per thread), then releases the buffer.  At the end of a
 // level the int32 sums are shifted to the common 64-bit fixed point and
@@ -48,7 +50,9 @@ constexpr int EB_PLANE = EBN * EBK * 2;                    // 4 KB
 constexpr int ESTAGE = 4 * (EA_PLANE + EB_PLANE);          // 48 KB
 constexpr int ESMEM = ESTAGES * ESTAGE + 1024;             // + alignment slack
 constexpr int EEPI_WARPS = 8;                              // two per TMEM lane quarter
-constexpr int ETHREADS = 64 + 32 * EEPI_WARPS;             // TMA warp, MMA warp, epilogue warps
+constexpr int EMMA_WARPS = 2;                              // MMA issuers: components 0-1 and 2-3
+constexpr int EEPI0 = 1 + EMMA_WARPS;                      // first epilogue warp
+constexpr int ETHREADS = 32 * (EEPI0 + EEPI_WARPS);        // TMA warp, MMA warps, epilogue warps
 constexpr int EGROUP_M = 16;
 // TMEM columns: two FP32 chunk accumulators of 256 columns (component c at
 // c * EBN): the MMAs of chunk w fill buffer w % 2 while the epilogue drains
@@ -111,10 +115,10 @@ __global__ void __launch_bounds__(ETHREADS, 1)
     abort_flag = 0;
     for (int s = 0; s < ESTAGES; s++) {
       mbar_init(smem_u32(&bar_full[s]), 1);
-      mbar_init(smem_u32(&bar_empty[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), EMMA_WARPS);  // one commit per MMA issuer
     }
     for (int b = 0; b < 2; b++) {
-      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_full[b]), EMMA_WARPS);
       mbar_init(smem_u32(&bar_acc_empty[b]), EEPI_WARPS);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -168,9 +172,10 @@ __global__ void __launch_bounds__(ETHREADS, 1)
        }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp < EEPI0) {
+    // ---------------- MMA issuers: warp 1 components 0, 1; warp 2 components 2, 3 ----------------
     if (lane == 0) {
+      const bool lo = warp == 1;
       int u = 0, w = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
@@ -200,8 +205,12 @@ __global__ void __launch_bounds__(ETHREADS, 1)
               const uint64_t ad0 = smem_desc_sw<ESWB>(smem_u32(sp)),
                              bd0 = smem_desc_sw<ESWB>(smem_u32(sp + 4 * EA_PLANE));
 #pragma unroll
-              for (int kk = 0; kk < EBK / 16; kk++)
-                qmma_k16<EA_PLANE, EB_PLANE>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
+              for (int kk = 0; kk < EBK / 16; kk++) {
+                if (lo)
+                  qmma_k16_half<EA_PLANE, EB_PLANE, 0>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
+                else
+                  qmma_k16_half<EA_PLANE, EB_PLANE, 2>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
+              }
               first = false;
               mma_commit(smem_u32(&bar_empty[st]));
             }
@@ -213,9 +222,9 @@ __global__ void __launch_bounds__(ETHREADS, 1)
     }
   } else {
     // ---------------- epilogue: exact FP32 -> int32 per chunk (registers), int64 per level ----------------
-    // Warp e = warp - 2 reads TMEM lane quarter warp % 4 (its 32 rows) and the
+    // Warp e = warp - EEPI0 reads TMEM lane quarter warp % 4 (its 32 rows) and the
     // column half e / 4 (components 2h, 2h + 1): 128 int32 level sums per thread.
-    const int e = warp - 2, quarter = warp & 3, half = e >> 2;
+    const int e = warp - EEPI0, quarter = warp & 3, half = e >> 2;
     const uint32_t tb0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * 128;
     int w = 0;
     bool ok = true;

@@ -86,6 +86,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __host__ __device__ constexpr bool qsign_neg(int r, int c) {
   return (r == 1 && (c == 0 || c == 2)) || (r == 2 && (c == 0 || c == 3)) || (r == 3 && (c == 0 || c == 1));
 }
+// The 8 of those MMAs that feed components C0 and C0 + 1 (two issuing
+// threads then share a K step).
+template <uint32_t A_PLANE, uint32_t B_PLANE, int C0>
+__device__ __forceinline__ void qmma_k16_half(uint32_t d_tmem, uint32_t ncols, uint64_t ad0, uint64_t bd0,
+                                              uint32_t idesc, bool fresh) {
+  constexpr uint32_t NEG_A = 1u << 13;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const uint64_t ad = ad0 + ((r * A_PLANE) >> 4);
+    const uint32_t acc = (fresh && r == 0) ? 0u : 1u;
+#pragma unroll
+    for (int c = C0; c < C0 + 2; c++)
+      mma_bf16(d_tmem + c * ncols, ad, bd0 + (((r ^ c) * B_PLANE) >> 4), qsign_neg(r, c) ? idesc | NEG_A : idesc,
+               acc);
+  }
+}
 // The 16 signed (r, c) MMAs of one K = 16 step: A plane r times B plane
 // r xor c into component c's accumulator (d_tmem + c * ncols), the sign from
 // the instruction descriptor's negate-A bit (bit 13).  ad0 / bd0 are the

@@ -146,10 +146,17 @@ def _unchi_t(torch, C):
 
 
 def _orth_t(torch, b, m, r, gen):
+    """Orthonormal columns by shifted CholeskyQR3 in FP32: the first Gram gets
+    a small diagonal shift (a square Gaussian factor is occasionally too
+    ill-conditioned for an FP32 Cholesky; the shift keeps the chi structure),
+    two unshifted passes restore orthonormality."""
     C = _chi_t(torch, torch.randn((b, 4, m, r), generator=gen, device=gen.device, dtype=torch.float32))
-    for _ in range(2):
+    for it in range(3):
         H = C.mH @ C
         H = 0.5 * (H + H.mH)
+        if it == 0:
+            d = H.diagonal(dim1=-2, dim2=-1).real.mean(-1)
+            H = H + (1e-4 * d)[:, None, None] * torch.eye(H.shape[-1], dtype=H.dtype, device=H.device)
         L = torch.linalg.cholesky(H)
         C = torch.linalg.solve_triangular(L, C.mH, upper=False).mH
     return C

@@ -827,12 +827,13 @@ def bench_learned(args, torch, qpinv):
 
 
 # DRAM bytes (read + write) per issued tensor flop from one ncu capture of
-# each current kernel on a 2048^3 product (profiles/k_qgemm_emu_2048_slices8.md:
-# 11.54 GB for 36 passes; profiles/k_qgemm_tc_2048_split2.md: 245 MB for 3
-# pairs); a launch's traffic is estimated as this times its issued flops.
-# None once the kernel changes after its capture.
-TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 11.536e9 / (36 * 32 * 2048.0 ** 3),
-                           "k_qgemm_tc": 245.07e6 / (3 * 32 * 2048.0 ** 3)}
+# the current exact-slice kernel on an 8-slice 2048^3 product
+# (profiles/k_qgemm_emu_2048_slices8.md: 11.90 GB for 36 passes); a launch's
+# traffic is estimated as this times its issued flops.  None where no
+# capture matches the launches the solve makes (the split GEMM's launches
+# carry the fused combine epilogue, the captured one a plain store).
+TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 11.8955e9 / (36 * 32 * 2048.0 ** 3),
+                           "k_qgemm_tc": None}
 
 
 def kernel_rooflines(st):

@@ -128,9 +128,11 @@ typedef struct {
   int stop_rule;     /* QPINV_STOP_*, default REL_PLATEAU */
   int penrose;       /* 1: compute E1..E4 in FP64 after the solve (default 1) */
   int profile;       /* 1: time every kernel launch with CUDA events (qpinv_get_stats) */
-  int batched_tile;  /* qpinv_solve_batched CTA GEMM tile: -1 = autotune (default; each batch
+  int batched_tile;  /* qpinv_solve_batched CTA GEMM engine: -1 = autotune (default; each batch
                         signature is timed once per context on a sample of its matrices),
-                        0 = 16x16, 1 = 32x32, 2 = 64x32, 3 = 32x64, 4 = 64x64 */
+                        CUDA-core double-FP32 tiles 0 = 16x16, 1 = 32x32, 2 = 64x32, 3 = 32x64,
+                        4 = 64x64, or 5 = tensor cores (exact 7-bit BF16 slices of the
+                        double-FP32 operands, tcgen05, int64 accumulation) */
   int hyper_order;   /* QPINV_QHPIM order k, 2..64 (default 19; k = 2 is Newton-Schulz, and
                         k = 1, X_{j+1} = X_j, makes no progress and is rejected) */
   int fuse_epilogue; /* 1 (default): the combine pass after a BF16 tensor-core product (residual
@@ -217,9 +219,11 @@ int qpinv_solve(qpinv_ctx* ctx, void* stream, int m, int n, const double* const 
  * solved in ONE persistent kernel launch: every CTA takes matrices from a
  * work counter (largest first) and runs alpha, X_0 = alpha A^H, the method
  * (residual on the smaller side), the stop rule of the context's options and
- * E1..E4 for each, in double-FP32 arithmetic (an unevaluated sum of two
+ * E1..E4 for each, with double-FP32 masters (an unevaluated sum of two
  * floats, ~2^-46: small blocks are often rank deficient, and null-space
- * noise grows by ~kappa^2 over a solve).  Options used: stop_rule, qrapid_N,
+ * noise grows by ~kappa^2 over a solve); the products run on the CUDA
+ * cores in double-FP32 or on the tensor cores as exact-slice products of
+ * the same accuracy (batched_tile).  Options used: stop_rule, qrapid_N,
  * hyper_order, batched_tile, alpha_mode (SAFE, FRO or USER; SPECTRAL and
  * LEARNED run as SAFE).
  * out[b] (host array, may be NULL) receives each outcome; tc_iters and

@@ -86,9 +86,13 @@ struct KParams {
 __device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // Fused combine for 16 consecutive columns j0.. of row i (this lane), plane c:
-// v = the product's values; see EpiArgs.  nc = valid columns (1..16).
-__device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0, int nc, const float* v,
-                                          float& sdx, float& sx, int& bad) {
+// v = the product's values; see EpiArgs.  nc = valid columns (1..16, the
+// same for the whole warp); rok = row i exists (the whole warp calls this:
+// the transposed B-form goes through `stg`, this warp's 16 x 32 BF16 block
+// of shared memory, so that each lane writes 16-byte pieces of B-form rows).
+__device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool rok, int row0, int M, int j0, int nc,
+                                          const float* v, bf16* stg, float& sdx, float& sx, int& bad) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int o = 0; o < E.nout; o++) {
     const EpiOut& O = E.out[o];
@@ -97,7 +101,7 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0
     for (int t = 0; t < 16; t++) w[t] = O.cacc != 0.f ? O.cacc * v[t] : 0.f;
 #pragma unroll 1
     for (int a = 0; a < 4; a++) {
-      if (!E.aux[a] || O.caux[a] == 0.f) continue;
+      if (!rok || !E.aux[a] || O.caux[a] == 0.f) continue;
       const float* ap = E.aux[a] + c * E.ps_aux[a] + (long)i * E.ld_aux[a] + j0;
       const float ca = O.caux[a];
       if (nc == 16 && al16(ap)) {
@@ -120,7 +124,7 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0
       for (int t = 0; t < 16; t++)
         if (i == j0 + t) w[t] += O.diag;
     }
-    if (o == 0 && E.partials) {
+    if (o == 0 && E.partials && rok) {
       const float* xp = E.aux[0] ? E.aux[0] + c * E.ps_aux[0] + (long)i * E.ld_aux[0] + j0 : nullptr;
 #pragma unroll
       for (int t = 0; t < 16; t++)
@@ -131,7 +135,7 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0
           bad += isfinite(w[t]) ? 0 : 1;
         }
     }
-    if (O.mp) {
+    if (O.mp && rok) {
       float* dst = O.mp + c * O.mps + (long)i * O.mld + j0;
       if (nc == 16 && al16(dst)) {
 #pragma unroll
@@ -155,7 +159,7 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0
           h[t] = __float2bfloat16_rn(r[t]);
           r[t] -= __bfloat162float(h[t]);
         }
-        if (O.a) {
+        if (O.a && rok) {
           bf16* dst = O.a + (long)l * 4 * O.psa + c * O.psa + (long)i * O.lda + j0;
           if (nc == 16 && al16(dst)) {
             uint32_t pk[8];
@@ -171,12 +175,28 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, int j0
           }
         }
         if (O.b) {
-          // B-form row j holds column j of the output: lanes (rows i) of one
-          // warp write consecutive entries of it
-          bf16* dst = O.b + (long)l * 4 * O.psb + c * O.psb + (long)j0 * O.ldb + i;
+          // B-form row j holds column j of the output (rows row0 .. row0 + 31
+          // contiguous): transpose the warp's 32 x 16 block through shared
+          // memory, then lane q writes 8 rows of column q / 4 (16 bytes), twice
 #pragma unroll
-          for (int t = 0; t < 16; t++)
-            if (t < nc) dst[(long)t * O.ldb] = h[t];
+          for (int t = 0; t < 16; t++) stg[t * 32 + lane] = h[t];
+          __syncwarp();
+          bf16* bl = O.b + (long)l * 4 * O.psb + c * O.psb;
+#pragma unroll
+          for (int k = 0; k < 2; k++) {
+            const int q = lane + 32 * k, t = q >> 2, part = q & 3;
+            const int r0 = row0 + part * 8;
+            if (t < nc && r0 < M) {
+              bf16* dst = bl + (long)(j0 + t) * O.ldb + r0;
+              const bf16* src = stg + t * 32 + part * 8;
+              if (r0 + 8 <= M && al16(dst)) {
+                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+              } else {
+                for (int x = 0; x < 8 && r0 + x < M; x++) dst[x] = src[x];
+              }
+            }
+          }
+          __syncwarp();
         }
       }
     }
@@ -281,8 +301,10 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
       fence_after();
     }
     if (have && P.E.nout > 0) {
-      // fused combine: one row per lane, 16 columns at a time, straight from TMEM
+      // fused combine: one row per lane, 16 columns at a time, straight from TMEM;
+      // the idle pipeline stages give each warp 1 KB for the B-form transpose
       const int i = row0 + lane;
+      bf16* stg = reinterpret_cast<bf16*>(smem) + (warp - 2) * 512;
       float sdx = 0.f, sx = 0.f;
       int bad = 0;
 #pragma unroll 1
@@ -298,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
           }
           const int j0 = n0 + ch * 16;
           const int nc = min(16, P.N - j0);
-          if (i < P.M && nc > 0) epi_piece(P.E, c, i, j0, nc, v, sdx, sx, bad);
+          if (nc > 0) epi_piece(P.E, c, i, i < P.M, row0, P.M, j0, nc, v, stg, sdx, sx, bad);
         }
       }
       if (P.E.partials) {

@@ -860,6 +860,17 @@ def kernel_rooflines(st):
                     "achieved_issued": iss, "frac_issued": iss / bf16_sust,
                     "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % src})
     out.sort(key=lambda r: -r["total_ms"])
+    # the HBM-bound passes that remain outside the GEMM epilogues (FP64-master
+    # combines, exact slicing, norms): bytes counted per launch by the library
+    # (every plane read or written once), over their summed event time
+    if st.get("ew_launches") and st.get("ew_ms", 0.0) > 0:
+        gbs = st["ew_bytes"] / (st["ew_ms"] * 1e-3) / 1e9
+        out.append({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "traffic": None, "kernel": "elementwise passes (combine, exact slicing, exponents, norms)",
+                     "launches": st["ew_launches"], "total_ms": st["ew_ms"],
+                     "ms_per_launch": st["ew_ms"] / st["ew_launches"],
+                     "bytes_per_launch": st["ew_bytes"] / st["ew_launches"],
+                     "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % src})
     return out or [None]
 
 

@@ -112,6 +112,19 @@ cudaError_t launch_maxexp(const Planes<const double>& A, int rows, int cols, int
 cudaError_t launch_f32_to_f64(const Planes<const float>& src, int rows, int cols,
                               const Planes<double>& dst, cudaStream_t st);
 
+// Exact slices (S balanced 7-bit digits of v * 2^-e) of a row-major plane
+// set: A-form rows (row exponents e[i]; dst [S][4][rows][ld]) or the
+// transposed B-form (column exponents e[j]; dst [S][4][cols][ld]); padding
+// up to the next multiple of 8 along the slice rows is written as 0.
+cudaError_t launch_slice_rows(const Planes<const double>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st);
+cudaError_t launch_slice_rows(const Planes<const float>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st);
+cudaError_t launch_slice_cols(const Planes<const double>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st);
+cudaError_t launch_slice_cols(const Planes<const float>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st);
+
 cudaError_t launch_qgemm_f64(int M, int K, int N, const Planes<const double>& A,
                              const Planes<const double>& B, const Planes<double>& C,
                              cudaStream_t st);

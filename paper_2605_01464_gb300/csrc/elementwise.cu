@@ -361,6 +361,83 @@ static bool combine_pairs_ok(const CombineArgs& a) {
   return true;
 }
 
+// ---------------------------------------------------------------- exact slicing
+// S exact slices (slice_store's digits) of 8 consecutive entries that share
+// one exponent, written as one 16-byte store per slice plane.
+template <typename T>
+__device__ __forceinline__ void slice8_store(bf16* base, long lstride, int S, const T* v, int e) {
+  long long F[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) F[q] = to_fixed(v[q], 7 * S - e);
+  for (int l = S - 1; l >= 0; l--) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      float x[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (l > 0) {
+          int d = (int)(F[q + h] & 127);
+          if (d >= 64) d -= 128;
+          F[q + h] = (F[q + h] - d) >> 7;
+          x[h] = ldexpf((float)d, -7 * (l + 1));
+        } else {
+          x[h] = ldexpf((float)F[q + h], -7);
+        }
+      }
+      pk[q >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
+    }
+    *reinterpret_cast<uint4*>(base + l * lstride) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// A-form slices of a row-major plane set (row exponents e[i]): one thread per
+// (plane, row, 8 columns), columns past `cols` up to the padded pitch as 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_slice_rows(Planes<const T> A, int rows, int cols, const int* __restrict__ e,
+                                                    int S, bf16* dst, long ld, long ps) {
+  const int g8 = (cols + 7) / 8;
+  const long total = 4L * rows * g8;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int g = (int)(t % g8);
+    const long ci = t / g8;
+    const int i = (int)(ci % rows), c = (int)(ci / rows);
+    const T* src = A.p + c * A.ps + (long)i * A.ld + 8 * g;
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = 8 * g + q < cols ? src[q] : (T)0;
+    slice8_store<T>(dst + c * ps + (long)i * ld + 8 * g, 4 * ps, S, v, e[i]);
+  }
+}
+
+// B-form slices (the plane-wise transpose; column exponents e[j]): a block
+// takes 32 rows x 64 columns of one plane through shared memory, then each
+// thread writes 8 consecutive rows of one column, rows past `rows` up to the
+// padded pitch as 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_slice_cols(Planes<const T> A, int rows, int cols, const int* __restrict__ e,
+                                                    int S, bf16* dst, long ld, long ps) {
+  __shared__ T tile[64][33];
+  const int c = blockIdx.z, i0 = blockIdx.y * 32, j0 = blockIdx.x * 64;
+  {
+    const int il = threadIdx.x >> 3, j8 = (threadIdx.x & 7) * 8;  // 32 rows x 8 groups of 8 columns
+    const T* src = A.p + c * A.ps + (long)(i0 + il) * A.ld + j0 + j8;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      tile[j8 + q][il] = (i0 + il < rows && j0 + j8 + q < cols) ? src[q] : (T)0;
+  }
+  __syncthreads();
+  const int jl = threadIdx.x >> 2, ig = (threadIdx.x & 3) * 8;  // 64 columns x 4 groups of 8 rows
+  const int j = j0 + jl;
+  if (j < cols && i0 + ig < ((rows + 7) / 8) * 8) {
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = tile[jl][ig + q];
+    slice8_store<T>(dst + c * ps + (long)j * ld + i0 + ig, 4 * ps, S, v, e[j]);
+  }
+}
+
 __global__ void k_reduce_partials(const double* p, int nblocks, int nvals, double* out) {
   __shared__ double sh[8];
   for (int v = 0; v < nvals; v++) {
@@ -704,6 +781,47 @@ cudaError_t launch_f64_to_f32(const Planes<const double>& src, int rows, int col
   k_f64_to_f32<<<grid_for((long)rows * cols), 256, 0, st>>>(src, rows, cols, dst);
   ++g_kernel_launches;
   return cudaGetLastError();
+}
+
+
+template <typename T>
+static cudaError_t slice_rows_t(const Planes<const T>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                                long ld, long ps, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if ((ld & 7) || (ps & 7) || (reinterpret_cast<uintptr_t>(dst) & 15) || ld < ((cols + 7) / 8) * 8)
+    return cudaErrorInvalidValue;
+  const long total = 4L * rows * ((cols + 7) / 8);
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_slice_rows<T><<<blocks, 256, 0, st>>>(A, rows, cols, e, S, dst, ld, ps);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t slice_cols_t(const Planes<const T>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                                long ld, long ps, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if ((ld & 7) || (ps & 7) || (reinterpret_cast<uintptr_t>(dst) & 15) || ld < ((rows + 7) / 8) * 8)
+    return cudaErrorInvalidValue;
+  dim3 grid((cols + 63) / 64, (rows + 31) / 32, 4);
+  k_slice_cols<T><<<grid, 256, 0, st>>>(A, rows, cols, e, S, dst, ld, ps);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+cudaError_t launch_slice_rows(const Planes<const double>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st) {
+  return slice_rows_t<double>(A, rows, cols, e, S, dst, ld, ps, st);
+}
+cudaError_t launch_slice_rows(const Planes<const float>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st) {
+  return slice_rows_t<float>(A, rows, cols, e, S, dst, ld, ps, st);
+}
+cudaError_t launch_slice_cols(const Planes<const double>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st) {
+  return slice_cols_t<double>(A, rows, cols, e, S, dst, ld, ps, st);
+}
+cudaError_t launch_slice_cols(const Planes<const float>& A, int rows, int cols, const int* e, int S, bf16* dst,
+                              long ld, long ps, cudaStream_t st) {
+  return slice_cols_t<float>(A, rows, cols, e, S, dst, ld, ps, st);
 }
 
 }  // namespace qp

@@ -458,23 +458,18 @@ struct Solver {
     zb.ldb = rup8(K);
     zb.psb = (long)N * zb.ldb;
     zb.b = (bf16*)buf(c, "emu.zb", sizeof(bf16) * 4 * S * (size_t)zb.psb + 64);
-    {
-      CombineArgs a = base_args(M, K, nullptr);
-      aux(a, 0, P);
-      OutSpec& o = a.out[a.nout++];
-      o.s16 = za;
-      o.exp_a = eP;
-      o.caux[0] = 1.0;
-      run(a);
-    }
-    {
-      CombineArgs a = base_args(K, N, nullptr);
-      aux(a, 0, Q);
-      OutSpec& o = a.out[a.nout++];
-      o.s16 = zb;
-      o.exp_b = eQ;
-      o.caux[0] = 1.0;
-      run(a);
+    // the slices: P's rows (A-form), Q's columns (B-form, transposed)
+    const double sbytes = 2.0 * S * 4;
+    if (dbl) {
+      timed(c, EV_EW, 0, 0, (32.0 + sbytes) * M * K,
+            [&] { return launch_slice_rows(dview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
+      timed(c, EV_EW, 0, 0, (32.0 + sbytes) * K * N,
+            [&] { return launch_slice_cols(dview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
+    } else {
+      timed(c, EV_EW, 0, 0, (16.0 + sbytes) * M * K,
+            [&] { return launch_slice_rows(fview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
+      timed(c, EV_EW, 0, 0, (16.0 + sbytes) * K * N,
+            [&] { return launch_slice_cols(fview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
     }
     long long* acc = (long long*)buf(c, "emu.acc", sizeof(long long) * 4 * (size_t)M * N + 64);
     ck(c, cudaMemsetAsync(acc, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");

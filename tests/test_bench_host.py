@@ -37,6 +37,17 @@ def test_rooflines_without_gemm_launches():
     assert bench.kernel_rooflines(stats()) == [None]
 
 
+def test_elementwise_entry_is_hbm_bytes_over_time():
+    st = stats(emu_n=1, emu_ms=5.0, emu_fl=1e11, emu_iss=3.6e12)
+    st.update(ew_launches=40, ew_ms=8.0, ew_bytes=16e9)
+    r = bench.kernel_rooflines(st)
+    e = r[-1]
+    assert e["bound"] == "hbm" and e["unit"] == "GB/s"
+    assert e["achieved"] == pytest.approx(16e9 / 8e-3 / 1e9)  # 2000 GB/s
+    assert e["frac"] == pytest.approx(e["achieved"] / e["peak"])
+    assert r[0]["kernel"].startswith("k_qgemm_emu")  # GEMMs first, the HBM entry last
+
+
 def test_ssim_of_identical_images_is_one_and_drops_with_noise():
     pytest.importorskip("scipy")
     rng = np.random.default_rng(0)

@@ -9,27 +9,29 @@
 //   1. per-row exponents of P and per-column exponents of Q (integer bit
 //      operations on the df high parts);
 //   2. every df entry v = hi + lo, scaled by 2^-e of its row (P) or column
-//      (Q), becomes S balanced 7-bit digits -- exact BF16 values -- in the
-//      slot's slice scratch (P row-major, Q transposed: both K-major), zero
-//      padded in K to a multiple of 32;
+//      (Q), becomes S = 7 balanced base-128 digits, each stored as the BF16
+//      value of the digit itself (an integer of at most 8 bits: exact), in
+//      the slot's slice scratch (P row-major, Q transposed: both K-major),
+//      zero padded in K to a multiple of 32;
 //   3. warp-specialised tensor-core phase over the product's 128 x 64
-//      quaternion tiles: TMA stages the slice planes (64-byte swizzle), one
-//      thread issues the 16 signed MMAs per K step, level d = s + t sums the
+//      quaternion tiles: TMA stages the slice planes (64-byte swizzle), two
+//      threads issue the 16 signed MMAs per K step, level d = s + t sums the
 //      pairs (s, t) in K chunks short enough for exact FP32 partial sums in
-//      TMEM, the epilogue warps add each chunk exactly into an int32 level
-//      sum in TMEM and each finished level into an int64 fixed-point
-//      accumulator (global, L2-resident);
-//   4. all threads turn the int64 sums back into df values (exact two-term
-//      split) and apply the pass's epilogue (scale, aux terms, diagonal,
-//      stop-test norms).
+//      TMEM (integers: the digits are unscaled), the epilogue warps add each
+//      chunk exactly into int32 level sums in registers and store each
+//      finished level to its own int32 plane (through a per-warp shared
+//      transposition tile, so that the stores are coalesced; stores only);
+//   4. all threads sum each entry's level planes in 64-bit fixed point, turn
+//      the sum into a df value (exact two-term split) and apply the pass's
+//      epilogue (scale, aux terms, diagonal, stop-test norms).
 // With S = 7 slices (49 bits) the products carry the df masters' accuracy
 // (about 2^-46), which rank-deficient blocks need: rounding that reaches the
 // complement of the range is multiplied by the method's order every step.
 //
-// Roles inside a product (256 threads): warp 0 lane 0 TMA, warp 1 lane 0
-// MMA (warp 1 owns TMEM: 512 columns, FP32 chunk buffer + int32 level sums),
-// warps 4-7 the TMEM epilogue (TMEM lane quarter = warp % 4); every phase in
-// between uses all warps.  mbarrier phases continue across products.  Every
+// Roles inside a product (352 threads): warp 0 lane 0 TMA, warps 1-2 lane 0
+// MMA (components 0-1 and 2-3; warp 1 owns TMEM: 512 columns, two FP32 chunk
+// buffers), warps 3-10 the TMEM epilogue (TMEM lane quarter = warp % 4,
+// column half = (warp - 3) / 4); exponents and slicing use all warps.  mbarrier phases continue across products.  Every
 // wait is bounded (2 s): on expiry the kernel raises an error word, stops
 // issuing tensor-core work, drains its copies and frees TMEM.
 #define QP_BATCHED_TILE 5
@@ -45,24 +47,30 @@ constexpr int TSTAGES = 4;
 constexpr int TA_PLANE = TBM * TBK * 2;            // 8 KB
 constexpr int TB_PLANE = TBN * TBK * 2;            // 4 KB
 constexpr int TSTAGE = 4 * (TA_PLANE + TB_PLANE);  // 48 KB
-constexpr int TSTAGING = 4 * 32 * 33 * 8;          // slicing transpose, aliased with stage 0
-constexpr int TSMEM = TSTAGES * TSTAGE + 1024;
-static_assert(TSTAGING <= TSTAGE, "the slicing staging fits in one idle stage");
+// per epilogue warp: a 32-row x 16-column int32 transposition tile (row
+// pitch 20 words: 16-byte aligned rows, conflict-free 16-byte stores)
+constexpr int TXP = 20;
+constexpr int TXTILE = 32 * TXP * 4;  // bytes
+constexpr int TSMEM = TSTAGES * TSTAGE + 8 * TXTILE + 1024;
 constexpr int TKP = MAXD;   // K pitch of the slice scratch (elements)
 constexpr int TMAXS = 8;    // slice planes reserved per operand
+constexpr int TS = 7;       // slices formed per operand (49 bits)
+static_assert(TS >= 2 && TS <= TMAXS, "slice count");
 constexpr uint32_t TIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
                             ((uint32_t)(TBM >> 4) << 24);
 static_assert(TSMEM + 4096 <= 227 * 1024, "shared memory per CTA");
 constexpr int TMMA_WARPS = 2;               // MMA issuers: components 0-1 and 2-3
 constexpr int TEPI0 = 1 + TMMA_WARPS;        // first of the 8 epilogue warps (two per TMEM lane quarter)
 constexpr int TTHREADS = 32 * (TEPI0 + 8);   // 352
+constexpr int TSTAGING = (TTHREADS / 32) * MAXD * (int)sizeof(int);  // column-exponent partials, in stage 0
+static_assert(TSTAGING <= TSTAGE, "the exponent staging fits in one idle stage");
 static_assert(TTHREADS <= TPB_MAX, "shared per-matrix state sized for the block");
 
 // slice scratch per slot: A-form and B-form [TMAXS][4][MAXD][TKP] BF16, then
-// the int64 accumulator [4][MAXD][MAXD]
+// the int32 level sums [TS][4][MAXD][MAXD]
 constexpr size_t TC_SLICE_BYTES = (size_t)TMAXS * 4 * MAXD * TKP * sizeof(bf16);
-constexpr size_t TC_C64_BYTES = (size_t)4 * MAXD * MAXD * sizeof(long long);
-constexpr size_t TC_SLOT_BYTES = 2 * TC_SLICE_BYTES + TC_C64_BYTES;
+constexpr size_t TC_LVL_BYTES = (size_t)TS * 4 * MAXD * MAXD * sizeof(int);
+constexpr size_t TC_SLOT_BYTES = 2 * TC_SLICE_BYTES + TC_LVL_BYTES;
 
 struct TcShared {
   uint64_t full[TSTAGES], empty[TSTAGES], acc_full[2], acc_empty[2];
@@ -77,61 +85,103 @@ __device__ __forceinline__ int fexp(float v) {
   const int ex = (int)((__float_as_uint(v) >> 23) & 0xFF);
   return ex == 0 ? -100000 : ex - 126;
 }
-// round(v * 2^sh) as an integer from the bits of v (|v * 2^sh| < 2^62).
-__device__ __forceinline__ long long ffixed(float v, int sh) {
-  const unsigned b = __float_as_uint(v);
-  const int ex = (int)((b >> 23) & 0xFF);
-  if (ex == 0) return 0;
-  const long long mant = (long long)((b & 0x7FFFFFu) | (1u << 23));
-  const int k = ex - 150 + sh;
-  long long F;
-  if (k >= 0) F = mant << k;
-  else if (k <= -26) F = 0;
-  else F = (mant + (1ll << (-k - 1))) >> (-k);
-  return (b >> 31) ? -F : F;
-}
-// S balanced base-128 digits of (hi + lo) * 2^(7S - e), slice l at
-// base[l * lstride]: slice l = digit_l * 2^-7(l+1) (the top digit may reach 128).
-__device__ __forceinline__ void slice_df(bf16* base, long lstride, int S, dfv v, int e) {
-  const int sh = 7 * S - e;
-  long long F = ffixed(v.hi, sh) + ffixed(v.lo, sh);
-  for (int l = S - 1; l >= 1; l--) {
-    int d = (int)(F & 127);
-    if (d >= 64) d -= 128;
-    F = (F - d) >> 7;
-    base[l * lstride] = __float2bfloat16_rn(ldexpf((float)d, -7 * (l + 1)));
-  }
-  base[0] = __float2bfloat16_rn(ldexpf((float)F, -7));
+// 2^a as a float for a in [-126, 127] (exponent bits).
+__device__ __forceinline__ float pow2f(int a) { return __int_as_float((a + 127) << 23); }
+
+// v * 2^x for an exponent x of any size: two exact power-of-two factors
+// (each clamped to the float range; a result below it is zero anyway).
+__device__ __forceinline__ float scale2(float v, int x) {
+  const int a = min(max(x >> 1, -126), 127), b = min(max(x - (x >> 1), -126), 127);
+  return v * pow2f(a) * pow2f(b);
 }
 
-// The same for 8 consecutive entries of one row (one exponent), written as
-// 16-byte stores per slice plane (base 16-byte aligned).
-__device__ __forceinline__ void slice_df8(bf16* base, long lstride, int S, const dfv* v, int e) {
-  const int sh = 7 * S - e;
-  long long F[8];
-#pragma unroll
-  for (int q = 0; q < 8; q++) F[q] = ffixed(v[q].hi, sh) + ffixed(v[q].lo, sh);
-  for (int l = S - 1; l >= 0; l--) {
-    uint32_t pk[4];
-#pragma unroll
-    for (int q = 0; q < 8; q += 2) {
-      float x[2];
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        if (l > 0) {
-          int d = (int)(F[q + h] & 127);
-          if (d >= 64) d -= 128;
-          F[q + h] = (F[q + h] - d) >> 7;
-          x[h] = ldexpf((float)d, -7 * (l + 1));
-        } else {
-          x[h] = ldexpf((float)F[q + h], -7);
-        }
-      }
-      pk[q >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
-    }
-    *reinterpret_cast<uint4*>(base + l * lstride) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+// Factors s1 s2 = 2^(7 TS - e) that bring a row (column) with exponent e to
+// |v 2^(7 TS - e)| <= 2^(7 TS); zero for a row of zeros / subnormals.
+__device__ __forceinline__ void slice_scale(int e, float& s1, float& s2) {
+  if (e < -10000) {
+    s1 = s2 = 0.f;
+    return;
   }
+  const int sh = min(max(7 * TS - e, -252), 252);
+  s1 = pow2f(sh >> 1);
+  s2 = pow2f(sh - (sh >> 1));
+}
+
+// Balanced base-128 digits: with F = round(v 2^(7 TS - e)), |F| <= 2^(7 TS),
+// and G = F + 64 (1 + 2^7 + ... + 2^(7 (TS - 2))), the digit of weight
+// 2^(7 q) is ((G >> 7 q) & 127) - 64 for q < TS - 1, and the top one is
+// G >> 7 (TS - 1), in [-128, 128].  Slice p (p = 0 the top) holds the digit of
+// weight 2^(7 (TS - 1 - p)), so that v 2^-e = sum_p digit_p 2^-7(p+1).
+constexpr long long digit_bias_of(int n) { return n == 0 ? 0 : (64LL << (7 * (n - 1))) + digit_bias_of(n - 1); }
+constexpr long long DIGIT_BIAS = digit_bias_of(TS - 1);
+__device__ __forceinline__ long long biased_fixed(dfv v, float s1, float s2) {
+  // each part scaled exactly, rounded to an integer (|part| <= 2^(7 TS))
+  return __float2ll_rn(v.hi * s1 * s2) + __float2ll_rn(v.lo * s1 * s2) + DIGIT_BIAS;
+}
+// Digit p of a biased value as a float, exactly: 2^23 + u - (2^23 + 64) for
+// the low digits (u the 7-bit field), 2^23 + (t + 128) - (2^23 + 128) for the
+// top one.
+template <int p>
+__device__ __forceinline__ float digit_f(long long G) {
+  if constexpr (p == 0) {
+    return __int_as_float(0x4B000000 | (int)((G >> (7 * (TS - 1))) + 128)) - 8388736.0f;
+  } else {
+    return __int_as_float(0x4B000000u | ((unsigned)(G >> (7 * (TS - 1 - p))) & 127u)) - 8388672.0f;
+  }
+}
+// Slice plane p of 8 consecutive biased values: 8 BF16 digits (the upper
+// halves of the exact floats) in one 16-byte store.
+template <int p>
+__device__ __forceinline__ void store_plane8(bf16* dst, const long long* G) {
+  uint32_t pk[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    pk[q] = __byte_perm(__float_as_uint(digit_f<p>(G[2 * q])), __float_as_uint(digit_f<p>(G[2 * q + 1])), 0x7632);
+  *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+template <int p>
+__device__ __forceinline__ void store_planes8(bf16* base, long lstride, const long long* G) {
+  store_plane8<p>(base + p * lstride, G);
+  if constexpr (p + 1 < TS) store_planes8<p + 1>(base, lstride, G);
+}
+// The TS slices of 8 consecutive entries sharing one scale (base 16-byte aligned).
+__device__ __forceinline__ void slice8(bf16* base, long lstride, const dfv* v, float s1, float s2) {
+  long long G[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) G[q] = biased_fixed(v[q], s1, s2);
+  store_planes8<0>(base, lstride, G);
+}
+
+// Epilogue: drain FP32 chunk w (TMEM buffer w % 2) into the thread's int32
+// level sums and release the buffer.  The level's first chunk assigns the
+// sums, later chunks add: the sums are dead between levels.
+template <bool FIRST>
+__device__ __forceinline__ bool drain_chunk(int (&acc)[128], int& w, uint32_t tb0, int lane, TcShared* ts, int* err) {
+  const int b = w & 1;
+  const uint32_t tb = tb0 + b * 256;
+  int have = 1;
+  if (lane == 0) have = mbar_wait(smem_u32(&ts->acc_full[b]), (w >> 1) & 1, &ts->abort_flag, err, 24) ? 1 : 0;
+  have = __shfl_sync(0xffffffffu, have, 0);
+  if (!have) return false;
+  fence_after();
+#pragma unroll
+  for (int p = 0; p < 8; p++) {
+    uint32_t f[16];
+    tmem_ld16u(tb + p * 16, f);
+    tmem_wait_ld();
+    // the chunk's FP32 sums are integers (products of unscaled digits)
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+      const int x = __float2int_rn(__uint_as_float(f[t]));
+      if constexpr (FIRST) acc[p * 16 + t] = x;
+      else acc[p * 16 + t] += x;
+    }
+  }
+  fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(smem_u32(&ts->acc_empty[b]));
+  w++;
+  return true;
 }
 
 // The tensor-core CTA GEMM: C = epilogue(P Q) for df matrices (P M x K, Q K x N).
@@ -143,16 +193,15 @@ struct TcGemm {
   const CUtensorMap* mapB;
   bf16* sa;  // A-form slices [TMAXS][4][MAXD][TKP]
   bf16* sb;  // B-form slices [TMAXS][4][MAXD][TKP] (row j = column j of Q)
-  long long* c64;  // [4][MAXD][MAXD]
-  int S;
+  int* lvl;  // int32 level sums [TS][4][MAXD][MAXD]
   int* err;
 
   __device__ void operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms);
   // the phases, each its own function (own register allocation)
   __device__ void exponents(const DM& P, const DM& Q);
   __device__ void slices(const DM& P, const DM& Q);
-  __device__ void products(int M, int N, int K, int shift, int u0, int w0);
-  __device__ void combine(int M, int N, int K, int shift, const DM& C, const Epi& e, double* norms);
+  __device__ void products(int M, int N, int K, int u0, int w0);
+  __device__ void combine(int M, int N, int shift, const DM& C, const Epi& e, double* norms);
 };
 
 __device__ __noinline__ void TcGemm::exponents(const DM& P, const DM& Q) {
@@ -195,85 +244,98 @@ __device__ __noinline__ void TcGemm::exponents(const DM& P, const DM& Q) {
 
 __device__ __noinline__ void TcGemm::slices(const DM& P, const DM& Q) {
   const int K = P.cols, M = P.rows, N = Q.cols;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  (void)warp;
-  (void)lane;
-  // ---- 2. exact slices (zero padded in K to a multiple of TBK) ----
+  const int tid = threadIdx.x;
+  // exact slices, zero padded in K to a multiple of TBK; units of 8
+  // consecutive k of one (component, row) for P and one (component, column)
+  // for Q, two units per thread in flight (their 16 loads issued first)
   const int KP = (K + TBK - 1) / TBK * TBK;
   const long lstride = 4L * MAXD * TKP;
   const int KP8 = KP / 8;
-  for (long t = tid; t < (long)M * KP8; t += TTHREADS) {
-    const int i = (int)(t / KP8), k = (int)(t % KP8) * 8;
-    // two planes' 16 loads in flight before any is used (the slot's
-    // matrices live in L2 / HBM and one CTA per SM has few warps to hide it)
-    const int e = ts->eP[i];
-#pragma unroll
-    for (int c0 = 0; c0 < 4; c0 += 2) {
+  {
+    const long units = 4L * M * KP8;
+    for (long t0 = tid; t0 < units; t0 += 2 * TTHREADS) {
       dfv v[2][8];
+      int ci[2], ii[2], kk[2];
 #pragma unroll
-      for (int c = 0; c < 2; c++)
+      for (int h = 0; h < 2; h++) {
+        const long t = t0 + h * TTHREADS;
+        const bool ok = t < units;
+        const long r = ok ? t : 0;
+        kk[h] = (int)(r % KP8) * 8;
+        ii[h] = (int)((r / KP8) % M);
+        ci[h] = (int)(r / ((long)KP8 * M));
 #pragma unroll
-        for (int q = 0; q < 8; q++) v[c][q] = k + q < K ? P.at(c0 + c, i, k + q) : dfv{0.f, 0.f};
+        for (int q = 0; q < 8; q++)
+          v[h][q] = ok && kk[h] + q < K ? P.at(ci[h], ii[h], kk[h] + q) : dfv{0.f, 0.f};
+      }
 #pragma unroll
-      for (int c = 0; c < 2; c++) slice_df8(sa + ((long)(c0 + c) * MAXD + i) * TKP + k, lstride, S, v[c], e);
+      for (int h = 0; h < 2; h++) {
+        if (t0 + h * TTHREADS >= units) break;
+        float s1, s2;
+        slice_scale(ts->eP[ii[h]], s1, s2);
+        slice8(sa + ((long)ci[h] * MAXD + ii[h]) * TKP + kk[h], lstride, v[h], s1, s2);
+      }
     }
   }
   {
-    // Q transposed through shared memory: reads along j, writes along k (the
-    // first 256 threads: 8 rows of 32 per pass)
-    dfv(*st)[32][33] = reinterpret_cast<dfv(*)[32][33]>(smem);  // the idle stage ring
-    const int tx = tid & 31, ty = tid >> 5;
-    for (int k0 = 0; k0 < KP; k0 += 32)
-      for (int j0 = 0; j0 < N; j0 += 32) {
-        if (tid < 256) {
+    // Q: lanes 0-15 take 16 consecutive columns at one group of 8 k, lanes
+    // 16-31 the same columns at the next group (coalesced loads along j; the
+    // two 16-byte stores of a column meet in one 32-byte sector)
+    const int NB = (N + 15) / 16, KP16 = KP / 16;
+    const long lanes_total = 4L * NB * KP16 * 32;  // (component, 16-column block, 16 k) x 32 lanes
+    for (long t0 = tid; t0 < lanes_total; t0 += 2 * TTHREADS) {
+      dfv v[2][8];
+      int ci[2], jj[2], kk[2];
+      bool ok[2];
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const int k = k0 + ty + 8 * q, j = j0 + tx;
+      for (int h = 0; h < 2; h++) {
+        const long t = t0 + h * TTHREADS;
+        const int jl = (int)(t & 15), kp = (int)((t >> 4) & 1);
+        long r = t >> 5;
+        const int k16 = (int)(r % KP16);
+        r /= KP16;
+        const int jb = (int)(r % NB);
+        ci[h] = (int)(r / NB);
+        jj[h] = jb * 16 + jl;
+        kk[h] = k16 * 16 + kp * 8;
+        ok[h] = t < lanes_total && jj[h] < N;
 #pragma unroll
-            for (int c = 0; c < 4; c++) st[c][ty + 8 * q][tx] = (k < K && j < N) ? Q.at(c, k, j) : dfv{0.f, 0.f};
-          }
-        }
-        __syncthreads();
-        if (tid < 256) {
-          // 32 columns x 4 groups of 8 k: thread (jl, g) = (tid / 4 % 32, tid % 4), one plane pass each
-          const int jl = (tid >> 2) & 31, g = tid & 3, j = j0 + jl, k = k0 + 8 * g;
-          if (j < N)
-#pragma unroll 1
-            for (int c = 0; c < 4; c++) {
-              if ((tid >> 7) != (c & 1)) continue;  // threads 0..127 planes 0, 2; 128..255 planes 1, 3
-              dfv v[8];
-#pragma unroll
-              for (int q = 0; q < 8; q++) v[q] = st[c][8 * g + q][jl];
-              slice_df8(sb + ((long)c * MAXD + j) * TKP + k, lstride, S, v, ts->eQ[j]);
-            }
-        }
-        __syncthreads();
+        for (int q = 0; q < 8; q++)
+          v[h][q] = ok[h] && kk[h] + q < K ? Q.at(ci[h], kk[h] + q, jj[h]) : dfv{0.f, 0.f};
       }
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (!ok[h]) continue;
+        float s1, s2;
+        slice_scale(ts->eQ[jj[h]], s1, s2);
+        slice8(sb + ((long)ci[h] * MAXD + jj[h]) * TKP + kk[h], lstride, v[h], s1, s2);
+      }
+    }
   }
-  // the slices are read by TMA (async proxy)
+  // the slices are read by TMA (async proxy), which also overwrites the
+  // stage ring the exponent phase used
   asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-
 }
 
-__device__ __noinline__ void TcGemm::products(int M, int N, int K, int shift, int u0, int w0) {
+__device__ __noinline__ void TcGemm::products(int M, int N, int K, int u0, int w0) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   (void)warp;
   (void)lane;
-  const bool aborted = false;
   // ---- 3. tensor-core phase ----
   int kc[TMAXS];
 #pragma unroll
   for (int d = 0; d < TMAXS; d++) {
     int c0 = K;
-    if (d <= S - 3) {
+    if (d <= TS - 3) {
       const int lim = d == 0 ? 256 : 1024 / (d + 3);
       c0 = (lim / TBK) * TBK;
     }
     kc[d] = c0 < K ? c0 : K;
   }
   const int Mt = (M + TBM - 1) / TBM, Nt = (N + TBN - 1) / TBN;
-  if (!aborted) {
+  {
     if (warp == 0) {
       // ---------------- TMA producer ----------------
       if (lane == 0) {
@@ -281,7 +343,7 @@ __device__ __noinline__ void TcGemm::products(int M, int N, int K, int shift, in
         bool ok = true;
         for (int tile = 0; tile < Mt * Nt && ok; tile++) {
           const int m0 = (tile % Mt) * TBM, n0 = (tile / Mt) * TBN;
-          for (int d = S - 1; d >= 0 && ok; d--) {
+          for (int d = TS - 1; d >= 0 && ok; d--) {
             for (int k0 = 0; k0 < K && ok; k0 += kc[d]) {
               const int kb0 = k0 / TBK, kb1 = (min(K, k0 + kc[d]) + TBK - 1) / TBK;
               for (int kb = kb0; kb < kb1 && ok; kb++) {
@@ -314,7 +376,7 @@ __device__ __noinline__ void TcGemm::products(int M, int N, int K, int shift, in
         int u = u0, w = w0;
         bool ok = true;
         for (int tile = 0; tile < Mt * Nt && ok; tile++) {
-          for (int d = S - 1; d >= 0 && ok; d--) {
+          for (int d = TS - 1; d >= 0 && ok; d--) {
             for (int k0 = 0; k0 < K && ok; k0 += kc[d], w++) {
               const int b = w & 1;  // FP32 buffer of this chunk, free once chunk w - 2 was drained
               if (w >= 2 && !mbar_wait(smem_u32(&ts->acc_empty[b]), ((w >> 1) - 1) & 1, &ts->abort_flag, err, 22)) {
@@ -356,115 +418,101 @@ __device__ __noinline__ void TcGemm::products(int M, int N, int K, int shift, in
         if (ok && lo) ts->w = w;
       }
     } else {
-      // ---------------- epilogue: FP32 chunk -> int32 level sums (registers) -> int64 (global) ----------------
+      // ---------------- epilogue: FP32 chunk -> int32 level sums (registers) -> int64 (global) -> C ----------------
       // Warp e = warp - TEPI0 reads TMEM lane quarter warp % 4 and column half e / 4
       // (components 2h, 2h + 1): 128 int32 level sums per thread.
       const int e8 = warp - TEPI0, quarter = warp & 3, half = e8 >> 2;
       const uint32_t tb0 = ts->tmem + ((uint32_t)(quarter * 32) << 16) + half * 128;
       int w = w0;
-      bool ok = true;
       int acc[128];
-      for (int tile = 0; tile < Mt * Nt && ok; tile++) {
+      int* xt = reinterpret_cast<int*>(smem + TSTAGES * TSTAGE + e8 * TXTILE);
+      const int rr = lane >> 4, cc = lane & 15;
+      for (int tile = 0; tile < Mt * Nt; tile++) {
         const int m0 = (tile % Mt) * TBM, n0 = (tile / Mt) * TBN;
-        const int row = m0 + quarter * 32 + lane;
-        for (int d = S - 1; d >= 0 && ok; d--) {
-          const float scale = ldexpf(1.0f, 7 * (d + 2));
-          const int shd = shift - 7 * (d + 2);
-          for (int k0 = 0; k0 < K && ok; k0 += kc[d], w++) {
-            const int b = w & 1;
-            const uint32_t tb = tb0 + b * 256;
-            int have = 1;
-            if (lane == 0)
-              have = mbar_wait(smem_u32(&ts->acc_full[b]), (w >> 1) & 1, &ts->abort_flag, err, 24) ? 1 : 0;
-            have = __shfl_sync(0xffffffffu, have, 0);
-            if (!have) {
-              ok = false;
-              break;
-            }
-            fence_after();
-            const bool first = k0 == 0;
+        const int row0 = m0 + quarter * 32;  // this warp's rows row0 .. row0 + 31 (TMEM lanes)
+        for (int d = TS - 1; d >= 0; d--) {
+          // a failed wait (abort) leaves the loops at once (no path from it
+          // reads the level sums: they stay dead across the combine call)
+          if (!drain_chunk<true>(acc, w, tb0, lane, ts, err)) goto epilogue_done;
+          for (int k0 = kc[d]; k0 < K; k0 += kc[d])
+            if (!drain_chunk<false>(acc, w, tb0, lane, ts, err)) goto epilogue_done;
+          // level done: this warp's 32 rows x 128 sums go to the level's
+          // int32 plane, 16 columns at a time through the warp's shared tile
+          // (each lane writes its row, then reads lane-consecutive columns),
+          // so that every global store instruction covers two 64-byte row
+          // segments; stores only (no read-modify-write: the combine sums the
+          // levels)
 #pragma unroll
-            for (int p = 0; p < 8; p++) {
-              uint32_t f[16];
-              tmem_ld16u(tb + p * 16, f);
-              tmem_wait_ld();
+          for (int p = 0; p < 8; p++) {
+            const int c = 2 * half + (p >> 2), j = n0 + (p & 3) * 16 + cc;
+            int4* trow = reinterpret_cast<int4*>(xt + lane * TXP);
 #pragma unroll
-              for (int t = 0; t < 16; t++) {
-                const int x = __float2int_rn(__uint_as_float(f[t]) * scale);
-                acc[p * 16 + t] = first ? x : acc[p * 16 + t] + x;
-              }
-            }
-            fence_before();
+            for (int q = 0; q < 4; q++)
+              trow[q] = make_int4(acc[p * 16 + 4 * q], acc[p * 16 + 4 * q + 1], acc[p * 16 + 4 * q + 2],
+                                  acc[p * 16 + 4 * q + 3]);
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ts->acc_empty[b]));
-            if (k0 + kc[d] < K || row >= M) continue;
-            // level done: int64 accumulator (+)= int32 sum * 2^shd, this
-            // thread's row, components 2 half and 2 half + 1 (16-byte accesses;
-            // a column past N in a pair lands in the row's padding, never read)
-#pragma unroll
-            for (int p = 0; p < 4; p++) {
-              const int c = 2 * half + (p >> 1), j0 = n0 + (p & 1) * 32;
-              long long* dst = c64 + ((long)c * MAXD + row) * MAXD + j0;
-#pragma unroll
-              for (int t = 0; t < 32; t += 2) {
-                if (j0 + t >= N) break;
-                const long long x0 = (long long)acc[p * 32 + t], x1 = (long long)acc[p * 32 + t + 1];
-                longlong2 y;
-                y.x = shd >= 0 ? (x0 << shd) : ((x0 + (1LL << (-shd - 1))) >> (-shd));
-                y.y = shd >= 0 ? (x1 << shd) : ((x1 + (1LL << (-shd - 1))) >> (-shd));
-                longlong2* dp = reinterpret_cast<longlong2*>(dst + t);
-                if (d != S - 1) {
-                  const longlong2 g0 = *dp;
-                  y.x += g0.x;
-                  y.y += g0.y;
-                }
-                *dp = y;
+            int* dst = lvl + (((long)d * 4 + c) * MAXD + row0) * MAXD + j;
+            if (j < N)
+#pragma unroll 4
+              for (int i = 0; i < 16; i++) {
+                const int r = 2 * i + rr;
+                if (row0 + r < M) dst[(long)r * MAXD] = xt[r * TXP + cc];
               }
-            }
+            __syncwarp();
           }
         }
       }
+    epilogue_done:;
     }
   }
 }
 
-__device__ __noinline__ void TcGemm::combine(int M, int N, int K, int shift, const DM& C, const Epi& e,
-                                             double* norms) {
-  (void)K;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  (void)warp;
-  (void)lane;
-  fence_before();
-  __syncthreads();
-  fence_after();
-
-  // ---- 4. int64 -> df, the pass's epilogue ----
+// All level planes written: every thread takes entries (i, j) in row-major
+// order (coalesced).  An entry's TS int32 level sums are shifted to the
+// common 64-bit fixed point (value 2^(eP + eQ - shift) times the integer) and
+// summed exactly, the sum split exactly in two floats, then
+// out = ca v + sum_a ct_a aux_a + diag I is stored to C, with the stop-test
+// partials against ref.  An entry's loads precede its store (C may alias an
+// aux plane at that entry only).
+__device__ __noinline__ void TcGemm::combine(int M, int N, int shift, const DM& C, const Epi& e, double* norms) {
+  const int tid = threadIdx.x;
+  const dfv ca = e.ca, diag = e.diag;
+  const bool has_ref = e.ref != nullptr;
+  const long lplane = 4L * MAXD * MAXD;
   float nd = 0.f, nx = 0.f;
   for (long t = tid; t < (long)M * N; t += TTHREADS) {
     const int i = (int)(t / N), j = (int)(t % N);
     const int ex = ts->eP[i] + ts->eQ[j] - shift;
-    // loads first (the stores to C may alias an aux plane at this very entry only)
-    long long q[4];
+    int L[4][TS];
     dfv ax[3][4], rf[4];
 #pragma unroll
-    for (int c = 0; c < 4; c++) q[c] = c64[((long)c * MAXD + i) * MAXD + j];
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+      for (int d = 0; d < TS; d++) L[c][d] = lvl[d * lplane + ((long)c * MAXD + i) * MAXD + j];
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int c = 0; c < 4; c++) ax[a][c] = e.aux[a] ? e.aux[a]->at(c, i, j) : dfv{0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < 4; c++) rf[c] = e.ref ? e.ref->at(c, i, j) : dfv{0.f, 0.f};
+    for (int c = 0; c < 4; c++) rf[c] = has_ref ? e.ref->at(c, i, j) : dfv{0.f, 0.f};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-      const float h = __ll2float_rn(q[c]);
-      const float l = __ll2float_rn(q[c] - (long long)h);
-      dfv v = df_quick(ldexpf(h, ex), ldexpf(l, ex));
-      v = df_mul(e.ca, v);
+      long long q = 0;
+#pragma unroll
+      for (int d = 0; d < TS; d++) {
+        const int shd = shift - 7 * (d + 2);
+        const long long x = (long long)L[c][d];
+        q += shd >= 0 ? (x << shd) : ((x + (1LL << (-shd - 1))) >> (-shd));
+      }
+      const float hq = __ll2float_rn(q);
+      const float lq = __ll2float_rn(q - (long long)hq);
+      dfv v = df_quick(scale2(hq, ex), scale2(lq, ex));
+      v = df_mul(ca, v);
 #pragma unroll
       for (int a = 0; a < 3; a++)
         if (e.aux[a]) v = df_fma(e.ct[a], ax[a][c], v);
-      if (c == 0 && i == j) v = df_add(v, e.diag);
-      if (e.ref) {
+      if (c == 0 && i == j) v = df_add(v, diag);
+      if (has_ref) {
         const dfv dd = df_add(v, df_neg(rf[c]));
         nd += dd.hi * dd.hi;
         nx += v.hi * v.hi;
@@ -472,14 +520,13 @@ __device__ __noinline__ void TcGemm::combine(int M, int N, int K, int shift, con
       C.at(c, i, j) = v;
     }
   }
-  if (e.ref) {
+  if (has_ref) {
     norms[0] = block_sum((double)nd, *sh, 0);
     norms[1] = block_sum((double)nx, *sh, 1);
   } else {
     __syncthreads();
   }
 }
-
 
 __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const DM& C, const Epi& e, double* norms) {
   const int M = P.rows, K = P.cols, N = Q.cols;
@@ -490,8 +537,12 @@ __device__ __noinline__ void TcGemm::operator()(const DM& P, const DM& Q, const 
   const int shift = 61 - lg;  // |sum| < 4K in normalized units
   exponents(P, Q);
   slices(P, Q);
-  if (!aborted) products(M, N, K, shift, u0, w0);
-  combine(M, N, K, shift, C, e, norms);
+  if (!aborted) products(M, N, K, u0, w0);
+  // every level plane written and visible to every thread
+  fence_before();
+  __syncthreads();
+  fence_after();
+  combine(M, N, shift, C, e, norms);
 }
 
 __global__ void __launch_bounds__(TTHREADS, 1) k_batched_tc(BatchParams P) {
@@ -533,8 +584,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_batched_tc(BatchParams P) {
   g.mapB = P.tc_maps + 2 * blockIdx.x + 1;
   g.sa = reinterpret_cast<bf16*>(slot);
   g.sb = reinterpret_cast<bf16*>(slot + TC_SLICE_BYTES);
-  g.c64 = reinterpret_cast<long long*>(slot + 2 * TC_SLICE_BYTES);
-  g.S = P.tc_slices;
+  g.lvl = reinterpret_cast<int*>(slot + 2 * TC_SLICE_BYTES);
   g.err = P.err;
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(g.mapA)) : "memory");
@@ -571,7 +621,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_batched_tc(BatchParams P) {
 }  // namespace
 
 cudaError_t batched_launch_tc(int slots, const BatchParams& P, cudaStream_t st) {
-  if (P.tc_slices < 2 || P.tc_slices > TMAXS || !P.tc_maps || !P.tc_ws || !P.err) return cudaErrorInvalidValue;
+  if (P.tc_slices != TS || !P.tc_maps || !P.tc_ws || !P.err) return cudaErrorInvalidValue;
   static std::atomic<unsigned long long> attr_done{0};
   if (cudaError_t e = ensure_smem_attr(k_batched_tc, TSMEM, attr_done)) return e;
   k_batched_tc<<<slots, TTHREADS, TSMEM, st>>>(P);

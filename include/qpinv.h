@@ -185,6 +185,9 @@ typedef struct {
   double batched_tune_ms;     /* time spent autotuning batched tiles */
   long long batched_graph_replays; /* batched calls served by replaying a captured CUDA graph */
   long long fused_epilogues;       /* tensor-core products whose combine pass ran in the GEMM epilogue */
+  long long penrose_reused;        /* Penrose passes that reused the residual I - AX (or I - XA) the last
+                                      iteration had formed for the returned X with FP64 masters and
+                                      FP64-accurate products (one product fewer) */
 } qpinv_stats;
 
 typedef struct qpinv_ctx qpinv_ctx;

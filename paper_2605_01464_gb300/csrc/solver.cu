@@ -282,6 +282,11 @@ struct Solver {
   int xSp = 0;            // ... of the update product in a polish step (0: xS)
   bool pre_res = false;   // pre_R is the residual of X[cur], computed ahead of the step
   QMat pre_R;
+  // The buffer "R" holds I - (residual product of X[res_cur]) with FP64
+  // masters and FP64-accurate products (-1: it does not): the Penrose pass
+  // then reuses it instead of forming that side's product again.
+  int res_cur = -1;
+  QMat res_R;
   long long gemms = 0;
   QMat A, X[2];
   int cur = 0;
@@ -686,6 +691,11 @@ struct Solver {
     CombineArgs a = base_args(s, s, nullptr);
     out(a, R, forms, -1.0, 1.0);
     res_run(Y, a, norm, 4);
+    if (strcmp(name, "R") == 0) {
+      const bool exact = dbl && (xmode == PM_F64 || (xmode == PM_EMU && xS >= 8));
+      res_cur = exact && &Y == &X[cur] ? cur : -1;
+      if (res_cur >= 0) res_R = R;
+    }
     return R;
   }
 
@@ -994,7 +1004,11 @@ double antiherm2(qpinv_ctx* c, const QMat& M) {
 
 // Penrose residuals (Sec. 4) for A (m x n) and X (n x m) FP64 masters, with
 // FP64-accurate products (mode PM_F64 or PM_EMU with 8 slices) and FP64 norms.
-void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, double* Er, long long* gemms) {
+// Rgiven: I - AX (right) or I - XA (left, given_left) of this X, already
+// formed with FP64 masters and FP64-accurate products (or null): that side's
+// product is not formed again (the norms do not depend on the sign).
+void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, double* Er, long long* gemms,
+             const QMat* Rgiven = nullptr, bool given_left = false) {
   // E1 = ||AXA - A|| = ||(AX - I) A||, E2 = ||XAX - X|| = ||(XA - I) X||,
   // E3 = ||(AX)^H - AX|| = ||Rr^H - Rr|| (Rr = AX - I), E4 likewise with XA.
   // Every product is FP64-accurate: AX - I is not small when A is
@@ -1013,8 +1027,19 @@ void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, do
     S.out(a, Out, "f", 1.0, diag);
     S.run(a);
   };
-  product(A, X, Rr, 8, -1.0);
-  product(X, A, Rl, 8, -1.0);
+  double sr = 1.0, sl = 1.0;  // Rr = sr (AX - I), Rl = sl (XA - I)
+  if (Rgiven && !given_left) {
+    Rr = *Rgiven;
+    sr = -1.0;
+  } else {
+    product(A, X, Rr, 8, -1.0);
+  }
+  if (Rgiven && given_left) {
+    Rl = *Rgiven;
+    sl = -1.0;
+  } else {
+    product(X, A, Rl, 8, -1.0);
+  }
   Planes<const double> a = dview(A), x = dview(X);
   const double fa = std::sqrt(fro2(c, a, nullptr, m, n)), fx = std::sqrt(fro2(c, x, nullptr, n, m));
   // ||R Q||_F with R = AX - I or XA - I.  When R is small (square
@@ -1039,16 +1064,16 @@ void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, do
   if (gemms) *gemms += S.gemms;
   E[2] = std::sqrt(antiherm2(c, Rr));
   E[3] = std::sqrt(antiherm2(c, Rl));
-  // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from AX = Rr + I instead
+  // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from AX = sr Rr + I instead
   QMat AX = mat(c, "pAX", m, m, MST_D, false, false), XA = mat(c, "pXA", n, n, MST_D, false, false);
   {
     CombineArgs t = S.base_args(m, m, nullptr);
     S.aux(t, 0, Rr);
-    S.out(t, AX, "f", 0.0, 1.0).caux[0] = 1.0;
+    S.out(t, AX, "f", 0.0, 1.0).caux[0] = sr;
     S.run(t);
     CombineArgs u = S.base_args(n, n, nullptr);
     S.aux(u, 0, Rl);
-    S.out(u, XA, "f", 0.0, 1.0).caux[0] = 1.0;
+    S.out(u, XA, "f", 0.0, 1.0).caux[0] = sl;
     S.run(u);
   }
   const double nr[4] = {fa, fx, std::sqrt(fro2(c, dview(AX), nullptr, m, m)),
@@ -1568,7 +1593,9 @@ int qpinv_solve(qpinv_ctx* c, void* stream, int m, int n, const double* const A[
     if (o.precision == QPINV_PREC_TC && m != n && res.status != QPINV_DIVERGED) S.range_projection();
     QMat& Xf = S.X[S.cur];
     if (o.penrose) {
-      penrose(c, S.A, Xf, fp64 ? PM_F64 : PM_EMU, res.E, res.E_rel, nullptr);
+      const bool reuse = S.res_cur == S.cur;
+      penrose(c, S.A, Xf, fp64 ? PM_F64 : PM_EMU, res.E, res.E_rel, nullptr, reuse ? &S.res_R : nullptr, S.left);
+      if (reuse) c->stats.penrose_reused++;
       if (!fp64) check_kernel_error(c);
     }
     res.gemms = gemms_before + S.gemms;

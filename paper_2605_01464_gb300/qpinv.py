@@ -56,7 +56,8 @@ class qpinv_stats(ctypes.Structure):
                 ("emu_gemm_launches", ctypes.c_longlong), ("emu_gemm_ms", ctypes.c_double),
                 ("emu_gemm_flops", ctypes.c_double), ("emu_gemm_flops_issued", ctypes.c_double),
                 ("batched_tile", ctypes.c_longlong), ("batched_tune_ms", ctypes.c_double),
-                ("batched_graph_replays", ctypes.c_longlong), ("fused_epilogues", ctypes.c_longlong)]
+                ("batched_graph_replays", ctypes.c_longlong), ("fused_epilogues", ctypes.c_longlong),
+                ("penrose_reused", ctypes.c_longlong)]
 
 
 class qpinv_cur_result(ctypes.Structure):

@@ -300,3 +300,26 @@ def test_fused_epilogue_matches_separate_combine(ctx, method, N):
     assert rel(X1, X2) <= 1e-6, rel(X1, X2)
     Xo, _ = oracle.solve(A, method, tol=1e-6, max_iter=60, N=N, order=7)
     assert rel(X1, Xo) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["emu", "fp64"])
+@pytest.mark.parametrize("shape", [(96, 64), (64, 96)])
+def test_penrose_reuses_final_residual(ctx, precision, shape):
+    """A solve whose stop rule rejects its last step (PLATEAU at an
+    unreachable tolerance) returns X_j, whose residual I - AX (I - XA on the
+    left side) that step formed with FP64-accurate products: the Penrose pass
+    takes it instead of forming the product again, and its E1..E4 equal the
+    stand-alone Penrose evaluation of the returned X (both sides formed)."""
+    m, n = shape
+    A = I.gaussian_quaternion(m, n, 23)
+    ctx.configure(precision=precision)
+    ctx.reset_stats()
+    X, info = ctx.solve(dev(A), "qhpi19", tol=1e-30, max_iter=100)
+    st = ctx.stats()
+    assert info["status"] == "plateau", info
+    assert st["penrose_reused"] == 1, st
+    E, _ = ctx.penrose(dev(A), X)
+    for k in range(4):
+        assert abs(info["E"][k] - E[k]) <= 1e-12 * max(E[k], 1e-300) + 1e-300, (k, info["E"], E)
+    Eo, Ro = oracle.penrose(A, X.cpu().numpy())
+    assert max(Ro) <= 1e-12, Ro

@@ -116,14 +116,43 @@ struct Coef {
   dfv v;
 };
 
-// Output of a fused CTA GEMM pass: out = ca * (P Q) + sum_t ct * aux_t + diag * I.
+// Output of a fused CTA GEMM pass: out = ca * (P Q) + sum_t ct * aux_t + diag * I,
+// and up to two more outputs formed from it: xo_k = out + sum_t cx_k,t * aux_t
+// (the polynomial blocks that would otherwise take their own elementwise
+// passes).  A zero coefficient skips its term.
 struct Epi {
   dfv ca = {1.f, 0.f};
   const DM* aux[3] = {nullptr, nullptr, nullptr};
   dfv ct[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   dfv diag = {0.f, 0.f};
   const DM* ref = nullptr;  // if set: accumulate ||out - ref||^2 and ||out||^2
+  int nx = 0;
+  const DM* xo[2] = {nullptr, nullptr};
+  dfv cx[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
 };
+__device__ __forceinline__ bool df_nonzero(dfv x) { return x.hi != 0.f || x.lo != 0.f; }
+
+// The pass's epilogue for one entry (i, j) of component c (tensor-core
+// engine): v = ca acc + sum ct aux + diag, stored to C, and the extra
+// outputs; av are the aux
+// values at (c, i, j) (loaded before any store: an output may alias an aux
+// plane at this entry only).  Returns v.
+__device__ __forceinline__ dfv epi_entry(const Epi& e, dfv acc, const dfv* av, int c, int i, int j, const DM& C) {
+  dfv v = df_mul(e.ca, acc);
+#pragma unroll
+  for (int t = 0; t < 3; t++)
+    if (e.aux[t] && df_nonzero(e.ct[t])) v = df_fma(e.ct[t], av[t], v);
+  if (c == 0 && i == j) v = df_add(v, e.diag);
+  for (int k = 0; k < e.nx; k++) {
+    dfv w = v;
+#pragma unroll
+    for (int t = 0; t < 3; t++)
+      if (e.aux[t] && df_nonzero(e.cx[k][t])) w = df_fma(e.cx[k][t], av[t], w);
+    e.xo[k]->at(c, i, j) = w;
+  }
+  C.at(c, i, j) = v;
+  return v;
+}
 
 }  // namespace
 
@@ -201,7 +230,7 @@ __device__ double block_sum(double v, Shared& sh, int slot) {
 // C (P.rows x Q.cols) = epilogue(P Q), quaternion; every thread of the CTA calls it.
 // Returns (in every thread) the two norms of Epi::ref, if requested.
 template <int RM, int RN>
-__device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Shared& sh, SimtTiles& tl,
+__device__ __noinline__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Shared& sh, SimtTiles& tl,
                          double* norms) {
   constexpr int BM = 16 * RM, BN = 16 * RN;
   const int M = P.rows, K = P.cols, N = Q.cols;
@@ -285,7 +314,7 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
             for (int c = 0; c < 4; c++) {
               dfv v = df_mul(e.ca, df_norm(acc[r][q][c]));
               for (int t = 0; t < 3; t++)
-                if (e.aux[t]) v = df_fma(e.ct[t], e.aux[t]->at(c, gi, gj), v);
+                if (e.aux[t] && df_nonzero(e.ct[t])) v = df_fma(e.ct[t], e.aux[t]->at(c, gi, gj), v);
               if (c == 0 && gi == gj) v = df_add(v, e.diag);
               if (e.ref) {
                 const dfv d = df_add(v, df_neg(e.ref->at(c, gi, gj)));
@@ -296,6 +325,23 @@ __device__ void cta_gemm(const DM& P, const DM& Q, const DM& C, const Epi& e, Sh
             }
           }
         }
+    }
+  }
+  if (e.nx) {
+    // the extra outputs from the finished main output (one pass: their
+    // code stays out of the register-tile epilogue above)
+    __syncthreads();
+    for (long t = threadIdx.x; t < (long)M * N; t += blockDim.x) {
+      const int i = (int)(t / N), j = (int)(t % N);
+      for (int c = 0; c < 4; c++) {
+        const dfv v = C.at(c, i, j);
+        for (int k = 0; k < e.nx; k++) {
+          dfv w = v;
+          for (int u = 0; u < 3; u++)
+            if (e.aux[u] && df_nonzero(e.cx[k][u])) w = df_fma(e.cx[k][u], e.aux[u]->at(c, i, j), w);
+          e.xo[k]->at(c, i, j) = w;
+        }
+      }
     }
   }
   if (e.ref) {
@@ -425,9 +471,16 @@ struct Solve {
     const DM Fa = c.buf(B_FA, s, s), Fb = c.buf(B_FB, s, s), q = c.buf(B_U, s, s), t = c.buf(B_T, s, s);
     residual(X[cur], R);
     gemm(R, R, R2, Epi());
-    gemm(R2, R2, R4, Epi());
-    cta_axpy(R2, Fa, dc(b1), &R4, dc(1.0), dc(0.0));
-    cta_axpy(R2, Fb, dc(b2), &R4, dc(1.0), dc(0.0));
+    {
+      Epi e;  // R4 = R2 R2, with Fa = R4 + b1 R2 and Fb = R4 + b2 R2
+      e.aux[0] = &R2;
+      e.nx = 2;
+      e.xo[0] = &Fa;
+      e.cx[0][0] = dc(b1);
+      e.xo[1] = &Fb;
+      e.cx[1][0] = dc(b2);
+      gemm(R2, R2, R4, e);
+    }
     {
       Epi e;  // q = Fa Fb + (b1 + b2) R2 + 2 R4
       e.aux[0] = &R2;
@@ -456,26 +509,38 @@ struct Solve {
     const DM w = c.buf(B_W, s, s), g = c.buf(B_G, s, s), t = c.buf(B_T, s, s);
     residual(X[cur], R);
     {
-      Epi e;  // R2 = R R
+      Epi e;  // R2 = R R, with S = R2 + R
+      e.aux[0] = &R;
+      e.nx = 1;
+      e.xo[0] = &S;
+      e.cx[0][0] = dc(1.0);
       gemm(R, R, R2, e);
     }
-    cta_axpy(R, S, dc(1.0), &R2, dc(1.0), dc(0.0));  // S = R + R2
-    gemm(R2, R2, R4, Epi());
-    cta_axpy(R2, Fa, dc(d1), &R4, dc(1.0), dc(0.0));
-    cta_axpy(R2, Fb, dc(d2), &R4, dc(1.0), dc(0.0));
     {
-      Epi e;  // u = Fa Fb + (d1 + d2) R2 + 2 R4
+      Epi e;  // R4 = R2 R2, with Fa = R4 + d1 R2 and Fb = R4 + d2 R2
+      e.aux[0] = &R2;
+      e.nx = 2;
+      e.xo[0] = &Fa;
+      e.cx[0][0] = dc(d1);
+      e.xo[1] = &Fb;
+      e.cx[1][0] = dc(d2);
+      gemm(R2, R2, R4, e);
+    }
+    {
+      // u = Fa Fb + (d1 + d2) R2 + 2 R4, with v = u + d3 R2 and
+      // w = u + e1 R2 + e2 R4
+      Epi e;
       e.aux[0] = &R2;
       e.ct[0] = dc(d1 + d2);
       e.aux[1] = &R4;
       e.ct[1] = dc(2.0);
+      e.nx = 2;
+      e.xo[0] = &v;
+      e.cx[0][0] = dc(d3);
+      e.xo[1] = &w;
+      e.cx[1][0] = dc(e1);
+      e.cx[1][1] = dc(e2);
       gemm(Fa, Fb, u, e);
-    }
-    cta_axpy(u, v, dc(1.0), &R2, dc(d3), dc(0.0));  // v = u + d3 R2
-    {
-      // w = u + e1 R2 + e2 R4
-      cta_axpy(u, w, dc(1.0), &R2, dc(e1), dc(0.0));
-      cta_axpy(w, w, dc(1.0), &R4, dc(e2), dc(0.0));
     }
     {
       Epi e;  // g = v w + 2 u + (d3 + e1 + c1) R2 + (e2 + c2) R4

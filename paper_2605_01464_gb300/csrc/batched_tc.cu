@@ -476,7 +476,6 @@ __device__ __noinline__ void TcGemm::products(int M, int N, int K, int u0, int w
 // aux plane at that entry only).
 __device__ __noinline__ void TcGemm::combine(int M, int N, int shift, const DM& C, const Epi& e, double* norms) {
   const int tid = threadIdx.x;
-  const dfv ca = e.ca, diag = e.diag;
   const bool has_ref = e.ref != nullptr;
   const long lplane = 4L * MAXD * MAXD;
   float nd = 0.f, nx = 0.f;
@@ -484,7 +483,7 @@ __device__ __noinline__ void TcGemm::combine(int M, int N, int shift, const DM& 
     const int i = (int)(t / N), j = (int)(t % N);
     const int ex = ts->eP[i] + ts->eQ[j] - shift;
     int L[4][TS];
-    dfv ax[3][4], rf[4];
+    dfv ax[4][3], rf[4];
 #pragma unroll
     for (int c = 0; c < 4; c++)
 #pragma unroll
@@ -492,7 +491,7 @@ __device__ __noinline__ void TcGemm::combine(int M, int N, int shift, const DM& 
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
-      for (int c = 0; c < 4; c++) ax[a][c] = e.aux[a] ? e.aux[a]->at(c, i, j) : dfv{0.f, 0.f};
+      for (int c = 0; c < 4; c++) ax[c][a] = e.aux[a] ? e.aux[a]->at(c, i, j) : dfv{0.f, 0.f};
 #pragma unroll
     for (int c = 0; c < 4; c++) rf[c] = has_ref ? e.ref->at(c, i, j) : dfv{0.f, 0.f};
 #pragma unroll
@@ -506,18 +505,12 @@ __device__ __noinline__ void TcGemm::combine(int M, int N, int shift, const DM& 
       }
       const float hq = __ll2float_rn(q);
       const float lq = __ll2float_rn(q - (long long)hq);
-      dfv v = df_quick(scale2(hq, ex), scale2(lq, ex));
-      v = df_mul(ca, v);
-#pragma unroll
-      for (int a = 0; a < 3; a++)
-        if (e.aux[a]) v = df_fma(e.ct[a], ax[a][c], v);
-      if (c == 0 && i == j) v = df_add(v, diag);
+      const dfv v = epi_entry(e, df_quick(scale2(hq, ex), scale2(lq, ex)), ax[c], c, i, j, C);
       if (has_ref) {
         const dfv dd = df_add(v, df_neg(rf[c]));
         nd += dd.hi * dd.hi;
         nx += v.hi * v.hi;
       }
-      C.at(c, i, j) = v;
     }
   }
   if (has_ref) {

@@ -96,6 +96,29 @@ __device__ __forceinline__ void slice_store(bf16* base, long idx, long lstride, 
   base[idx] = __float2bfloat16_rn(ldexpf((float)F, -7));
 }
 
+// q 2^e as a double, rounded to nearest (ties to even) from the integer bits:
+// the same value as ldexp((double)q, e), without FP64 arithmetic (GB300's
+// FP64 rate is a small fraction of its integer rate).  Results below the
+// normal range or above the finite range take ldexp.
+__device__ __forceinline__ double i64_scaled(long long q, int e) {
+  if (q == 0) return 0.0;
+  const unsigned long long sgn = q < 0 ? (1ull << 63) : 0ull;
+  unsigned long long mag = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  const int lz = __clzll((long long)mag);
+  mag <<= lz;  // leading one at bit 63
+  unsigned long long m = mag >> 11;  // 53 significant bits
+  const unsigned long long rem = mag & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) m++;
+  int ex = 63 - lz + e;  // value = m 2^(ex - 52)
+  if (m >> 53) {
+    m >>= 1;
+    ex++;
+  }
+  const int biased = ex + 1023;
+  if (biased <= 0 || biased >= 2047) return ldexp((double)q, e);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)biased << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
 template <typename T>
 __device__ __forceinline__ T acc_value(const CombineArgs& a, int c, int i, int j) {
   const long off = c * a.ps_acc + (long)i * a.ld_acc + j;
@@ -104,9 +127,17 @@ __device__ __forceinline__ T acc_value(const CombineArgs& a, int c, int i, int j
     const long long q = ((const long long*)a.acc)[off] + (a.acc2 ? a.acc2[off] : 0LL);
     const int e = a.acc_erow[i] + a.acc_ecol[j] - a.acc_shift;
     if (sizeof(T) == 4) return (T)ldexpf((float)q, e);
-    return (T)ldexp((double)q, e);
+    return (T)i64_scaled(q, e);
   }
   return (T)((const float*)a.acc)[off];
+}
+
+// cacc x for cacc = +-1 without arithmetic (a sign flip), else the product.
+template <typename T>
+__device__ __forceinline__ T times_coef(T x, T cacc) {
+  if (cacc == (T)1) return x;
+  if (cacc == (T)-1) return -x;
+  return cacc * x;
 }
 
 // One 32x32 tile per block; threads (tx, ty), tid = ty * 32 + tx.
@@ -127,7 +158,7 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
       T v[4] = {0, 0, 0, 0};
       if (i < a.rows && j < a.cols) {
         if (a.acc && O.cacc != 0.0)
-          for (int c = 0; c < 4; c++) v[c] = cacc * acc_value<T>(a, c, i, j);
+          for (int c = 0; c < 4; c++) v[c] = times_coef<T>(acc_value<T>(a, c, i, j), cacc);
         for (int t = 0; t < 4; t++) {
           if (!a.aux[t] || O.caux[t] == 0.0) continue;
           const T* ap = (const T*)a.aux[t];
@@ -138,9 +169,11 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
         if (o == 0 && a.partials) {
           const T* x0p = (const T*)a.aux[0];
           for (int c = 0; c < 4; c++) {
-            const T x0 = x0p ? x0p[c * a.ps_aux[0] + (long)i * a.ld_aux[0] + j] : (T)0;
-            s_dx += (v[c] - x0) * (v[c] - x0);
             s_x += v[c] * v[c];
+            if (x0p) {
+              const T dx = v[c] - x0p[c * a.ps_aux[0] + (long)i * a.ld_aux[0] + j];
+              s_dx += dx * dx;
+            }
             s_bad += isfinite(v[c]) ? 0 : 1;
           }
         }
@@ -174,6 +207,7 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
     }
   }
   if (a.partials) {
+    if (!a.aux[0]) s_dx = s_x;  // ||v - 0||^2
     const long b = (long)blockIdx.y * gridDim.x + blockIdx.x;
     const double t0 = block_sum((double)s_dx, red);
     const double t1 = block_sum((double)s_x, red);

@@ -266,7 +266,8 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    mats = inputs.pure_quaternion_batch(4096, seed=3 + 1000 * rank)
+    count = args.batch_count
+    mats = inputs.pure_quaternion_batch(count, seed=3 + 1000 * rank)
     As = [torch.from_numpy(a).cuda() for a in mats]
     Xs = [torch.empty((4, a.shape[2], a.shape[1]), dtype=torch.float64, device="cuda") for a in As]
     ctx = qpinv.Context(local)
@@ -282,7 +283,7 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
         for _ in range(args.steps):
             _, infos = ctx.solve_batched(As, args.method, tol=args.tol, max_iter=200, Xs=Xs)
         torch.cuda.synchronize()
-    dt, solves = reduce_timing(time.perf_counter() - t0, 4096 * args.steps, dist, "cuda")
+    dt, solves = reduce_timing(time.perf_counter() - t0, count * args.steps, dist, "cuda")
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -304,7 +305,7 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
-        sample = list(range(0, 4096, 256))  # 16 evenly spaced blocks
+        sample = list(range(0, count, max(1, count // 16)))[:16]  # 16 evenly spaced blocks
         t0 = time.perf_counter()
         errs = []
         for b in sample:
@@ -321,9 +322,10 @@ def bench_batched(args, torch, qpinv, world=1, rank=0, local=0):
                       "higher_is_better": True, "scaling": "weak",
                       "dtype": "df32 masters (double-FP32); tc engine: exact 7-bit BF16 slices",
                       "data": "synthetic",
-                      "config": {"workload": "4096 pure-quaternion blocks, m, n ~ U[16,256], rank ~ U[4,min(m,n)], "
+                      "config": {"workload": "%d pure-quaternion blocks, m, n ~ U[16,256], rank ~ U[4,min(m,n)], "
                                              "seed 3, %s, rel. tol %g, one persistent kernel per step replayed as a "
-                                             "captured CUDA graph, autotuned CTA GEMM tile" % (args.method, args.tol),
+                                             "captured CUDA graph, autotuned CTA GEMM tile"
+                                             % (count, args.method, args.tol),
                                  "tile": BATCH_ENGINES[st["batched_tile"]],
                                  "autotune_ms": tune_ms, "graph_replays": st["batched_graph_replays"]},
                       "gpu_launches": st["kernel_launches"], "roofline": roof, "cpu_baseline": cpu,
@@ -925,6 +927,8 @@ def main():
                          "cur: CUR image completion (Sec. 5.1); filter: Lorenz signal filtering (Sec. 5.2); "
                          "krylov: QSAI-preconditioned global Krylov solvers (Sec. 3.5)")
     ap.add_argument("--train-count", type=int, default=20000, help="--workload learned: training matrices")
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="--workload batched: blocks per step (4096 is the workload; fewer only for profiling)")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="device that builds the synthetic input (cpu under profilers)")
     args = ap.parse_args()

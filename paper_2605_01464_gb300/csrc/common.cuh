@@ -178,8 +178,9 @@ struct TcGemmArgs {
 cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);
 
 // FP64-accurate product from S exact slices per operand in one launch
-// (qgemm_emu.cu): C64 += sum over levels d < S of the level-d slice products,
-// in 64-bit fixed point (value * 2^shift).  kc[d] = K chunk of level d
+// (qgemm_emu.cu): C64 (+ C64b) = sum over levels d < S of the level-d slice
+// products, in 64-bit fixed point (value * 2^shift); the accumulators are
+// written, not added to (no clearing needed).  kc[d] = K chunk of level d
 // (multiple of 32, or >= K), short enough that every FP32 partial sum of the
 // level is exact.  emu_fused_ok(K, S) says whether K is small enough for the
 // kernel's int32 per-level sums.

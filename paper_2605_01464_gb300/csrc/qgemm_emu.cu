@@ -21,7 +21,8 @@
 // registers (128 per thread), then releases the buffer.  At the end of a
 // level the int32 sums are shifted to the common 64-bit fixed point and
 // added to the global int64 accumulator of the item's group (each thread its
-// own row segment, 16-byte accesses).  Global traffic per product is one
+// own row segment, 16-byte accesses; the group's first level stores, so the
+// accumulators need no clearing).  Global traffic per product is one
 // read-modify-write of an accumulator per level instead of one per chunk, and
 // there is a single launch per product.
 //
@@ -88,16 +89,17 @@ __device__ __forceinline__ void tile_origin(const EParams& P, int t, int& m0, in
   n0 = (local / gm) * EBN;
 }
 
-// int64 += v (two columns when both exist and the address is 16-byte aligned).
-__device__ __forceinline__ void add64_pair(long long* dst, long long v0, long long v1, bool two) {
+// int64 += v, or = v for the group's first level (two columns when both
+// exist and the address is 16-byte aligned).
+__device__ __forceinline__ void add64_pair(long long* dst, long long v0, long long v1, bool two, bool first) {
   if (two && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-    longlong2 g = *reinterpret_cast<longlong2*>(dst);
+    longlong2 g = first ? make_longlong2(0, 0) : *reinterpret_cast<longlong2*>(dst);
     g.x += v0;
     g.y += v1;
     *reinterpret_cast<longlong2*>(dst) = g;
   } else {
-    dst[0] += v0;
-    if (two) dst[1] += v1;
+    dst[0] = first ? v0 : dst[0] + v0;
+    if (two) dst[1] = first ? v1 : dst[1] + v1;
   }
 }
 
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(ETHREADS, 1)
             const long long x0 = (long long)acc[p * 32 + t], x1 = (long long)acc[p * 32 + t + 1];
             const long long y0 = sh >= 0 ? (x0 << sh) : ((x0 + (1LL << (-sh - 1))) >> (-sh));
             const long long y1 = sh >= 0 ? (x1 << sh) : ((x1 + (1LL << (-sh - 1))) >> (-sh));
-            add64_pair(dst + t, y0, y1, j0 + t + 1 < P.N);
+            add64_pair(dst + t, y0, y1, j0 + t + 1 < P.N, li == 0);
           }
         }
       }

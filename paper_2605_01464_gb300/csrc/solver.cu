@@ -477,7 +477,6 @@ struct Solver {
             [&] { return launch_slice_cols(fview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
     }
     long long* acc = (long long*)buf(c, "emu.acc", sizeof(long long) * 4 * (size_t)M * N + 64);
-    ck(c, cudaMemsetAsync(acc, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");
     int lg = 0;
     while ((1L << lg) < 4L * K) lg++;
     const int shift = 61 - lg;  // |sum| < 4K in normalized units: no int64 overflow
@@ -512,8 +511,8 @@ struct Solver {
         }
       }
       // half of the levels go to a second accumulator (see qgemm_emu.cu)
+      // (each group's first level stores: neither accumulator needs clearing)
       long long* acc2 = (long long*)buf(c, "emu.acc2", sizeof(long long) * 4 * (size_t)M * N + 64);
-      ck(c, cudaMemsetAsync(acc2, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");
       g.C64 = acc;
       g.C64b = S >= 2 ? acc2 : nullptr;
       g.ld64 = N;
@@ -525,6 +524,7 @@ struct Solver {
       r.p2 = g.C64b;
       return r;
     }
+    ck(c, cudaMemsetAsync(acc, 0, sizeof(long long) * 4 * (size_t)M * N, c->st), "memset");
     for (int hi = S - 1; hi >= 0; hi -= 2) {
       const int lo = hi - 1;  // second level of the launch (-1: none)
       TcGemmArgs g;

@@ -31,9 +31,10 @@
 // Roles inside a product (352 threads): warp 0 lane 0 TMA, warps 1-2 lane 0
 // MMA (components 0-1 and 2-3; warp 1 owns TMEM: 512 columns, two FP32 chunk
 // buffers), warps 3-10 the TMEM epilogue (TMEM lane quarter = warp % 4,
-// column half = (warp - 3) / 4); exponents and slicing use all warps.  mbarrier phases continue across products.  Every
-// wait is bounded (2 s): on expiry the kernel raises an error word, stops
-// issuing tensor-core work, drains its copies and frees TMEM.
+// column half = (warp - 3) / 4); exponents, slicing and the combine use all
+// warps.  mbarrier phases continue across products.  Every wait is bounded
+// (2 s): on expiry the kernel raises an error word, stops issuing tensor-core
+// work, drains its copies and frees TMEM.
 #define QP_BATCHED_TILE 5
 #define QP_BATCHED_TC_UNIT 1
 #include "batched_impl.cuh"
@@ -188,7 +189,8 @@ __device__ __forceinline__ bool drain_chunk(int (&acc)[128], int& w, uint32_t tb
 struct TcGemm {
   Shared* sh;
   TcShared* ts;
-  uint8_t* smem;  // 1024-aligned: TSTAGES stages (the first doubles as staging outside the tensor-core phase)
+  uint8_t* smem;  // 1024-aligned: TSTAGES stages (the first doubles as the exponent staging), then the
+                  // epilogue warps' transposition tiles
   const CUtensorMap* mapA;
   const CUtensorMap* mapB;
   bf16* sa;  // A-form slices [TMAXS][4][MAXD][TKP]

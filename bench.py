@@ -177,6 +177,7 @@ def kernel_qgemm(args, torch, qpinv):
     A = torch.from_numpy(inputs.gaussian_quaternion(n, n, 21)).cuda()
     B = torch.from_numpy(inputs.gaussian_quaternion(n, n, 22)).cuda()
     ctx = qpinv.Context(0, profile=True)
+    ctx.configure(emu_pair={"auto": "auto", "0": False, "1": True}[args.emu_pair])
     prec = args.gemm_precision
     for _ in range(args.warmup):
         ctx.qgemm(A, B, precision=prec, split_level=args.split)
@@ -191,7 +192,11 @@ def kernel_qgemm(args, torch, qpinv):
     key = "emu" if st["emu_gemm_launches"] else "tc"
     launches = max(st["%s_gemm_launches" % key], 1)
     gms = st["%s_gemm_ms" % key]
-    print(json.dumps({"kernel": "k_qgemm_emu" if key == "emu" else "k_qgemm_tc", "n": n, "precision": prec,
+    kname = "k_qgemm_tc"
+    if key == "emu":
+        kname = "k_qgemm_emu_pair" if (args.emu_pair == "1" or (args.emu_pair == "auto" and n ** 3 > 2 * 2048 ** 3)) \
+            else "k_qgemm_emu"
+    print(json.dumps({"kernel": kname, "n": n, "precision": prec,
                       "split": args.split, "launches_per_product": launches / args.steps, "ms_per_launch": gms / launches,
                       "gemm_ms_per_product": gms / args.steps,
                       "all_kernels_ms_per_product": (gms + st["ew_ms"]) / args.steps,
@@ -919,6 +924,8 @@ def main():
     ap.add_argument("--split", type=int, default=1,
                     help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
     ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
+    ap.add_argument("--emu-pair", default="auto", choices=["auto", "0", "1"],
+                    help="--kernel qgemm: exact-slice products on SM pairs (auto: for products above 2 * 2048^3)")
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "batched", "rankdef", "learned", "hyper", "cur", "filter", "krylov"],
                     help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "

@@ -138,6 +138,11 @@ typedef struct {
   int fuse_epilogue; /* 1 (default): the combine pass after a BF16 tensor-core product (residual
                         R = I - A X, the polynomial blocks in R, the X update with its stop norms)
                         runs in the GEMM's epilogue; 0: separate combine kernel (same arithmetic) */
+  int emu_pair;      /* FP64-accurate exact-slice products on pairs of SMs (256-row tiles, one MMA
+                        for both CTAs, half of the B operand staged per SM) or on one SM per 128-row
+                        tile: -1 (default) pairs for products of more than 2 * 2048^3 multiply-adds
+                        (measured: 23 % faster at 4096^3, 4 % slower at 2048^3), 1 pairs whenever
+                        M > 128, 0 never.  Same arithmetic, bit-identical results */
 } qpinv_options;
 
 typedef struct {

@@ -198,6 +198,9 @@ struct EmuGemmArgs {
 };
 bool emu_fused_ok(int K, int S);
 cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st);
+// The same product on pairs of SMs (qgemm_emu_pair.cu: 256 x 64 tiles,
+// tcgen05 cta_group::2); same arguments and result.
+cudaError_t launch_qgemm_emu_pair(const EmuGemmArgs& a, cudaStream_t st);
 bool tc_supported();
 
 // Batched solver (batched_impl.cuh: host side in batched.cu, kernels in batched_tile<t>.cu).

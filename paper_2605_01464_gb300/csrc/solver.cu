@@ -519,7 +519,10 @@ struct Solver {
       g.ps64 = (long)M * N;
       g.shift = shift;
       g.err = c->d_err;
-      timed(c, EV_EMU, flops, flops * S * (S + 1) / 2, 0, [&] { return launch_qgemm_emu(g, c->st); });
+      const bool pair = M > 128 && (c->opt.emu_pair == 1 ||
+                                    (c->opt.emu_pair == -1 && (double)M * N * K > 2.0 * 2048.0 * 2048.0 * 2048.0));
+      timed(c, EV_EMU, flops, flops * S * (S + 1) / 2, 0,
+            [&] { return pair ? launch_qgemm_emu_pair(g, c->st) : launch_qgemm_emu(g, c->st); });
       Acc r{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};
       r.p2 = g.C64b;
       return r;
@@ -1147,6 +1150,7 @@ void qpinv_default_options(qpinv_options* o) {
   o->batched_tile = -1;
   o->hyper_order = 19;
   o->fuse_epilogue = 1;
+  o->emu_pair = -1;
 }
 
 static int check_opts(const qpinv_options* o) {
@@ -1160,6 +1164,7 @@ static int check_opts(const qpinv_options* o) {
   if (o->batched_tile < -1 || o->batched_tile >= qp::BATCH_TILES) return 0;
   if (o->hyper_order < 2 || o->hyper_order > 64) return 0;
   if (o->fuse_epilogue < 0 || o->fuse_epilogue > 1) return 0;
+  if (o->emu_pair < -1 || o->emu_pair > 1) return 0;
   return 1;
 }
 

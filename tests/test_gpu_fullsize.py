@@ -134,3 +134,18 @@ def test_solve_rank_deficient_2560x2048_against_exact_pinv(ctx, method):
     assert info["status"] in ("converged", "plateau"), info
     assert info["E_rel"][0] <= 1e-10, info
     assert err <= 1e-6, (err, info)
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_qgemm_exact_slices_on_sm_pairs_full_size(ctx, products, shape):
+    """The pair kernel (256-row tiles on two SMs) at the full-size shapes:
+    several work items per cluster, partial raster groups, ragged tails;
+    equal to the one-SM kernel bit for bit and FP64-level against the oracle."""
+    A, B, Co = products[shape]
+    ctx.configure(emu_pair=True)
+    Cp = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=8).cpu().numpy()
+    ctx.configure(emu_pair=False)
+    C1 = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=8).cpu().numpy()
+    ctx.configure(emu_pair="auto")
+    assert rel(Cp, Co) <= EMU_TOL[8], rel(Cp, Co)
+    assert np.array_equal(Cp, C1)

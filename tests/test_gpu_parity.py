@@ -323,3 +323,24 @@ def test_penrose_reuses_final_residual(ctx, precision, shape):
         assert abs(info["E"][k] - E[k]) <= 1e-12 * max(E[k], 1e-300) + 1e-300, (k, info["E"], E)
     Eo, Ro = oracle.penrose(A, X.cpu().numpy())
     assert max(Ro) <= 1e-12, Ro
+
+
+@pytest.mark.parametrize("S", [2, 4, 8])
+@pytest.mark.parametrize("m,k,n", [(130, 300, 257), (200, 64, 90), (300, 1000, 40), (513, 96, 200)])
+def test_qgemm_exact_slices_on_sm_pairs(ctx, S, m, k, n):
+    """The exact-slice product on pairs of SMs (256-row tiles, one M = 256
+    MMA for both CTAs, half of B staged per CTA) against the oracle, and
+    equal bit for bit to the one-SM kernel (same slices, levels, chunks and
+    int64 sums); shapes with partial pair tiles (rows past the second CTA's
+    half) and ragged columns."""
+    A = I.gaussian_quaternion(m, k, 15)
+    B = I.gaussian_quaternion(k, n, 16)
+    ctx.configure(emu_pair=True)
+    ctx.reset_stats()
+    Cp = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=S).cpu().numpy()
+    assert ctx.stats()["emu_gemm_launches"] >= 1
+    ctx.configure(emu_pair=False)
+    C1 = ctx.qgemm(dev(A), dev(B), precision="emu", split_level=S).cpu().numpy()
+    ctx.configure(emu_pair="auto")
+    assert rel(Cp, oracle.matmul(A, B)) <= EMU_TOL[S], rel(Cp, oracle.matmul(A, B))
+    assert np.array_equal(Cp, C1)

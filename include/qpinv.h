@@ -143,6 +143,12 @@ typedef struct {
                         tile: -1 (default) pairs for products of more than 2 * 2048^3 multiply-adds
                         (measured: 23 % faster at 4096^3, 4 % slower at 2048^3), 1 pairs whenever
                         M > 128, 0 never.  Same arithmetic, bit-identical results */
+  int tc_broad;      /* BF16-split products with M, N >= 128 and one accumulator on 128-column tiles
+                        (one CTA per SM, a 512-column TMEM accumulator) or 64-column tiles (two CTAs
+                        per SM): -1 (default) 128 columns for products without a fused combine
+                        epilogue (measured 10-19 % faster; with the epilogue the one CTA per SM
+                        cancels the gain), 1 always, 0 never.  Same arithmetic, bit-identical
+                        results */
 } qpinv_options;
 
 typedef struct {

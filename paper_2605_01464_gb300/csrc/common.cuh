@@ -154,7 +154,7 @@ struct EpiArgs {
   long ld_aux[4] = {0, 0, 0, 0}, ps_aux[4] = {0, 0, 0, 0};
   double* partials = nullptr;  // 3 values per (CTA, epilogue warp): tc_partial_blocks(M, N) blocks
 };
-int tc_partial_blocks(int M, int N);
+int tc_partial_blocks(int M, int N, int broad);
 
 // Tensor-core quaternion GEMM on BF16 split operands.  acc (FP32) = sum over
 // the listed (i, j) term pairs of A_i * B_j, restricted to k in [k0, k1).
@@ -173,6 +173,8 @@ struct TcGemmArgs {
   int pair_acc[16] = {0};  // TMEM accumulator of each pair (1 only with C64: the two are summed)
   Planes<float> C;  // FP32 output
   EpiArgs epi;      // epi.nout > 0: fused combine instead of the plain store (FP32 output only)
+  int broad = -1;   // one-accumulator products with N >= 128 on 128-column tiles (one CTA per SM):
+                    // 1 always, 0 never, -1 when the epilogue is not fused
   int* err = nullptr;  // device error word (bounded-wait expiry)
 };
 cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st);

@@ -34,8 +34,8 @@ namespace qp {
 namespace {
 
 constexpr int BM = 128;  // output rows per CTA = TMEM lanes
-constexpr int BN = 64;   // quaternion output columns per CTA (per component)
-constexpr int ACC_COLS = 4 * BN;  // TMEM columns of one accumulator (four output components)
+constexpr int BN = 64;   // quaternion output columns per CTA (per component) of the 64-column shapes
+constexpr int ACC_COLS = 4 * BN;  // TMEM columns of one 64-column accumulator (four output components)
 constexpr int GROUP_M = 16;       // CTA rasterization: 16 row tiles per group share B tiles in L2
 
 // Stage shape.  BK BF16 K-elements per stage = one swizzle row of 2*BK bytes.
@@ -43,28 +43,35 @@ constexpr int GROUP_M = 16;       // CTA rasterization: 16 row tiles per group s
 //         CTA's epilogue overlaps the other's main loop (one accumulator).
 //   Deep: BK = 64 (128-byte swizzle), 96 KB per stage, one CTA per SM (two
 //         accumulators take all 512 TMEM columns).
-template <int BK_, int SWB_, int MINB_>
+//   Broad: BK = 32, 128 columns per CTA (a 512-column accumulator), three
+//         64 KB stages, one CTA per SM: twice the MMA work per operand tile
+//         read of the wide shape.
+template <int BK_, int SWB_, int MINB_, int BN_ = 64, int STAGES_ = 2>
 struct Cfg {
   static constexpr int BK = BK_;
   static constexpr int SWB = SWB_;
   static constexpr int MINB = MINB_;
-  static constexpr int STAGES = 2;
+  static constexpr int BN = BN_;
+  static constexpr int ACC = 4 * BN_;  // TMEM columns of one accumulator
+  static constexpr int STAGES = STAGES_;
   static constexpr int A_PLANE = BM * BK * 2;
   static constexpr int B_PLANE = BN * BK * 2;
   static constexpr int STAGE = 4 * (A_PLANE + B_PLANE);
   static constexpr int SMEM = STAGES * STAGE + 1024;
+  // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
 };
 using CfgWide = Cfg<32, 64, 2>;
 using CfgDeep = Cfg<64, 128, 1>;
+using CfgBroad = Cfg<32, 64, 1, 128, 3>;
 static_assert(CfgWide::SMEM * 2 <= 227 * 1024, "two wide CTAs per SM");
 static_assert(CfgDeep::SMEM * 2 > 228 * 1024, "one deep CTA per SM");
+static_assert(CfgBroad::SMEM <= 227 * 1024 && CfgBroad::ACC == 512, "one broad CTA per SM, all TMEM columns");
 constexpr int THREADS = 192;
 
 static_assert(ACC_COLS == 256, "TMEM allocations must be powers of two (256 or 512 columns)");
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
 
 struct KParams {
   int M, N;
@@ -207,7 +214,7 @@ template <class C>
 __global__ void __launch_bounds__(THREADS, C::MINB)
     k_qgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KParams P) {
   constexpr int BK = C::BK, STAGES = C::STAGES, A_PLANE_BYTES = C::A_PLANE, B_PLANE_BYTES = C::B_PLANE,
-                STAGE_BYTES = C::STAGE;
+                STAGE_BYTES = C::STAGE, BN = C::BN, ACC_COLS = C::ACC;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc;
   __shared__ uint32_t tmem_slot;
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
         const bool fresh = u < P.npairs && P.pfirst[pr];  // first K block of this accumulator
 #pragma unroll
         for (int kk = 0; kk < BK / 16; kk++)
-          qmma_k16<A_PLANE_BYTES, B_PLANE_BYTES>(dacc, BN, ad0 + kk * 2, bd0 + kk * 2, IDESC, fresh && kk == 0);
+          qmma_k16<A_PLANE_BYTES, B_PLANE_BYTES>(dacc, BN, ad0 + kk * 2, bd0 + kk * 2, C::IDESC, fresh && kk == 0);
         mma_commit(smem_u32(&bar_empty[s]));
         if (u == nunits - 1) mma_commit(smem_u32(&bar_acc));
       }
@@ -405,13 +412,13 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
     return cudaErrorInvalidValue;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM, BK)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, BN, BK)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, C::BN, BK)) return cudaErrorInvalidValue;
   static std::atomic<unsigned long long> attr_done{0};
   if (cudaError_t e = ensure_smem_attr(k_qgemm_tc<C>, C::SMEM, attr_done)) return e;
   P.kb0 = a.k0 / BK;
   P.kb1 = (a.k1 + BK - 1) / BK;
   P.Mt = (a.M + BM - 1) / BM;
-  P.Nt = (a.N + BN - 1) / BN;
+  P.Nt = (a.N + C::BN - 1) / C::BN;
   k_qgemm_tc<C><<<P.Mt * P.Nt, THREADS, C::SMEM, st>>>(mA, mB, P);
   ++g_kernel_launches;
   return cudaGetLastError();
@@ -419,7 +426,19 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
 
 }  // namespace
 
-int tc_partial_blocks(int M, int N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * 4; }
+// One-accumulator products take the broad shape (128 columns per CTA) when
+// N fills its tiles and either it is asked for (broad = 1) or (broad = -1)
+// the product has no fused epilogue: with one CTA per SM a fused combine no
+// longer overlaps another CTA's MMAs, which cancels the shape's gain
+// (measured on the 2048^2 solve), while plain products gain 10-19 %.  The
+// fused epilogue's partials follow the shape chosen.
+static bool use_broad(int broad, bool fused, int M, int N) {
+  return N >= 128 && M >= 128 && (broad == 1 || (broad == -1 && !fused));
+}
+int tc_partial_blocks(int M, int N, int broad) {
+  const int bn = use_broad(broad, true, M, N) ? CfgBroad::BN : CfgWide::BN;
+  return ((M + BM - 1) / BM) * ((N + bn - 1) / bn) * 4;
+}
 
 bool tc_supported() {
   int dev = 0;
@@ -465,7 +484,8 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   P.ps64 = a.ps64;
   P.scale = ldexpf(1.0f, a.shift);
   P.err = a.err;
-  return nacc == 2 ? launch_cfg<CfgDeep>(a, P, st) : launch_cfg<CfgWide>(a, P, st);
+  if (nacc == 2) return launch_cfg<CfgDeep>(a, P, st);
+  return use_broad(a.broad, P.E.nout > 0, a.M, a.N) ? launch_cfg<CfgBroad>(a, P, st) : launch_cfg<CfgWide>(a, P, st);
 }
 
 }  // namespace qp

@@ -356,6 +356,7 @@ struct Solver {
       g.npairs = 1;
     }
     g.err = c->d_err;
+    g.broad = c->opt.tc_broad;
     return g;
   }
 
@@ -421,7 +422,7 @@ struct Solver {
         e.ld_aux[t] = a.ld_aux[t];
         e.ps_aux[t] = a.ps_aux[t];
       }
-      const int blocks = tc_partial_blocks(M, N);
+      const int blocks = tc_partial_blocks(M, N, c->opt.tc_broad);
       if (with_partials) {
         if (blocks > partial_cap) {
           partials = (double*)buf(c, "partials", sizeof(double) * 3 * (size_t)blocks + 64);
@@ -1151,6 +1152,7 @@ void qpinv_default_options(qpinv_options* o) {
   o->hyper_order = 19;
   o->fuse_epilogue = 1;
   o->emu_pair = -1;
+  o->tc_broad = -1;
 }
 
 static int check_opts(const qpinv_options* o) {
@@ -1165,6 +1167,7 @@ static int check_opts(const qpinv_options* o) {
   if (o->hyper_order < 2 || o->hyper_order > 64) return 0;
   if (o->fuse_epilogue < 0 || o->fuse_epilogue > 1) return 0;
   if (o->emu_pair < -1 || o->emu_pair > 1) return 0;
+  if (o->tc_broad < -1 || o->tc_broad > 1) return 0;
   return 1;
 }
 

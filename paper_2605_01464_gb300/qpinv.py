@@ -36,7 +36,7 @@ class qpinv_options(ctypes.Structure):
                 ("alpha_mode", ctypes.c_int), ("alpha_user", ctypes.c_double), ("qrapid_N", ctypes.c_int),
                 ("side", ctypes.c_int), ("stop_rule", ctypes.c_int), ("penrose", ctypes.c_int),
                 ("profile", ctypes.c_int), ("batched_tile", ctypes.c_int), ("hyper_order", ctypes.c_int),
-                ("fuse_epilogue", ctypes.c_int), ("emu_pair", ctypes.c_int)]
+                ("fuse_epilogue", ctypes.c_int), ("emu_pair", ctypes.c_int), ("tc_broad", ctypes.c_int)]
 
 
 class qpinv_result(ctypes.Structure):
@@ -225,7 +225,7 @@ class Context:
 
     def configure(self, precision=None, split_level=None, polish_iters=None, alpha=None, alpha_user=None,
                   qrapid_N=None, side=None, stop=None, penrose=None, profile=None, batched_tile=None,
-                  hyper_order=None, fuse_epilogue=None, emu_pair=None, _apply=True):
+                  hyper_order=None, fuse_epilogue=None, emu_pair=None, tc_broad=None, _apply=True):
         o = self.options
         if precision is not None: o.precision = PRECISION[precision]
         if split_level is not None: o.split_level = int(split_level)
@@ -241,6 +241,7 @@ class Context:
         if hyper_order is not None: o.hyper_order = int(hyper_order)
         if fuse_epilogue is not None: o.fuse_epilogue = int(bool(fuse_epilogue))
         if emu_pair is not None: o.emu_pair = -1 if emu_pair == "auto" else int(bool(emu_pair))
+        if tc_broad is not None: o.tc_broad = -1 if tc_broad == "auto" else int(bool(tc_broad))
         if _apply:
             _check(self.h, lib().qpinv_set_options(self.h, ctypes.byref(o)), "qpinv_set_options")
 

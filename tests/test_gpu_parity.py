@@ -344,3 +344,40 @@ def test_qgemm_exact_slices_on_sm_pairs(ctx, S, m, k, n):
     ctx.configure(emu_pair="auto")
     assert rel(Cp, oracle.matmul(A, B)) <= EMU_TOL[S], rel(Cp, oracle.matmul(A, B))
     assert np.array_equal(Cp, C1)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+@pytest.mark.parametrize("m,k,n", [(128, 64, 128), (200, 130, 300), (257, 300, 129), (64, 1000, 200)])
+def test_qgemm_tc_broad_tiles(ctx, L, m, k, n):
+    """BF16-split products on 128-column tiles (one CTA per SM, a 512-column
+    accumulator) against the oracle, and equal bit for bit to the 64-column
+    tiles (same MMAs per K step into the same FP32 accumulator entries)."""
+    A = I.gaussian_quaternion(m, k, 25)
+    B = I.gaussian_quaternion(k, n, 26)
+    ctx.configure(tc_broad=True)
+    Cb = ctx.qgemm(dev(A), dev(B), precision="tc", split_level=L).cpu().numpy()
+    ctx.configure(tc_broad=False)
+    Cw = ctx.qgemm(dev(A), dev(B), precision="tc", split_level=L).cpu().numpy()
+    ctx.configure(tc_broad="auto")
+    Co = oracle.matmul(A, B)
+    tol = {1: 1e-2, 2: 3e-4}.get(L, 5e-5 * max(1.0, k / 1000.0))
+    assert rel(Cb, Co) <= tol, rel(Cb, Co)
+    assert np.array_equal(Cb, Cw)
+
+
+@pytest.mark.parametrize("method", ["qhpi19", "qsai"])
+def test_solve_tc_broad_tiles_match(ctx, method):
+    """A mixed-precision solve with the fused epilogues on 128-column tiles
+    gives the same iterates as on 64-column tiles (the stop norms' partial
+    sums are grouped differently, nothing else changes)."""
+    A, U, s, V = I.logspaced_square(256, 1e-6, seed_u=1, seed_v=2)
+    got = {}
+    for broad in (False, True):
+        ctx.configure(tc_broad=broad)
+        X, info = ctx.solve(dev(A), method, tol=1e-12, max_iter=200)
+        got[broad] = (X.cpu().numpy(), info)
+    ctx.configure(tc_broad="auto")
+    (Xw, iw), (Xb, ib) = got[False], got[True]
+    assert iw["iters"] == ib["iters"] and iw["status"] == ib["status"], (iw, ib)
+    assert rel(Xb, Xw) <= 1e-12, rel(Xb, Xw)
+    assert ib["E_rel"][0] <= 1e-10, ib

@@ -194,8 +194,7 @@ def kernel_qgemm(args, torch, qpinv):
     gms = st["%s_gemm_ms" % key]
     kname = "k_qgemm_tc"
     if key == "emu":
-        kname = "k_qgemm_emu_pair" if (args.emu_pair == "1" or (args.emu_pair == "auto" and n ** 3 > 2 * 2048 ** 3)) \
-            else "k_qgemm_emu"
+        kname = "k_qgemm_emu_pair" if args.emu_pair == "1" else "k_qgemm_emu"
     print(json.dumps({"kernel": kname, "n": n, "precision": prec,
                       "split": args.split, "launches_per_product": launches / args.steps, "ms_per_launch": gms / launches,
                       "gemm_ms_per_product": gms / args.steps,
@@ -925,7 +924,7 @@ def main():
                     help="--kernel qgemm: BF16 terms (tc: 1..3) or exact slices (emu: 2..8)")
     ap.add_argument("--gemm-precision", default="tc", choices=["tc", "emu"], help="--kernel qgemm precision")
     ap.add_argument("--emu-pair", default="auto", choices=["auto", "0", "1"],
-                    help="--kernel qgemm: exact-slice products on SM pairs (auto: for products above 2 * 2048^3)")
+                    help="--kernel qgemm: exact-slice products on SM pairs (1) or one SM (0, auto: the default)")
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "batched", "rankdef", "learned", "hyper", "cur", "filter", "krylov"],
                     help="dense: one 2048^2 solve per step; batched: 4096 pure-quaternion blocks per step; "

@@ -138,11 +138,11 @@ typedef struct {
   int fuse_epilogue; /* 1 (default): the combine pass after a BF16 tensor-core product (residual
                         R = I - A X, the polynomial blocks in R, the X update with its stop norms)
                         runs in the GEMM's epilogue; 0: separate combine kernel (same arithmetic) */
-  int emu_pair;      /* FP64-accurate exact-slice products on pairs of SMs (256-row tiles, one MMA
-                        for both CTAs, half of the B operand staged per SM) or on one SM per 128-row
-                        tile: -1 (default) pairs for products of more than 2 * 2048^3 multiply-adds
-                        (measured: 23 % faster at 4096^3, 4 % slower at 2048^3), 1 pairs whenever
-                        M > 128, 0 never.  Same arithmetic, bit-identical results */
+  int emu_pair;      /* 1: FP64-accurate exact-slice products with more than 128 rows on pairs of SMs
+                        (256 x 64 tiles, one MMA for both CTAs, half of the B operand staged per SM);
+                        0 or -1 (default): one SM per 128 x 128 tile and component pair, which was
+                        measured faster at every size (5.3 against 7.3 ms at 2048^3, 44.9 against
+                        58.3 ms at 4096^3, 8 slices).  Same arithmetic, bit-identical results */
   int tc_broad;      /* BF16-split products with M, N >= 128 and one accumulator on 128-column tiles
                         (one CTA per SM, a 512-column TMEM accumulator) or 64-column tiles (two CTAs
                         per SM): -1 (default) 128 columns for products without a fused combine

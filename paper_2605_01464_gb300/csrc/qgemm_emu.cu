@@ -9,28 +9,34 @@
 // it spans is short enough (host-chosen chunk per level); the two lowest
 // levels run over the whole K.
 //
-// A persistent grid (one CTA per SM) walks work items (tile, level group):
-// the levels are split into two groups of equal cost, each summed into its
-// own int64 accumulator, so that 2 x tiles items balance over the SMs.  For
-// each level of its item the MMA warp accumulates K-chunks into two FP32 TMEM
-// buffers in turn (256 columns each), so the tensor core fills one while the
-// eight epilogue warps drain the other (two MMA-issuing warps share each K
-// step, components 0-1 and 2-3, so that one thread's issue rate does not
-// bound the tensor core): each converts its 32 rows x 128
-// columns exactly to int32 and adds them into the level's sums, held in its
-// registers (128 per thread), then releases the buffer.  At the end of a
-// level the int32 sums are shifted to the common 64-bit fixed point and
-// added to the global int64 accumulator of the item's group (each thread its
-// own row segment, 16-byte accesses; the group's first level stores, so the
-// accumulators need no clearing).  Global traffic per product is one
-// read-modify-write of an accumulator per level instead of one per chunk, and
-// there is a single launch per product.
+// A persistent grid (one CTA per SM) walks work items (tile, component
+// pair, level group) over 128 x 128 quaternion tiles: an item computes two
+// of the four output components (0-1 or 2-3) of its tile for one of two
+// level groups of equal cost, each group summed into its own int64
+// accumulator, so that 4 x tiles items balance over the SMs.  For each level
+// of its item the MMA warps accumulate K-chunks into two FP32 TMEM buffers in
+// turn (256 columns each: the pair's two components x 128 columns), so the
+// tensor core fills one while the eight epilogue warps drain the other (one
+// MMA-issuing warp per component of the pair, so that one thread's issue
+// rate does not bound the tensor core): each epilogue warp converts its 32
+// rows x 128 columns of one component exactly to int32 and adds them into
+// the level's sums, held in its registers (128 per thread), then releases
+// the buffer.  At the end of a level the int32 sums are shifted to the
+// common 64-bit fixed point and added to the global int64 accumulator of the
+// item's group (each thread its own row segment, 16-byte accesses; the
+// group's first level stores, so the accumulators need no clearing).  Global
+// traffic per product is one read-modify-write of an accumulator per level
+// instead of one per chunk, and there is a single launch per product.
 //
-// The kernel is bound by the tensor core's shared-memory operand reads (one
-// 128 x 16 A tile and one 64 x 16 B tile per MMA of N = 64: ncu shows the
-// tensor core's shared-memory wavefronts at 1.5 times its pipe activity);
-// staging A in tensor memory with tcgen05.cp instead was measured slower
-// (10.7 against 9.2 ms for the 8-slice 2048^3 product).
+// Tile shape: every MMA of an item reads one 128 x 16 A tile and one 128 x 16
+// B tile for a 128 x 128 x 16 product; with 64-column tiles and all four
+// components per item (the earlier shape) each 128 x 64 x 16 MMA read a
+// 128 x 16 A and a 64 x 16 B tile, and the tensor core's shared-memory operand
+// reads held it at 58 % pipe activity.  A component pair reads all four A and
+// B planes per K step (each component takes every plane once), so the TMA
+// traffic per MMA work is a third higher than with four components.  Staging
+// A in tensor memory with tcgen05.cp instead was measured slower (10.7
+// against 9.2 ms for the 8-slice 2048^3 product, 64-column shape).
 //
 // int32 range: a level-d sum is bounded by 4K 2^12 (d + 3) (2^14 for d = 0)
 // level units; launch_qgemm_emu refuses K beyond what keeps this below 2^31.
@@ -44,35 +50,47 @@
 namespace qp {
 namespace {
 
-constexpr int EBM = 128, EBN = 64, EBK = 32, ESWB = 64;
-constexpr int ESTAGES = 4;
+constexpr int EBM = 128, EBN = 128, EBK = 32, ESWB = 64;
+constexpr int ESTAGES = 3;
 constexpr int EA_PLANE = EBM * EBK * 2;                    // 8 KB
-constexpr int EB_PLANE = EBN * EBK * 2;                    // 4 KB
-constexpr int ESTAGE = 4 * (EA_PLANE + EB_PLANE);          // 48 KB
+constexpr int EB_PLANE = EBN * EBK * 2;                    // 8 KB
+constexpr int ESTAGE = 4 * (EA_PLANE + EB_PLANE);          // 64 KB
 constexpr int ESMEM = ESTAGES * ESTAGE + 1024;             // + alignment slack
 constexpr int EEPI_WARPS = 8;                              // two per TMEM lane quarter
-constexpr int EMMA_WARPS = 2;                              // MMA issuers: components 0-1 and 2-3
+constexpr int EMMA_WARPS = 2;                              // MMA issuers: one per component of the item
 constexpr int EEPI0 = 1 + EMMA_WARPS;                      // first epilogue warp
 constexpr int ETHREADS = 32 * (EEPI0 + EEPI_WARPS);        // TMA warp, MMA warps, epilogue warps
 constexpr int EGROUP_M = 16;
-// TMEM columns: two FP32 chunk accumulators of 256 columns (component c at
-// c * EBN): the MMAs of chunk w fill buffer w % 2 while the epilogue drains
-// the other.
-constexpr uint32_t ECHUNK_COLS = 4 * EBN;
+// A work item computes two of the four output components (a component
+// pair) of a 128 x 128 tile.  TMEM columns: two FP32 chunk accumulators of
+// 256 columns (the pair's first component at 0, the second at EBN): the
+// MMAs of chunk w fill buffer w % 2 while the epilogue drains the other.
+constexpr uint32_t ECHUNK_COLS = 2 * EBN;
 static_assert(ESMEM <= 227 * 1024, "shared memory per CTA");
 static_assert(2 * ECHUNK_COLS == 512, "TMEM columns");
 
 constexpr uint32_t EIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EBN >> 3) << 17) |
                             ((uint32_t)(EBM >> 4) << 24);
 
+// The 4 signed MMAs of one K = 16 step that feed output component c (its
+// accumulator at d_tmem): A plane r times B plane r xor c, the sign of block
+// (r, c) of M(B) in the negate-A bit.
+__device__ __forceinline__ void qmma_k16_comp(uint32_t d_tmem, int c, uint64_t ad0, uint64_t bd0, bool fresh) {
+  constexpr uint32_t NEG_A = 1u << 13;
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+    mma_bf16(d_tmem, ad0 + ((r * EA_PLANE) >> 4), bd0 + (((r ^ c) * EB_PLANE) >> 4),
+             qsign_neg(r, c) ? EIDESC | NEG_A : EIDESC, (fresh && r == 0) ? 0u : 1u);
+}
+
 struct EParams {
   int M, N, K, S;
   int Mt, Nt;
   int kc[8];  // K chunk of each level (elements; multiple of EBK, or >= K)
-  // Work items (tile, group): the levels are split into `ngroups` groups of
-  // about equal cost (level d costs d + 1 slice pairs), each with its own
-  // int64 accumulator, so that two CTAs share a tile without atomics and the
-  // persistent grid balances (tiles x groups) items instead of whole tiles.
+  // Work items (tile, component pair, group): the levels are split into
+  // `ngroups` groups of about equal cost (level d costs d + 1 slice pairs),
+  // each with its own int64 accumulator, so that CTAs share a tile without
+  // atomics and the persistent grid balances (tiles x 2 x groups) items.
   int ngroups, items;
   int nlv[2], lv[2][8];  // levels of each group, largest first
   long long* C64g[2];
@@ -147,7 +165,7 @@ __global__ void __launch_bounds__(ETHREADS, 1)
       for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
        const int g = item % P.ngroups;
        int m0, n0;
-       tile_origin(P, item / P.ngroups, m0, n0);
+       tile_origin(P, item / (2 * P.ngroups), m0, n0);
        for (int li = 0; li < P.nlv[g] && ok; li++) {
         const int d = P.lv[g][li];
         for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d]) {
@@ -175,13 +193,14 @@ __global__ void __launch_bounds__(ETHREADS, 1)
       }
     }
   } else if (warp < EEPI0) {
-    // ---------------- MMA issuers: warp 1 components 0, 1; warp 2 components 2, 3 ----------------
+    // ---------------- MMA issuers: warp 1 the pair's first component, warp 2 its second ----------------
     if (lane == 0) {
-      const bool lo = warp == 1;
+      const int half = warp - 1;
       int u = 0, w = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
        const int g = item % P.ngroups;
+       const int c = 2 * ((item / P.ngroups) & 1) + half;  // output component of this issuer
        for (int li = 0; li < P.nlv[g] && ok; li++) {
         const int d = P.lv[g][li];
         for (int k0 = 0; k0 < P.K && ok; k0 += P.kc[d], w++) {
@@ -192,7 +211,7 @@ __global__ void __launch_bounds__(ETHREADS, 1)
             break;
           }
           fence_after();
-          const uint32_t dacc = tmem + b * ECHUNK_COLS;
+          const uint32_t dacc = tmem + b * ECHUNK_COLS + half * EBN;
           const int kb0 = k0 / EBK, kb1 = (min(P.K, k0 + P.kc[d]) + EBK - 1) / EBK;
           bool first = true;
           for (int kb = kb0; kb < kb1 && ok; kb++) {
@@ -207,12 +226,8 @@ __global__ void __launch_bounds__(ETHREADS, 1)
               const uint64_t ad0 = smem_desc_sw<ESWB>(smem_u32(sp)),
                              bd0 = smem_desc_sw<ESWB>(smem_u32(sp + 4 * EA_PLANE));
 #pragma unroll
-              for (int kk = 0; kk < EBK / 16; kk++) {
-                if (lo)
-                  qmma_k16_half<EA_PLANE, EB_PLANE, 0>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
-                else
-                  qmma_k16_half<EA_PLANE, EB_PLANE, 2>(dacc, EBN, ad0 + kk * 2, bd0 + kk * 2, EIDESC, first && kk == 0);
-              }
+              for (int kk = 0; kk < EBK / 16; kk++)
+                qmma_k16_comp(dacc, c, ad0 + kk * 2, bd0 + kk * 2, first && kk == 0);
               first = false;
               mma_commit(smem_u32(&bar_empty[st]));
             }
@@ -224,17 +239,19 @@ __global__ void __launch_bounds__(ETHREADS, 1)
     }
   } else {
     // ---------------- epilogue: exact FP32 -> int32 per chunk (registers), int64 per level ----------------
-    // Warp e = warp - EEPI0 reads TMEM lane quarter warp % 4 (its 32 rows) and the
-    // column half e / 4 (components 2h, 2h + 1): 128 int32 level sums per thread.
+    // Warp e = warp - EEPI0 reads TMEM lane quarter warp % 4 (its 32 rows) and
+    // the column half e / 4 (one component of the item's pair, 128 columns):
+    // 128 int32 level sums per thread.
     const int e = warp - EEPI0, quarter = warp & 3, half = e >> 2;
-    const uint32_t tb0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * 128;
+    const uint32_t tb0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * EBN;
     int w = 0;
     bool ok = true;
     int acc[128];
     for (int item = blockIdx.x; item < P.items && ok; item += gridDim.x) {
      const int g = item % P.ngroups;
+     const int c = 2 * ((item / P.ngroups) & 1) + half;  // this warp's output component
      int m0, n0;
-     tile_origin(P, item / P.ngroups, m0, n0);
+     tile_origin(P, item / (2 * P.ngroups), m0, n0);
      const int row = m0 + quarter * 32 + lane;
      long long* const C64 = P.C64g[g];
      for (int li = 0; li < P.nlv[g] && ok; li++) {
@@ -271,10 +288,10 @@ __global__ void __launch_bounds__(ETHREADS, 1)
         const bool last = k0 + P.kc[d] >= P.K;
         if (!last || row >= P.M) continue;
         // level done: int64 += int32 * 2^sh (rounded shift when sh < 0), this
-        // thread's row, components 2 half and 2 half + 1
+        // thread's row of component c, 128 columns
 #pragma unroll
         for (int p = 0; p < 4; p++) {
-          const int c = 2 * half + (p >> 1), j0 = n0 + (p & 1) * 32;
+          const int j0 = n0 + p * 32;
           long long* dst = C64 + c * P.ps64 + (long)row * P.ld64 + j0;
 #pragma unroll
           for (int t = 0; t < 32; t += 2) {
@@ -350,7 +367,7 @@ cudaError_t launch_qgemm_emu(const EmuGemmArgs& a, cudaStream_t st) {
   if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, EBN, EBK)) return cudaErrorInvalidValue;
   static std::atomic<unsigned long long> attr_done{0};
   if (cudaError_t e = ensure_smem_attr(k_qgemm_emu, ESMEM, attr_done)) return e;
-  P.items = P.Mt * P.Nt * P.ngroups;
+  P.items = P.Mt * P.Nt * 2 * P.ngroups;
   static int nsm[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidValue;

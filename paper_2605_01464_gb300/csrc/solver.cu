@@ -520,8 +520,7 @@ struct Solver {
       g.ps64 = (long)M * N;
       g.shift = shift;
       g.err = c->d_err;
-      const bool pair = M > 128 && (c->opt.emu_pair == 1 ||
-                                    (c->opt.emu_pair == -1 && (double)M * N * K > 2.0 * 2048.0 * 2048.0 * 2048.0));
+      const bool pair = M > 128 && c->opt.emu_pair == 1;
       timed(c, EV_EMU, flops, flops * S * (S + 1) / 2, 0,
             [&] { return pair ? launch_qgemm_emu_pair(g, c->st) : launch_qgemm_emu(g, c->st); });
       Acc r{acc, ACC_I64, (long)N, (long)M * N, eP, eQ, shift};

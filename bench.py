@@ -834,11 +834,11 @@ def bench_learned(args, torch, qpinv):
 
 # DRAM bytes (read + write) per issued tensor flop from one ncu capture of
 # the current exact-slice kernel on an 8-slice 2048^3 product
-# (profiles/k_qgemm_emu_2048_slices8.md: 11.90 GB for 36 passes); a launch's
+# (profiles/k_qgemm_emu_2048_slices8.md: 7.46 GB for 36 passes); a launch's
 # traffic is estimated as this times its issued flops.  None where no
 # capture matches the launches the solve makes (the split GEMM's launches
 # carry the fused combine epilogue, the captured one a plain store).
-TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 11.8955e9 / (36 * 32 * 2048.0 ** 3),
+TRAFFIC_PER_ISSUED_FLOP = {"k_qgemm_emu": 7.4628e9 / (36 * 32 * 2048.0 ** 3),
                            "k_qgemm_tc": None}
 
 

@@ -27,6 +27,8 @@
 // an error code, stops issuing work, drains what it started and frees TMEM.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
@@ -405,6 +407,247 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
   }
 }
 
+// Persistent shape for products with the fused combine epilogue: work items
+// (128 x 128 tile, component pair), one CTA per SM, two accumulators of 256
+// TMEM columns (the pair's two components x 128 columns) used by items in
+// turn, so the epilogue warps run the combine of one item while the MMA
+// warp accumulates the next.  Each 128 x 128 x 16 MMA reads a 128 x 16 A and
+// a 128 x 16 B tile (one operand wavefront per pipe cycle, against 1.5 for
+// the 64-column shape); an item takes all four A and B planes of a K step
+// (each output component uses every plane once).  Same MMAs per output
+// entry in the same order as the other shapes: bit-identical products.
+constexpr int CP_BN = 128, CP_BK = 32, CP_STAGES = 3;
+constexpr int CP_A_PLANE = BM * CP_BK * 2, CP_B_PLANE = CP_BN * CP_BK * 2;
+constexpr int CP_STAGE = 4 * (CP_A_PLANE + CP_B_PLANE);  // 64 KB
+constexpr int CP_STG = 4 * 1024;                         // the epilogue warps' B-form transpose tiles
+constexpr int CP_SMEM = CP_STAGES * CP_STAGE + CP_STG + 1024;
+constexpr uint32_t CP_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP_BN >> 3) << 17) |
+                              ((uint32_t)(BM >> 4) << 24);
+static_assert(CP_SMEM <= 227 * 1024, "shared memory per CTA");
+
+// The 4 signed MMAs of one K = 16 step into output component c (accumulator at d_tmem).
+__device__ __forceinline__ void qmma_k16_one(uint32_t d_tmem, int c, uint64_t ad0, uint64_t bd0, bool fresh) {
+  constexpr uint32_t NEG_A = 1u << 13;
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+    mma_bf16(d_tmem, ad0 + ((r * CP_A_PLANE) >> 4), bd0 + (((r ^ c) * CP_B_PLANE) >> 4),
+             qsign_neg(r, c) ? CP_IDESC | NEG_A : CP_IDESC, (fresh && r == 0) ? 0u : 1u);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_qgemm_tc_pairs(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_full[CP_STAGES], bar_empty[CP_STAGES], bar_acc_full[2], bar_acc_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = (P.kb1 - P.kb0) * P.npairs;  // (K block, split pair) units per item
+  const int items = P.Mt * P.Nt * 2;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < CP_STAGES; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 4);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  int issued = 0;
+
+  auto item_origin = [&](int item, int& m0, int& n0, int& c0) {
+    const int t = item >> 1;
+    c0 = 2 * (item & 1);
+    const int per_group = GROUP_M * P.Nt, group = t / per_group, local = t % per_group;
+    const int gm = min(GROUP_M, P.Mt - group * GROUP_M);
+    m0 = (group * GROUP_M + local % gm) * BM;
+    n0 = (local / gm) * CP_BN;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int u = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        int m0, n0, c0;
+        item_origin(item, m0, n0, c0);
+        for (int x = 0; x < units; x++, u++) {
+          const int s = u % CP_STAGES;
+          if (u >= CP_STAGES &&
+              !mbar_wait(smem_u32(&bar_empty[s]), ((u / CP_STAGES) - 1) & 1, &abort_flag, P.err, 41)) {
+            ok = false;
+            break;
+          }
+          const int kb = P.kb0 + x / P.npairs, pr = x % P.npairs;
+          const uint32_t fb = smem_u32(&bar_full[s]);
+          mbar_expect_tx(fb, CP_STAGE);
+          uint8_t* st = smem + (size_t)s * CP_STAGE;
+          for (int c = 0; c < 4; c++)
+            tma_load_3d(smem_u32(st + c * CP_A_PLANE), &tmA, kb * CP_BK, m0, P.pi[pr] * 4 + c, fb);
+          for (int c = 0; c < 4; c++)
+            tma_load_3d(smem_u32(st + 4 * CP_A_PLANE + c * CP_B_PLANE), &tmB, kb * CP_BK, n0, P.pj[pr] * 4 + c, fb);
+          issued = u + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one lane): both components of the item's pair ----------------
+    if (lane == 0) {
+      int u = 0, w = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x, w++) {
+        int m0, n0, c0;
+        item_origin(item, m0, n0, c0);
+        const int b = w & 1;
+        if (w >= 2 && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((w >> 1) - 1) & 1, &abort_flag, P.err, 42)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t dacc = tmem + b * 256;
+        for (int x = 0; x < units && ok; x++, u++) {
+          const int s = u % CP_STAGES;
+          if (!mbar_wait(smem_u32(&bar_full[s]), (u / CP_STAGES) & 1, &abort_flag, P.err, 43)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint8_t* st = smem + (size_t)s * CP_STAGE;
+          const uint64_t ad0 = smem_desc_sw<64>(smem_u32(st)), bd0 = smem_desc_sw<64>(smem_u32(st + 4 * CP_A_PLANE));
+          const bool fresh = x < P.npairs && P.pfirst[x % P.npairs];  // first K block of the accumulator
+#pragma unroll
+          for (int kk = 0; kk < CP_BK / 16; kk++) {
+            qmma_k16_one(dacc, c0, ad0 + kk * 2, bd0 + kk * 2, fresh && kk == 0);
+            qmma_k16_one(dacc + CP_BN, c0 + 1, ad0 + kk * 2, bd0 + kk * 2, fresh && kk == 0);
+          }
+          mma_commit(smem_u32(&bar_empty[s]));
+        }
+        if (ok) mma_commit(smem_u32(&bar_acc_full[b]));
+      }
+    }
+  } else {
+    // ---------------- epilogue: the fused combine of each item, one row per lane ----------------
+    const int quarter = warp & 3;
+    const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+    bf16* stg = reinterpret_cast<bf16*>(smem + CP_STAGES * CP_STAGE) + (warp - 2) * 512;
+    float sdx = 0.f, sx = 0.f;
+    int bad = 0;
+    int w = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x, w++) {
+      int m0, n0, c0;
+      item_origin(item, m0, n0, c0);
+      const int b = w & 1;
+      int have = 1;
+      if (units > 0) {
+        if (lane == 0) have = mbar_wait(smem_u32(&bar_acc_full[b]), (w >> 1) & 1, &abort_flag, P.err, 44) ? 1 : 0;
+        have = __shfl_sync(0xffffffffu, have, 0);
+        fence_after();
+      }
+      if (!have) break;
+      const int row0 = m0 + quarter * 32, i = row0 + lane;
+#pragma unroll 1
+      for (int h = 0; h < 2; h++) {
+#pragma unroll 1
+        for (int ch = 0; ch < CP_BN / 16; ch++) {
+          float v[16];
+          if (units > 0) {
+            tmem_ld16(tq + b * 256 + h * CP_BN + ch * 16, v);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; t++) v[t] = 0.f;
+          }
+          const int j0 = n0 + ch * 16;
+          const int nc = min(16, P.N - j0);
+          if (nc > 0) epi_piece(P.E, c0 + h, i, i < P.M, row0, P.M, j0, nc, v, stg, sdx, sx, bad);
+        }
+      }
+      // the accumulator is read: release it to the MMA warp
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty[b]));
+    }
+    if (P.E.partials) {
+      double d0 = sdx, d1 = sx, d2 = bad;
+      for (int o = 16; o > 0; o >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      }
+      if (lane == 0) {
+        double* pp = P.E.partials + 3 * ((long)blockIdx.x * 4 + quarter);
+        pp[0] = d0;
+        pp[1] = d1;
+        pp[2] = d2;
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && abort_flag) {
+    for (int u = (issued > CP_STAGES ? issued - CP_STAGES : 0); u < issued; u++)
+      (void)mbar_wait(smem_u32(&bar_full[u % CP_STAGES]), (u / CP_STAGES) & 1, &abort_flag, nullptr, 0);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+int sm_count() {
+  static int nsm[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!nsm[dev] && cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return nsm[dev];
+}
+
+// Grid of the persistent component-pair shape: one CTA per SM at most.
+int pairs_grid(int M, int N) {
+  const int items = ((M + BM - 1) / BM) * ((N + CP_BN - 1) / CP_BN) * 2;
+  return std::min(items, std::max(1, sm_count()));
+}
+
+cudaError_t launch_pairs(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
+  if ((a.k0 % CP_BK) != 0 || (a.k1 != a.K && (a.k1 % CP_BK) != 0) || a.k0 < 0 || a.k1 > a.K || a.k0 > a.k1)
+    return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.A->a, a.K, a.M, 4 * a.A->levels, a.A->lda, a.A->psa, BM, CP_BK)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.B->b, a.K, a.N, 4 * a.B->levels, a.B->ldb, a.B->psb, CP_BN, CP_BK))
+    return cudaErrorInvalidValue;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k_qgemm_tc_pairs, CP_SMEM, attr_done)) return e;
+  P.kb0 = a.k0 / CP_BK;
+  P.kb1 = (a.k1 + CP_BK - 1) / CP_BK;
+  P.Mt = (a.M + BM - 1) / BM;
+  P.Nt = (a.N + CP_BN - 1) / CP_BN;
+  const int grid = pairs_grid(a.M, a.N);
+  if (grid < 1) return cudaErrorInvalidValue;
+  k_qgemm_tc_pairs<<<grid, THREADS, CP_SMEM, st>>>(mA, mB, P);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
 template <class C>
 cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
   constexpr int BK = C::BK;
@@ -426,18 +669,26 @@ cudaError_t launch_cfg(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
 
 }  // namespace
 
-// One-accumulator products take the broad shape (128 columns per CTA) when
-// N fills its tiles and either it is asked for (broad = 1) or (broad = -1)
-// the product has no fused epilogue: with one CTA per SM a fused combine no
-// longer overlaps another CTA's MMAs, which cancels the shape's gain
-// (measured on the 2048^2 solve), while plain products gain 10-19 %.  The
-// fused epilogue's partials follow the shape chosen.
-static bool use_broad(int broad, bool fused, int M, int N) {
-  return N >= 128 && M >= 128 && (broad == 1 || (broad == -1 && !fused));
+// One-accumulator products with M, N >= 128 take a 128-column shape unless
+// broad = 0: without a fused epilogue the broad shape (one tile per CTA,
+// 128 x 128, all four components; plain products gain 10-19 %), with one
+// the persistent component-pair shape (broad = -1), whose epilogue overlaps
+// the MMAs of the CTA's next item -- the broad shape's one tile per CTA
+// would expose it (measured: no gain on the 2048^2 solve).  broad = 1 takes
+// the broad shape for both.  The fused epilogue's partials follow the shape
+// chosen: one set per (CTA, epilogue warp).
+enum TcShape { SHAPE_WIDE, SHAPE_BROAD, SHAPE_PAIRS };
+static TcShape tc_shape(int broad, bool fused, int M, int N) {
+  if (broad == 0 || N < 128 || M < 128) return SHAPE_WIDE;
+  if (broad == 1 || !fused) return SHAPE_BROAD;
+  return SHAPE_PAIRS;
 }
 int tc_partial_blocks(int M, int N, int broad) {
-  const int bn = use_broad(broad, true, M, N) ? CfgBroad::BN : CfgWide::BN;
-  return ((M + BM - 1) / BM) * ((N + bn - 1) / bn) * 4;
+  switch (tc_shape(broad, true, M, N)) {
+    case SHAPE_PAIRS: return pairs_grid(M, N) * 4;
+    case SHAPE_BROAD: return ((M + BM - 1) / BM) * ((N + CfgBroad::BN - 1) / CfgBroad::BN) * 4;
+    default: return ((M + BM - 1) / BM) * ((N + CfgWide::BN - 1) / CfgWide::BN) * 4;
+  }
 }
 
 bool tc_supported() {
@@ -485,7 +736,11 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   P.scale = ldexpf(1.0f, a.shift);
   P.err = a.err;
   if (nacc == 2) return launch_cfg<CfgDeep>(a, P, st);
-  return use_broad(a.broad, P.E.nout > 0, a.M, a.N) ? launch_cfg<CfgBroad>(a, P, st) : launch_cfg<CfgWide>(a, P, st);
+  switch (tc_shape(a.broad, P.E.nout > 0, a.M, a.N)) {
+    case SHAPE_PAIRS: return launch_pairs(a, P, st);
+    case SHAPE_BROAD: return launch_cfg<CfgBroad>(a, P, st);
+    default: return launch_cfg<CfgWide>(a, P, st);
+  }
 }
 
 }  // namespace qp

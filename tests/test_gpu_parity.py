@@ -367,17 +367,38 @@ def test_qgemm_tc_broad_tiles(ctx, L, m, k, n):
 
 @pytest.mark.parametrize("method", ["qhpi19", "qsai"])
 def test_solve_tc_broad_tiles_match(ctx, method):
-    """A mixed-precision solve with the fused epilogues on 128-column tiles
-    gives the same iterates as on 64-column tiles (the stop norms' partial
-    sums are grouped differently, nothing else changes)."""
+    """A mixed-precision solve with the fused epilogues on 64-column tiles
+    (two CTAs per SM), on the broad 128-column tiles, and on the persistent
+    component-pair items (the default for fused products) gives the same
+    iterates: the products are the same bit for bit, only the stop norms'
+    partial sums are grouped differently."""
     A, U, s, V = I.logspaced_square(256, 1e-6, seed_u=1, seed_v=2)
     got = {}
-    for broad in (False, True):
+    for broad in (False, True, "auto"):
         ctx.configure(tc_broad=broad)
+        ctx.reset_stats()
         X, info = ctx.solve(dev(A), method, tol=1e-12, max_iter=200)
+        assert ctx.stats()["fused_epilogues"] > 0
         got[broad] = (X.cpu().numpy(), info)
     ctx.configure(tc_broad="auto")
-    (Xw, iw), (Xb, ib) = got[False], got[True]
-    assert iw["iters"] == ib["iters"] and iw["status"] == ib["status"], (iw, ib)
-    assert rel(Xb, Xw) <= 1e-12, rel(Xb, Xw)
-    assert ib["E_rel"][0] <= 1e-10, ib
+    Xw, iw = got[False]
+    for key in (True, "auto"):
+        Xb, ib = got[key]
+        assert iw["iters"] == ib["iters"] and iw["status"] == ib["status"], (key, iw, ib)
+        assert rel(Xb, Xw) <= 1e-12, (key, rel(Xb, Xw))
+        assert ib["E_rel"][0] <= 1e-10, ib
+
+
+@pytest.mark.parametrize("m,k,n", [(200, 130, 300), (300, 257, 136), (640, 512, 520)])
+def test_fused_epilogue_component_pairs_match_wide(ctx, m, k, n):
+    """One Newton-Schulz step's fused residual product on the persistent
+    component-pair shape equals the 64-column shape's, bit for bit in X
+    (several items per CTA at 640 x 520: 5 x 5 tiles x 2 pairs)."""
+    A = I.gaussian_quaternion(m, n, 27)
+    out = {}
+    for broad in (False, "auto"):
+        ctx.configure(precision="tc", tc_broad=broad)
+        X, info = ctx.solve(dev(A), "ns", tol=1e-30, max_iter=2)
+        out[broad] = X.cpu().numpy()
+    ctx.configure(precision="mixed", tc_broad="auto")
+    assert np.array_equal(out[False], out["auto"])

@@ -287,6 +287,12 @@ struct Solver {
   // then reuses it instead of forming that side's product again.
   int res_cur = -1;
   QMat res_R;
+  // Exponents and exact slices of A (an operand of every residual product,
+  // constant during the solve), kept in their own buffers across products:
+  // the form (0: A-form rows, 1: B-form columns), slice count and master
+  // precision they were made for (form -1: none yet).
+  int acache_form = -1, acache_S = 0;
+  bool acache_dbl = false;
   long long gemms = 0;
   QMat A, X[2];
   int cur = 0;
@@ -446,36 +452,54 @@ struct Solver {
 
   Acc prod_emu(const QMat& P, const QMat& Q, int S, double flops) {
     const int M = P.rows, K = P.cols, N = Q.cols;
-    int* eP = (int*)buf(c, "emu.eP", sizeof(int) * (size_t)M + 64);
-    int* eQ = (int*)buf(c, "emu.eQ", sizeof(int) * (size_t)N + 64);
+    // A as an operand: its exponents and slices come from (or go to) the cache
+    const bool pA = &P == &A, qA = &Q == &A;
+    const bool pA_hit = pA && acache_form == 0 && acache_S == S && acache_dbl == dbl;
+    const bool qA_hit = qA && acache_form == 1 && acache_S == S && acache_dbl == dbl;
+    int* eP = (int*)buf(c, pA ? "emu.cacheA.e" : "emu.eP", sizeof(int) * (size_t)M + 64);
+    int* eQ = (int*)buf(c, qA ? "emu.cacheA.e" : "emu.eQ", sizeof(int) * (size_t)N + 64);
     int* eS = (int*)buf(c, "emu.eS", sizeof(int) * (size_t)COL_SCRATCH(N) + 64);
     if (dbl) {
-      timed(c, EV_EW, 0, 0, 32.0 * M * K, [&] { return launch_maxexp(dview(P), M, K, 0, eP, nullptr, c->st); });
-      timed(c, EV_EW, 0, 0, 32.0 * K * N, [&] { return launch_maxexp(dview(Q), K, N, 1, eQ, eS, c->st); });
+      if (!pA_hit)
+        timed(c, EV_EW, 0, 0, 32.0 * M * K, [&] { return launch_maxexp(dview(P), M, K, 0, eP, nullptr, c->st); });
+      if (!qA_hit)
+        timed(c, EV_EW, 0, 0, 32.0 * K * N, [&] { return launch_maxexp(dview(Q), K, N, 1, eQ, eS, c->st); });
     } else {
-      timed(c, EV_EW, 0, 0, 16.0 * M * K, [&] { return launch_maxexp_f32(fview(P), M, K, 0, eP, nullptr, c->st); });
-      timed(c, EV_EW, 0, 0, 16.0 * K * N, [&] { return launch_maxexp_f32(fview(Q), K, N, 1, eQ, eS, c->st); });
+      if (!pA_hit)
+        timed(c, EV_EW, 0, 0, 16.0 * M * K,
+              [&] { return launch_maxexp_f32(fview(P), M, K, 0, eP, nullptr, c->st); });
+      if (!qA_hit)
+        timed(c, EV_EW, 0, 0, 16.0 * K * N, [&] { return launch_maxexp_f32(fview(Q), K, N, 1, eQ, eS, c->st); });
     }
     Split16 za, zb;
     za.levels = zb.levels = S;
     za.lda = rup8(K);
     za.psa = (long)M * za.lda;
-    za.a = (bf16*)buf(c, "emu.za", sizeof(bf16) * 4 * S * (size_t)za.psa + 64);
+    za.a = (bf16*)buf(c, pA ? "emu.cacheA.z" : "emu.za", sizeof(bf16) * 4 * S * (size_t)za.psa + 64);
     zb.ldb = rup8(K);
     zb.psb = (long)N * zb.ldb;
-    zb.b = (bf16*)buf(c, "emu.zb", sizeof(bf16) * 4 * S * (size_t)zb.psb + 64);
+    zb.b = (bf16*)buf(c, qA ? "emu.cacheA.z" : "emu.zb", sizeof(bf16) * 4 * S * (size_t)zb.psb + 64);
     // the slices: P's rows (A-form), Q's columns (B-form, transposed)
     const double sbytes = 2.0 * S * 4;
     if (dbl) {
-      timed(c, EV_EW, 0, 0, (32.0 + sbytes) * M * K,
-            [&] { return launch_slice_rows(dview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
-      timed(c, EV_EW, 0, 0, (32.0 + sbytes) * K * N,
-            [&] { return launch_slice_cols(dview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
+      if (!pA_hit)
+        timed(c, EV_EW, 0, 0, (32.0 + sbytes) * M * K,
+              [&] { return launch_slice_rows(dview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
+      if (!qA_hit)
+        timed(c, EV_EW, 0, 0, (32.0 + sbytes) * K * N,
+              [&] { return launch_slice_cols(dview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
     } else {
-      timed(c, EV_EW, 0, 0, (16.0 + sbytes) * M * K,
-            [&] { return launch_slice_rows(fview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
-      timed(c, EV_EW, 0, 0, (16.0 + sbytes) * K * N,
-            [&] { return launch_slice_cols(fview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
+      if (!pA_hit)
+        timed(c, EV_EW, 0, 0, (16.0 + sbytes) * M * K,
+              [&] { return launch_slice_rows(fview(P), M, K, eP, S, za.a, za.lda, za.psa, c->st); });
+      if (!qA_hit)
+        timed(c, EV_EW, 0, 0, (16.0 + sbytes) * K * N,
+              [&] { return launch_slice_cols(fview(Q), K, N, eQ, S, zb.b, zb.ldb, zb.psb, c->st); });
+    }
+    if (pA || qA) {
+      acache_form = pA ? 0 : 1;
+      acache_S = S;
+      acache_dbl = dbl;
     }
     long long* acc = (long long*)buf(c, "emu.acc", sizeof(long long) * 4 * (size_t)M * N + 64);
     int lg = 0;

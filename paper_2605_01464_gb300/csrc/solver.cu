@@ -66,7 +66,11 @@ struct EvRec {
   int kind;
 };
 
-long rup8(long x) { return (x + 7) / 8 * 8; }
+// Row pitch of BF16 operand planes (split forms, exact slices): 64 elements,
+// 128 bytes, so that every 64-byte TMA box row lies in whole 32-byte L2
+// sectors (an odd K such as 2001 otherwise makes each row straddle one: 1.5x
+// the sectors, measured 2x slower exact-slice products at n = 2001).
+long rup64(long x) { return (x + 63) / 64 * 64; }
 
 }  // namespace
 
@@ -154,18 +158,20 @@ QMat mat(qpinv_ctx* c, const std::string& name, int rows, int cols, int masters,
     M.d.p = (double*)buf(c, name + ".d", sizeof(double) * 4 * (size_t)ps + 64);
   }
   if (masters & MST_F) {
-    M.f.ld = cols;
-    M.f.ps = ps;
-    M.f.p = (float*)buf(c, name + ".f", sizeof(float) * 4 * (size_t)ps + 64);
+    // 16-byte rows, so that the tensor-core epilogues' FP32 accesses stay
+    // vectorised for any column count
+    M.f.ld = (cols + 3) / 4 * 4;
+    M.f.ps = (long)rows * M.f.ld;
+    M.f.p = (float*)buf(c, name + ".f", sizeof(float) * 4 * (size_t)M.f.ps + 64);
   }
   M.s16.levels = levels;
   if (aform) {
-    M.s16.lda = rup8(cols);
+    M.s16.lda = rup64(cols);
     M.s16.psa = (long)rows * M.s16.lda;
     M.s16.a = (bf16*)buf(c, name + ".a16", sizeof(bf16) * 4 * levels * (size_t)M.s16.psa + 64);
   }
   if (bform) {
-    M.s16.ldb = rup8(rows);
+    M.s16.ldb = rup64(rows);
     M.s16.psb = (long)cols * M.s16.ldb;
     M.s16.b = (bf16*)buf(c, name + ".b16", sizeof(bf16) * 4 * levels * (size_t)M.s16.psb + 64);
   }
@@ -330,7 +336,7 @@ struct Solver {
       return Acc{C.p, ACC_F64, C.ld, C.ps, nullptr, nullptr, 0};
     }
     Planes<float> C;
-    C.ld = rup8(N);
+    C.ld = (N + 31) / 32 * 32;  // 128-byte FP32 rows
     C.ps = (long)M * C.ld;
     C.p = (float*)buf(c, "acc32", sizeof(float) * 4 * (size_t)C.ps + 64);
     TcGemmArgs g = tc_args(P, Q);
@@ -473,10 +479,10 @@ struct Solver {
     }
     Split16 za, zb;
     za.levels = zb.levels = S;
-    za.lda = rup8(K);
+    za.lda = rup64(K);
     za.psa = (long)M * za.lda;
     za.a = (bf16*)buf(c, pA ? "emu.cacheA.z" : "emu.za", sizeof(bf16) * 4 * S * (size_t)za.psa + 64);
-    zb.ldb = rup8(K);
+    zb.ldb = rup64(K);
     zb.psb = (long)N * zb.ldb;
     zb.b = (bf16*)buf(c, qA ? "emu.cacheA.z" : "emu.zb", sizeof(bf16) * 4 * S * (size_t)zb.psb + 64);
     // the slices: P's rows (A-form), Q's columns (B-form, transposed)

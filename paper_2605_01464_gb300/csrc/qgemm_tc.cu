@@ -419,7 +419,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB)
 constexpr int CP_BN = 128, CP_BK = 32, CP_STAGES = 3;
 constexpr int CP_A_PLANE = BM * CP_BK * 2, CP_B_PLANE = CP_BN * CP_BK * 2;
 constexpr int CP_STAGE = 4 * (CP_A_PLANE + CP_B_PLANE);  // 64 KB
-constexpr int CP_STG = 4 * 1024;                         // the epilogue warps' B-form transpose tiles
+constexpr int CP_EPI_WARPS = 8;                          // two per TMEM lane quarter: one per component
+constexpr int CP_THREADS = 32 * (2 + CP_EPI_WARPS);      // TMA warp, MMA warp, epilogue warps
+constexpr int CP_STG = CP_EPI_WARPS * 1024;              // the epilogue warps' B-form transpose tiles
 constexpr int CP_SMEM = CP_STAGES * CP_STAGE + CP_STG + 1024;
 constexpr uint32_t CP_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP_BN >> 3) << 17) |
                               ((uint32_t)(BM >> 4) << 24);
@@ -434,7 +436,7 @@ __device__ __forceinline__ void qmma_k16_one(uint32_t d_tmem, int c, uint64_t ad
              qsign_neg(r, c) ? CP_IDESC | NEG_A : CP_IDESC, (fresh && r == 0) ? 0u : 1u);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(CP_THREADS, 1)
     k_qgemm_tc_pairs(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KParams P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_full[CP_STAGES], bar_empty[CP_STAGES], bar_acc_full[2], bar_acc_empty[2];
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
-      mbar_init(smem_u32(&bar_acc_empty[b]), 4);  // one arrival per epilogue warp
+      mbar_init(smem_u32(&bar_acc_empty[b]), CP_EPI_WARPS);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -545,9 +547,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- epilogue: the fused combine of each item, one row per lane ----------------
-    const int quarter = warp & 3;
+    // warp e = warp - 2: TMEM lane quarter warp % 4, component c0 + e / 4 of the item's pair
+    const int quarter = warp & 3, e8 = warp - 2, h = e8 >> 2;
     const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
-    bf16* stg = reinterpret_cast<bf16*>(smem + CP_STAGES * CP_STAGE) + (warp - 2) * 512;
+    bf16* stg = reinterpret_cast<bf16*>(smem + CP_STAGES * CP_STAGE) + e8 * 512;
     float sdx = 0.f, sx = 0.f;
     int bad = 0;
     int w = 0;
@@ -564,20 +567,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!have) break;
       const int row0 = m0 + quarter * 32, i = row0 + lane;
 #pragma unroll 1
-      for (int h = 0; h < 2; h++) {
-#pragma unroll 1
-        for (int ch = 0; ch < CP_BN / 16; ch++) {
-          float v[16];
-          if (units > 0) {
-            tmem_ld16(tq + b * 256 + h * CP_BN + ch * 16, v);
-          } else {
+      for (int ch = 0; ch < CP_BN / 16; ch++) {
+        float v[16];
+        if (units > 0) {
+          tmem_ld16(tq + b * 256 + h * CP_BN + ch * 16, v);
+        } else {
 #pragma unroll
-            for (int t = 0; t < 16; t++) v[t] = 0.f;
-          }
-          const int j0 = n0 + ch * 16;
-          const int nc = min(16, P.N - j0);
-          if (nc > 0) epi_piece(P.E, c0 + h, i, i < P.M, row0, P.M, j0, nc, v, stg, sdx, sx, bad);
+          for (int t = 0; t < 16; t++) v[t] = 0.f;
         }
+        const int j0 = n0 + ch * 16;
+        const int nc = min(16, P.N - j0);
+        if (nc > 0) epi_piece(P.E, c0 + h, i, i < P.M, row0, P.M, j0, nc, v, stg, sdx, sx, bad);
       }
       // the accumulator is read: release it to the MMA warp
       fence_before();
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         d2 += __shfl_xor_sync(0xffffffffu, d2, o);
       }
       if (lane == 0) {
-        double* pp = P.E.partials + 3 * ((long)blockIdx.x * 4 + quarter);
+        double* pp = P.E.partials + 3 * ((long)blockIdx.x * CP_EPI_WARPS + e8);
         pp[0] = d0;
         pp[1] = d1;
         pp[2] = d2;
@@ -643,7 +643,7 @@ cudaError_t launch_pairs(const TcGemmArgs& a, KParams& P, cudaStream_t st) {
   P.Nt = (a.N + CP_BN - 1) / CP_BN;
   const int grid = pairs_grid(a.M, a.N);
   if (grid < 1) return cudaErrorInvalidValue;
-  k_qgemm_tc_pairs<<<grid, THREADS, CP_SMEM, st>>>(mA, mB, P);
+  k_qgemm_tc_pairs<<<grid, CP_THREADS, CP_SMEM, st>>>(mA, mB, P);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -685,7 +685,7 @@ static TcShape tc_shape(int broad, bool fused, int M, int N) {
 }
 int tc_partial_blocks(int M, int N, int broad) {
   switch (tc_shape(broad, true, M, N)) {
-    case SHAPE_PAIRS: return pairs_grid(M, N) * 4;
+    case SHAPE_PAIRS: return pairs_grid(M, N) * CP_EPI_WARPS;
     case SHAPE_BROAD: return ((M + BM - 1) / BM) * ((N + CfgBroad::BN - 1) / CfgBroad::BN) * 4;
     default: return ((M + BM - 1) / BM) * ((N + CfgWide::BN - 1) / CfgWide::BN) * 4;
   }

@@ -129,30 +129,33 @@ cudaError_t launch_qgemm_f64(int M, int K, int N, const Planes<const double>& A,
                              const Planes<const double>& B, const Planes<double>& C,
                              cudaStream_t st);
 
-// Combine pass fused into the epilogue of the tensor-core GEMM (FP32 phase):
-// the product never goes to HBM; each output o is
+// Combine pass fused into the epilogue of the tensor-core GEMM: the product
+// never goes to HBM; each output o is
 //   out_o = cacc * (A B) + sum_t caux[t] * aux_t + diag * I   (diag on plane s)
-// written as an FP32 master and/or round-to-nearest BF16 splits (A-form
-// row-major, B-form transposed), with the stop-test partials of output 0
-// (||out0 - aux0||^2, ||out0||^2, non-finite count) per (CTA, epilogue warp).
+// evaluated in the master type (FP32, or FP64 with f64 = 1) and written as a
+// master and/or round-to-nearest BF16 splits of its FP32 rounding (A-form
+// row-major, B-form transposed); in the FP32 case optionally with the
+// stop-test partials of output 0 (||out0 - aux0||^2, ||out0||^2, non-finite
+// count) per (CTA, epilogue warp).
 // Outputs must not alias the product's operand forms (other CTAs are still
 // reading them); an output may alias an aux plane (same element, same thread).
 struct EpiOut {
-  float* mp = nullptr;  // FP32 master planes (may be null)
+  void* mp = nullptr;  // master planes, float (double when EpiArgs::f64); may be null
   long mld = 0, mps = 0;
   bf16* a = nullptr;  // A-form splits [level][comp][rows][lda] (may be null)
   long lda = 0, psa = 0;
   bf16* b = nullptr;  // B-form splits [level][comp][cols][ldb] (may be null)
   long ldb = 0, psb = 0;
   int levels = 0;
-  float cacc = 0.f, caux[4] = {0.f, 0.f, 0.f, 0.f}, diag = 0.f;
+  double cacc = 0.0, caux[4] = {0, 0, 0, 0}, diag = 0.0;  // rounded to the master type at use
 };
 struct EpiArgs {
   int nout = 0;  // 0: plain FP32 store of the product into TcGemmArgs::C
   EpiOut out[kMaxOut];
-  const float* aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  const void* aux[4] = {nullptr, nullptr, nullptr, nullptr};  // planes of the master type
   long ld_aux[4] = {0, 0, 0, 0}, ps_aux[4] = {0, 0, 0, 0};
-  double* partials = nullptr;  // 3 values per (CTA, epilogue warp): tc_partial_blocks(M, N) blocks
+  double* partials = nullptr;  // 3 values per (CTA, epilogue warp): tc_partial_blocks(M, N) blocks (f64 == 0 only)
+  int f64 = 0;  // 1: aux inputs and output masters are double planes (FP64 arithmetic in the epilogue)
 };
 int tc_partial_blocks(int M, int N, int broad);
 

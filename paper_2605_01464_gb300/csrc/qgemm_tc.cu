@@ -99,28 +99,42 @@ __device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<u
 // same for the whole warp); rok = row i exists (the whole warp calls this:
 // the transposed B-form goes through `stg`, this warp's 16 x 32 BF16 block
 // of shared memory, so that each lane writes 16-byte pieces of B-form rows).
-__device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool rok, int row0, int M, int j0, int nc,
-                                          const float* v, bf16* stg, float& sdx, float& sx, int& bad) {
+// T is the master type of the aux inputs and the output masters (float, or
+// double when E.f64: the combine's arithmetic then runs in FP64 and the split
+// forms are taken from the FP32 rounding of the result, as in the combine
+// kernel).
+template <typename T>
+__device__ __forceinline__ void epi_piece_t(const EpiArgs& E, int c, int i, bool rok, int row0, int M, int j0, int nc,
+                                            const float* v, bf16* stg, float& sdx, float& sx, int& bad) {
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int o = 0; o < E.nout; o++) {
     const EpiOut& O = E.out[o];
-    float w[16];
+    T w[16];
+    const T cacc = (T)O.cacc;
 #pragma unroll
-    for (int t = 0; t < 16; t++) w[t] = O.cacc != 0.f ? O.cacc * v[t] : 0.f;
+    for (int t = 0; t < 16; t++)  // +-1 as a sign flip (the combine kernel's arithmetic)
+      w[t] = cacc == (T)0 ? (T)0 : cacc == (T)1 ? (T)v[t] : cacc == (T)-1 ? -(T)v[t] : cacc * (T)v[t];
 #pragma unroll 1
     for (int a = 0; a < 4; a++) {
-      if (!rok || !E.aux[a] || O.caux[a] == 0.f) continue;
-      const float* ap = E.aux[a] + c * E.ps_aux[a] + (long)i * E.ld_aux[a] + j0;
-      const float ca = O.caux[a];
-      if (nc == 16 && al16(ap)) {
+      if (!rok || !E.aux[a] || O.caux[a] == 0.0) continue;
+      const T* ap = reinterpret_cast<const T*>(E.aux[a]) + c * E.ps_aux[a] + (long)i * E.ld_aux[a] + j0;
+      const T ca = (T)O.caux[a];
+      if (sizeof(T) == 4 && nc == 16 && al16(ap)) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          const float4 u = reinterpret_cast<const float4*>(ap)[q];
+          const float4 u = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(ap))[q];
           w[4 * q] += ca * u.x;
           w[4 * q + 1] += ca * u.y;
           w[4 * q + 2] += ca * u.z;
           w[4 * q + 3] += ca * u.w;
+        }
+      } else if (sizeof(T) == 8 && nc == 16 && al16(ap)) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const double2 u = reinterpret_cast<const double2*>(reinterpret_cast<const double*>(ap))[q];
+          w[2 * q] += ca * u.x;
+          w[2 * q + 1] += ca * u.y;
         }
       } else {
 #pragma unroll
@@ -128,28 +142,35 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool r
           if (t < nc) w[t] += ca * ap[t];
       }
     }
-    if (c == 0 && O.diag != 0.f) {
+    if (c == 0 && O.diag != 0.0) {
 #pragma unroll
       for (int t = 0; t < 16; t++)
-        if (i == j0 + t) w[t] += O.diag;
+        if (i == j0 + t) w[t] += (T)O.diag;
     }
     if (o == 0 && E.partials && rok) {
-      const float* xp = E.aux[0] ? E.aux[0] + c * E.ps_aux[0] + (long)i * E.ld_aux[0] + j0 : nullptr;
+      const T* xp = E.aux[0] ? reinterpret_cast<const T*>(E.aux[0]) + c * E.ps_aux[0] + (long)i * E.ld_aux[0] + j0
+                             : nullptr;
 #pragma unroll
       for (int t = 0; t < 16; t++)
         if (t < nc) {
-          const float x0 = xp ? xp[t] : 0.f;
-          sdx += (w[t] - x0) * (w[t] - x0);
-          sx += w[t] * w[t];
+          const float x0 = xp ? (float)(w[t] - xp[t]) : (float)w[t];
+          sdx += x0 * x0;
+          sx += (float)w[t] * (float)w[t];
           bad += isfinite(w[t]) ? 0 : 1;
         }
     }
     if (O.mp && rok) {
-      float* dst = O.mp + c * O.mps + (long)i * O.mld + j0;
-      if (nc == 16 && al16(dst)) {
+      T* dst = reinterpret_cast<T*>(O.mp) + c * O.mps + (long)i * O.mld + j0;
+      if (sizeof(T) == 4 && nc == 16 && al16(dst)) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
-          reinterpret_cast<float4*>(dst)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          reinterpret_cast<float4*>(reinterpret_cast<float*>(dst))[q] =
+              make_float4((float)w[4 * q], (float)w[4 * q + 1], (float)w[4 * q + 2], (float)w[4 * q + 3]);
+      } else if (sizeof(T) == 8 && nc == 16 && al16(dst)) {
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          reinterpret_cast<double2*>(reinterpret_cast<double*>(dst))[q] =
+              make_double2((double)w[2 * q], (double)w[2 * q + 1]);
       } else {
 #pragma unroll
         for (int t = 0; t < 16; t++)
@@ -159,7 +180,7 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool r
     if (O.a || O.b) {
       float r[16];
 #pragma unroll
-      for (int t = 0; t < 16; t++) r[t] = w[t];
+      for (int t = 0; t < 16; t++) r[t] = (float)w[t];
 #pragma unroll 1
       for (int l = 0; l < O.levels; l++) {
         bf16 h[16];
@@ -210,6 +231,14 @@ __device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool r
       }
     }
   }
+}
+
+__device__ __forceinline__ void epi_piece(const EpiArgs& E, int c, int i, bool rok, int row0, int M, int j0, int nc,
+                                          const float* v, bf16* stg, float& sdx, float& sx, int& bad) {
+  if (E.f64)
+    epi_piece_t<double>(E, c, i, rok, row0, M, j0, nc, v, stg, sdx, sx, bad);
+  else
+    epi_piece_t<float>(E, c, i, rok, row0, M, j0, nc, v, stg, sdx, sx, bad);
 }
 
 template <class C>
@@ -729,7 +758,8 @@ cudaError_t launch_qgemm_tc(const TcGemmArgs& a, cudaStream_t st) {
   P.nacc = nacc;
   P.C = a.C;
   P.E = a.epi;
-  if (P.E.nout < 0 || P.E.nout > kMaxOut || (P.E.nout > 0 && (a.C64 || nacc == 2))) return cudaErrorInvalidValue;
+  if (P.E.nout < 0 || P.E.nout > kMaxOut || (P.E.nout > 0 && (a.C64 || nacc == 2)) || (P.E.f64 && P.E.partials))
+    return cudaErrorInvalidValue;
   P.C64 = a.C64;
   P.ld64 = a.ld64;
   P.ps64 = a.ps64;

@@ -384,11 +384,12 @@ struct Solver {
   }
 
   // Whether the combine pass `a` (no accumulator set yet) can run in the
-  // epilogue of the tensor-core product P Q: FP32 phase, round-to-nearest
-  // splits only, and no output that overwrites an operand form the product
-  // is still reading.
-  bool epi_fusable(const CombineArgs& a, const QMat& P, const QMat& Q) const {
-    if (!c->opt.fuse_epilogue || dbl || a.f64 || a.acc || a.nout < 1 || a.nout > kMaxOut) return false;
+  // epilogue of the tensor-core product P Q: round-to-nearest splits only, no
+  // output that overwrites an operand form the product is still reading, and
+  // in the FP64 phase no stop-test partials (those norms stay FP64 sums).
+  bool epi_fusable(const CombineArgs& a, const QMat& P, const QMat& Q, bool with_partials) const {
+    if (!c->opt.fuse_epilogue || a.acc || a.nout < 1 || a.nout > kMaxOut) return false;
+    if (a.f64 != (dbl ? 1 : 0) || (dbl && with_partials)) return false;
     for (int o = 0; o < a.nout; o++) {
       const OutSpec& O = a.out[o];
       if (O.exp_a || O.exp_b) return false;
@@ -405,7 +406,7 @@ struct Solver {
   // possible, else the product and the combine kernel.
   void prod_run(const QMat& P, const QMat& Q, int mode, CombineArgs a, bool with_partials = false,
                 int red_slot = 0) {
-    if (mode == PM_TC && epi_fusable(a, P, Q)) {
+    if (mode == PM_TC && epi_fusable(a, P, Q, with_partials)) {
       const int M = P.rows, K = P.cols, N = Q.cols;
       gemms++;
       const double flops = 32.0 * M * (double)K * N;
@@ -415,7 +416,7 @@ struct Solver {
       for (int o = 0; o < a.nout; o++) {
         const OutSpec& O = a.out[o];
         EpiOut& d = e.out[o];
-        d.mp = (float*)O.mp;
+        d.mp = O.mp;
         d.mld = O.mld;
         d.mps = O.mps;
         d.a = O.s16.a;
@@ -425,12 +426,13 @@ struct Solver {
         d.ldb = O.s16.ldb;
         d.psb = O.s16.psb;
         d.levels = O.s16.levels;
-        d.cacc = (float)O.cacc;
-        for (int t = 0; t < 4; t++) d.caux[t] = (float)O.caux[t];
-        d.diag = (float)O.diag;
+        d.cacc = O.cacc;
+        for (int t = 0; t < 4; t++) d.caux[t] = O.caux[t];
+        d.diag = O.diag;
       }
+      e.f64 = a.f64;
       for (int t = 0; t < 4; t++) {
-        e.aux[t] = (const float*)a.aux[t];
+        e.aux[t] = a.aux[t];
         e.ld_aux[t] = a.ld_aux[t];
         e.ps_aux[t] = a.ps_aux[t];
       }

@@ -302,6 +302,36 @@ def test_fused_epilogue_matches_separate_combine(ctx, method, N):
     assert rel(X1, Xo) <= 1e-5
 
 
+@pytest.mark.parametrize("case", ["logspaced256", "gaussian200x136"])
+def test_fused_epilogue_fp64_polish(ctx, case):
+    """In the FP64 polish steps of the mixed schedule the BF16 R-products
+    take their combine pass (FP64 arithmetic on FP64 masters) in the GEMM's
+    epilogue: fewer tensor-core products run unfused than the five R-products
+    of each QHPI19 polish step, and X equals the separate combine's result up
+    to the FMA contraction of two compilations (ragged tiles at 200 x 136)."""
+    if case == "logspaced256":
+        A, U, s, V = I.logspaced_square(256, 1e-6, seed_u=1, seed_v=2)
+        want = oracle.pinv_from_svd(U, s, V)
+    else:
+        A = I.gaussian_quaternion(200, 136, 17)
+        want = None
+    runs = {}
+    for fuse in (True, False):
+        ctx.configure(precision="mixed", fuse_epilogue=fuse)
+        ctx.reset_stats()
+        X, info = ctx.solve(dev(A), "qhpi19", tol=1e-12, max_iter=200)
+        runs[fuse] = (X.cpu().numpy(), info, ctx.stats())
+    ctx.configure(precision="mixed", fuse_epilogue=True)
+    (X1, i1, s1), (X2, i2, s2) = runs[True], runs[False]
+    assert i1["tc_iters"] == i2["tc_iters"] > 0 and i1["polish_iters"] == i2["polish_iters"] > 0, (i1, i2)
+    assert s2["fused_epilogues"] == 0, s2
+    assert s1["tc_gemm_launches"] - s1["fused_epilogues"] < 5 * i1["polish_iters"], (s1, i1)
+    assert i1["E_rel"][0] <= 1e-10 and i2["E_rel"][0] <= 1e-10, (i1, i2)
+    assert rel(X1, X2) <= 1e-9, rel(X1, X2)
+    if want is not None:
+        assert rel(X1, want) <= 1e-8, rel(X1, want)
+
+
 @pytest.mark.parametrize("precision", ["emu", "fp64"])
 @pytest.mark.parametrize("shape", [(96, 64), (64, 96)])
 def test_penrose_reuses_final_residual(ctx, precision, shape):

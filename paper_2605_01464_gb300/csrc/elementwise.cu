@@ -35,6 +35,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0 only
 }
 
+// Inf / NaN from the exponent bits (integer instructions: GB300's FP64 pipe
+// is the scarce resource in these passes).
+__device__ __forceinline__ int nonfinite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF ? 1 : 0;
+}
+__device__ __forceinline__ int nonfinite_bits(float x) { return ((__float_as_int(x) >> 23) & 0xFF) == 0xFF ? 1 : 0; }
+
 // Round-to-nearest BF16 split of the FP32 value: 3 terms cover all 24 bits.
 __device__ __forceinline__ void split_store(bf16* base, long idx, long lstride, int levels, float v) {
   float r = v;
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs a) {
               const T dx = v[c] - x0p[c * a.ps_aux[0] + (long)i * a.ld_aux[0] + j];
               s_dx += dx * dx;
             }
-            s_bad += isfinite(v[c]) ? 0 : 1;
+            s_bad += nonfinite_bits(v[c]);
           }
         }
         if (O.mp)
@@ -548,22 +555,32 @@ __global__ void k_max(const double* v, int n, double* out) {
 }
 
 // partials per block: sum |A - B|^2 (or |A|^2 if B is null), non-finite count of A.
-__global__ void k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m, int n,
-                       double* partials) {
+// ||A - B||_F^2 (B optional) and the non-finite count of A.  Work is split
+// into tasks of one row and FRO_COLS consecutive columns (a block takes tasks
+// blockIdx.x, blockIdx.x + gridDim.x, ...); per element four FP64 FMAs (and
+// four subtractions with B), nothing else on the FP64 pipe.
+constexpr int FRO_COLS = 256;
+__global__ void __launch_bounds__(FRO_COLS) k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m,
+                                                   int n, double* partials) {
   __shared__ double sh[8];
-  const long total = (long)m * n;
-  double s = 0.0, bad = 0.0;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-    const long i = t / n, j = t % n;
-    for (int c = 0; c < 4; c++) {
-      double x = A.p[c * A.ps + i * A.ld + j];
-      bad += isfinite(x) ? 0.0 : 1.0;
-      if (hasB) x -= B.p[c * B.ps + i * B.ld + j];
-      s += x * x;
+  const long chunks = (n + FRO_COLS - 1) / FRO_COLS, tasks = (long)m * chunks;
+  double s = 0.0;
+  int bad = 0;
+  for (long t = blockIdx.x; t < tasks; t += gridDim.x) {
+    const long i = t / chunks;
+    const int j = (int)(t - i * chunks) * FRO_COLS + threadIdx.x;
+    if (j < n) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        double x = A.p[c * A.ps + i * A.ld + j];
+        bad += nonfinite_bits(x);
+        if (hasB) x -= B.p[c * B.ps + i * B.ld + j];
+        s = fma(x, x, s);
+      }
     }
   }
   const double t0 = block_sum(s, sh);
-  const double t1 = block_sum(bad, sh);
+  const double t1 = block_sum((double)bad, sh);
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = t0;
     partials[2 * blockIdx.x + 1] = t1;
@@ -745,13 +762,12 @@ cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st) {
 
 cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m, int n,
                                  double* partials, cudaStream_t st, int* blocks_out) {
-  const long total = (long)m * n;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 1024) blocks = 1024;
+  const long tasks = (long)m * ((n + FRO_COLS - 1) / FRO_COLS);
+  int blocks = (int)(tasks < 1024 ? tasks : 1024);
   if (blocks < 1) blocks = 1;
   *blocks_out = blocks;
   Planes<const double> Bz = B ? *B : Planes<const double>();
-  k_fro2<<<blocks, 256, 0, st>>>(A, Bz, B ? 1 : 0, m, n, partials);
+  k_fro2<<<blocks, FRO_COLS, 0, st>>>(A, Bz, B ? 1 : 0, m, n, partials);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

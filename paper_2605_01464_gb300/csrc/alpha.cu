@@ -135,12 +135,68 @@ __global__ void k_lanczos_next(const float* w, float* q, float* qprev, const dou
   qprev[t] = q[t];
   q[t] = w[t] * inv;
 }
-// v = y / sqrt(d2[0]) (0 when the norm vanishes)
-__global__ void k_normalize(const float* y, float* v, const double* d2, int len) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= len) return;
-  const double b2 = d2[0];
-  v[t] = b2 > 1e-60 ? y[t] * (float)(1.0 / sqrt(b2)) : 0.f;
+// One power-iteration step: y = M v with v = yprev / ||yprev|| (v = yprev on
+// the first step, d2prev null; 0 when the norm vanishes), and d2[0] = ||y||^2.
+// One warp per row; each block writes the sum of its rows' squares to
+// part[blockIdx.x], and the last block to finish (counted in *count, which it
+// resets) adds the block sums in block order, so the result does not depend
+// on the blocks' timing.
+constexpr int PW_ROWS = 8;
+__global__ void __launch_bounds__(32 * PW_ROWS) k_power_step(Planes<const float> M, int s, const float* yprev,
+                                                             const double* d2prev, float* y, double* part,
+                                                             unsigned int* count, double* d2) {
+  __shared__ double wsum[PW_ROWS];
+  __shared__ int last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * PW_ROWS + warp;
+  float inv = 1.f;
+  if (d2prev) {
+    const double b2 = d2prev[0];
+    inv = b2 > 1e-60 ? (float)(1.0 / sqrt(b2)) : 0.f;
+  }
+  double rs = 0.0;
+  if (row < s) {
+    float acc[4] = {0, 0, 0, 0};
+    const float* mr = M.p + (long)row * M.ld;
+#pragma unroll 4
+    for (int j = lane; j < s; j += 32) {
+      float a[4], b[4];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        a[c] = mr[c * M.ps + j];
+        b[c] = yprev[4 * j + c] * inv;
+      }
+      acc[0] += a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+      acc[1] += a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+      acc[2] += a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+      acc[3] += a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0)
+      for (int c = 0; c < 4; c++) {
+        y[4 * row + c] = acc[c];
+        rs += (double)acc[c] * acc[c];
+      }
+  }
+  if (lane == 0) wsum[warp] = rs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < PW_ROWS; w++) t += wsum[w];
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) t += reinterpret_cast<volatile const double*>(part)[b];
+    d2[0] = t;
+    *count = 0;
+  }
 }
 
 // ------------------------------------------------------------ MLP kernels
@@ -372,15 +428,21 @@ cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fr
   return cudaSuccess;
 }
 
+int power_radius_doubles(int s, int steps) { return steps + (s + PW_ROWS - 1) / PW_ROWS + 1; }
+
 // Spectral radius of a square quaternion matrix M (FP32 planes, s x s) by
 // power iteration v <- M v / ||M v|| from the features' start vector: the
 // geometric mean of the last four norms ||M v_k|| (a complex-conjugate
 // dominant pair makes single norms oscillate).  Scratch: 8 s floats and
-// `steps` doubles; one host synchronisation.
+// power_radius_doubles(s, steps) doubles; one launch per step, one host
+// synchronisation.
 cudaError_t power_radius(const Planes<const float>& M, int s, int steps, float* scratch, double* dscratch,
                          double* pin, cudaStream_t st, double* rho) {
   float* v = scratch;
   float* y = v + 4 * s;
+  const int blocks = (s + PW_ROWS - 1) / PW_ROWS;
+  double* part = dscratch + steps;
+  unsigned int* count = reinterpret_cast<unsigned int*>(part + blocks);
   std::vector<float> hv(4 * (size_t)s);
   double nrm = 0.0;
   for (int i = 0; i < 4 * s; i++) {
@@ -390,13 +452,12 @@ cudaError_t power_radius(const Planes<const float>& M, int s, int steps, float* 
   for (int i = 0; i < 4 * s; i++) hv[i] = (float)(hv[i] / std::sqrt(nrm));
   cudaError_t e;
   if ((e = cudaMemcpyAsync(v, hv.data(), sizeof(float) * 4 * s, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-  const int len = 4 * s, tb = 256, gb = (len + tb - 1) / tb;
-  for (int k = 0; k < steps; k++) {
-    k_gemv<<<(s * 32 + 255) / 256, 256, 0, st>>>(M, s, s, v, y);
-    k_dot<<<1, 256, 0, st>>>(y, y, len, dscratch + k);
-    k_normalize<<<gb, tb, 0, st>>>(y, v, dscratch + k, len);
-  }
-  g_kernel_launches += 3 * steps;
+  if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+  float* buf2[2] = {v, y};
+  for (int k = 0; k < steps; k++)
+    k_power_step<<<blocks, 32 * PW_ROWS, 0, st>>>(M, s, buf2[k & 1], k ? dscratch + k - 1 : nullptr,
+                                                    buf2[(k + 1) & 1], part, count, dscratch + k);
+  g_kernel_launches += steps;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(pin, dscratch, sizeof(double) * steps, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return e;

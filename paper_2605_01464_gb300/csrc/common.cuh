@@ -96,8 +96,11 @@ cudaError_t launch_abs_sums(const Planes<const double>& A, int m, int n, double*
 cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st);
 // scratch entries of a column reduction over `cols` columns
 inline long COL_SCRATCH(long cols) { return 64 * cols; }
+// Partials (sum of squares, non-finite count of A) of ||scale A + diag I - B||_F^2
+// (B optional; diag on plane s only): 2 doubles per block, *blocks_out blocks.
 cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m,
-                                 int n, double* partials, cudaStream_t st, int* blocks_out);
+                                 int n, double* partials, cudaStream_t st, int* blocks_out, double scale = 1.0,
+                                 double diag = 0.0);
 cudaError_t launch_antiherm_partials(const Planes<const double>& M, int n, double* partials,
                                      cudaStream_t st, int* blocks_out);
 cudaError_t launch_init_x0(const Planes<const double>& A, int m, int n, double alpha, const Planes<double>& X,
@@ -253,6 +256,7 @@ size_t batched_tc_slot_bytes();  // slice scratch of one tensor-core engine slot
 int alpha_nweights();
 int alpha_ntrain();
 int alpha_feature_scratch_floats(int m, int n);
+int power_radius_doubles(int s, int steps);  // dscratch entries of power_radius
 cudaError_t power_radius(const Planes<const float>& M, int s, int steps, float* scratch, double* dscratch,
                          double* pin, cudaStream_t st, double* rho);
 cudaError_t alpha_features(const Planes<const float>& A, int m, int n, double fro2, double norm1, double norminf,

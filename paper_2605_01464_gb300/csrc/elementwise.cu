@@ -555,13 +555,14 @@ __global__ void k_max(const double* v, int n, double* out) {
 }
 
 // partials per block: sum |A - B|^2 (or |A|^2 if B is null), non-finite count of A.
-// ||A - B||_F^2 (B optional) and the non-finite count of A.  Work is split
-// into tasks of one row and FRO_COLS consecutive columns (a block takes tasks
-// blockIdx.x, blockIdx.x + gridDim.x, ...); per element four FP64 FMAs (and
-// four subtractions with B), nothing else on the FP64 pipe.
+// ||scale A + diag I - B||_F^2 (B optional; diag on plane s) and the
+// non-finite count of A.  Work is split into tasks of one row and FRO_COLS
+// consecutive columns (a block takes tasks blockIdx.x, blockIdx.x +
+// gridDim.x, ...); per element four FP64 FMAs (and the scaling and the
+// subtraction of B where asked), nothing else on the FP64 pipe.
 constexpr int FRO_COLS = 256;
 __global__ void __launch_bounds__(FRO_COLS) k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m,
-                                                   int n, double* partials) {
+                                                   int n, double scale, double diag, double* partials) {
   __shared__ double sh[8];
   const long chunks = (n + FRO_COLS - 1) / FRO_COLS, tasks = (long)m * chunks;
   double s = 0.0;
@@ -574,6 +575,8 @@ __global__ void __launch_bounds__(FRO_COLS) k_fro2(Planes<const double> A, Plane
       for (int c = 0; c < 4; c++) {
         double x = A.p[c * A.ps + i * A.ld + j];
         bad += nonfinite_bits(x);
+        if (scale != 1.0) x *= scale;
+        if (c == 0 && i == j && diag != 0.0) x += diag;
         if (hasB) x -= B.p[c * B.ps + i * B.ld + j];
         s = fma(x, x, s);
       }
@@ -761,13 +764,13 @@ cudaError_t launch_max(const double* v, int n, double* out, cudaStream_t st) {
 }
 
 cudaError_t launch_fro2_partials(const Planes<const double>& A, const Planes<const double>* B, int m, int n,
-                                 double* partials, cudaStream_t st, int* blocks_out) {
+                                 double* partials, cudaStream_t st, int* blocks_out, double scale, double diag) {
   const long tasks = (long)m * ((n + FRO_COLS - 1) / FRO_COLS);
   int blocks = (int)(tasks < 1024 ? tasks : 1024);
   if (blocks < 1) blocks = 1;
   *blocks_out = blocks;
   Planes<const double> Bz = B ? *B : Planes<const double>();
-  k_fro2<<<blocks, FRO_COLS, 0, st>>>(A, Bz, B ? 1 : 0, m, n, partials);
+  k_fro2<<<blocks, FRO_COLS, 0, st>>>(A, Bz, B ? 1 : 0, m, n, scale, diag, partials);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

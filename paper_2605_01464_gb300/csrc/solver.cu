@@ -1011,13 +1011,14 @@ void store_planes(qpinv_ctx* c, const QMat& src, double* const dst[4], long ld, 
   }
 }
 
+// ||scale P + diag I - Q||_F^2 (Q optional; diag on plane s).
 double fro2(qpinv_ctx* c, const Planes<const double>& P, const Planes<const double>* Q, int rows, int cols,
-            double* bad = nullptr) {
+            double* bad = nullptr, double scale = 1.0, double diag = 0.0) {
   int blocks = 0;
   double* part = (double*)buf(c, "fro_part", sizeof(double) * 2 * 1024 + 64);
   double* red = (double*)buf(c, "fro_red", sizeof(double) * 4);
   timed(c, EV_EW, 0, 0, (double)rows * cols * 32 * (Q ? 2 : 1),
-        [&] { return launch_fro2_partials(P, Q, rows, cols, part, c->st, &blocks); });
+        [&] { return launch_fro2_partials(P, Q, rows, cols, part, c->st, &blocks, scale, diag); });
   timed(c, EV_EW, 0, 0, 16.0 * blocks, [&] { return launch_reduce_partials(part, blocks, 2, red, c->st); });
   double h[2];
   read_back(c, red, 2, h);
@@ -1099,20 +1100,11 @@ void penrose(qpinv_ctx* c, const QMat& A, const QMat& X, int mode, double* E, do
   if (gemms) *gemms += S.gemms;
   E[2] = std::sqrt(antiherm2(c, Rr));
   E[3] = std::sqrt(antiherm2(c, Rl));
-  // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from AX = sr Rr + I instead
-  QMat AX = mat(c, "pAX", m, m, MST_D, false, false), XA = mat(c, "pXA", n, n, MST_D, false, false);
-  {
-    CombineArgs t = S.base_args(m, m, nullptr);
-    S.aux(t, 0, Rr);
-    S.out(t, AX, "f", 0.0, 1.0).caux[0] = sr;
-    S.run(t);
-    CombineArgs u = S.base_args(n, n, nullptr);
-    S.aux(u, 0, Rl);
-    S.out(u, XA, "f", 0.0, 1.0).caux[0] = sl;
-    S.run(u);
-  }
-  const double nr[4] = {fa, fx, std::sqrt(fro2(c, dview(AX), nullptr, m, m)),
-                        std::sqrt(fro2(c, dview(XA), nullptr, n, n))};
+  // ||AX||_F^2 = ||Rr||^2 + 2 Re tr(Rr) + m: computed directly from
+  // AX = sr Rr + I instead (each element formed in registers, as a combine
+  // pass would store it), and XA = sl Rl + I likewise
+  const double nr[4] = {fa, fx, std::sqrt(fro2(c, dview(Rr), nullptr, m, m, nullptr, sr, 1.0)),
+                        std::sqrt(fro2(c, dview(Rl), nullptr, n, n, nullptr, sl, 1.0))};
   for (int t = 0; t < 4; t++) Er[t] = nr[t] > 0 ? E[t] / nr[t] : E[t];
 }
 
@@ -1135,7 +1127,7 @@ void features_of(qpinv_ctx* c, const QMat& A, double fro2, double n1, double nin
 double spec_radius_est(qpinv_ctx* c, const QMat& M) {
   const int steps = 24;
   float* sc = (float*)buf(c, "rho.v", sizeof(float) * 8 * (size_t)M.rows + 256);
-  double* ds = (double*)buf(c, "rho.d", sizeof(double) * steps);
+  double* ds = (double*)buf(c, "rho.d", sizeof(double) * power_radius_doubles(M.rows, steps));
   double rho = 0.0;
   const long long before = g_kernel_launches;
   ck(c, power_radius(fview(M), M.rows, steps, sc, ds, c->h_pin, c->st, &rho), "spectral radius estimate");

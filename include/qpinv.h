@@ -412,8 +412,7 @@ int qpinv_penrose(qpinv_ctx* ctx, void* stream, int m, int n, const double* cons
  *   - Runs on the caller's current device and on `stream`; synchronous: it
  *     reads the kernel's error word into host memory and waits for `stream`
  *     before it returns.
- *   - The first call on each device looks up the array's device address; make
- *     that first call before any stream capture.
+ *   - The first call on each device looks up the array's device address.
  *   - Every call shares the one array: calls whose work may overlap on the GPU
  *     (other streams, unsynchronised host threads) race and must be
  *     serialised by the caller. */

@@ -15,7 +15,7 @@
 // Set-up: the host cannot use the array's name as a device address (in host
 // code it is only a stand-in).  The first call on each device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches
-// it; make that first call before any stream capture.
+// it.
 //
 // Each call is synchronous: it reads the kernel's error word back into host
 // memory and waits for its stream before it returns.

@@ -139,8 +139,8 @@ __global__ void k_lanczos_next(const float* w, float* q, float* qprev, const dou
 // the first step, d2prev null; 0 when the norm vanishes), and d2[0] = ||y||^2.
 // One warp per row; each block writes the sum of its rows' squares to
 // part[blockIdx.x], and the last block to finish (counted in *count, which it
-// resets) adds the block sums in block order, so the result does not depend
-// on the blocks' timing.
+// resets) adds the block sums in a fixed order, so the result does not
+// depend on the blocks' timing.
 constexpr int PW_ROWS = 8;
 __global__ void __launch_bounds__(32 * PW_ROWS) k_power_step(Planes<const float> M, int s, const float* yprev,
                                                              const double* d2prev, float* y, double* part,
@@ -190,12 +190,19 @@ __global__ void __launch_bounds__(32 * PW_ROWS) k_power_step(Planes<const float>
     last = atomicAdd(count, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {  // the whole block: strided sums, then a fixed shuffle and warp order
     __threadfence();
     double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++) t += reinterpret_cast<volatile const double*>(part)[b];
-    d2[0] = t;
-    *count = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) wsum[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < PW_ROWS; w++) r += wsum[w];
+      d2[0] = r;
+      *count = 0;
+    }
   }
 }
 

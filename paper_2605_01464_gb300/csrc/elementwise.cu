@@ -557,28 +557,42 @@ __global__ void k_max(const double* v, int n, double* out) {
 // partials per block: sum |A - B|^2 (or |A|^2 if B is null), non-finite count of A.
 // ||scale A + diag I - B||_F^2 (B optional; diag on plane s) and the
 // non-finite count of A.  Work is split into tasks of one row and FRO_COLS
-// consecutive columns (a block takes tasks blockIdx.x, blockIdx.x +
-// gridDim.x, ...); per element four FP64 FMAs (and the scaling and the
-// subtraction of B where asked), nothing else on the FP64 pipe.
-constexpr int FRO_COLS = 256;
+// consecutive columns; a block takes tasks blockIdx.x + k gridDim.x, FRO_U of
+// them at a time with all their loads issued before the first use (bytes in
+// flight, not the FP64 pipe, bound this pass).  Per element four FP64 FMAs
+// (and the scaling and the subtraction of B where asked).
+constexpr int FRO_COLS = 256, FRO_U = 2;
 __global__ void __launch_bounds__(FRO_COLS) k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m,
                                                    int n, double scale, double diag, double* partials) {
   __shared__ double sh[8];
   const long chunks = (n + FRO_COLS - 1) / FRO_COLS, tasks = (long)m * chunks;
   double s = 0.0;
   int bad = 0;
-  for (long t = blockIdx.x; t < tasks; t += gridDim.x) {
-    const long i = t / chunks;
-    const int j = (int)(t - i * chunks) * FRO_COLS + threadIdx.x;
-    if (j < n) {
+  for (long t0 = blockIdx.x; t0 < tasks; t0 += (long)FRO_U * gridDim.x) {
+    double x[FRO_U][4];
+    long ii[FRO_U];
+    int jj[FRO_U];
+    bool ok[FRO_U];
+#pragma unroll
+    for (int u = 0; u < FRO_U; u++) {
+      const long t = t0 + (long)u * gridDim.x;
+      ii[u] = t / chunks;
+      jj[u] = (int)(t - ii[u] * chunks) * FRO_COLS + threadIdx.x;
+      ok[u] = t < tasks && jj[u] < n;
+#pragma unroll
+      for (int c = 0; c < 4; c++) x[u][c] = ok[u] ? A.p[c * A.ps + ii[u] * A.ld + jj[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < FRO_U; u++) {
+      if (!ok[u]) continue;
 #pragma unroll
       for (int c = 0; c < 4; c++) {
-        double x = A.p[c * A.ps + i * A.ld + j];
-        bad += nonfinite_bits(x);
-        if (scale != 1.0) x *= scale;
-        if (c == 0 && i == j && diag != 0.0) x += diag;
-        if (hasB) x -= B.p[c * B.ps + i * B.ld + j];
-        s = fma(x, x, s);
+        double v = x[u][c];
+        bad += nonfinite_bits(v);
+        if (scale != 1.0) v *= scale;
+        if (c == 0 && ii[u] == jj[u] && diag != 0.0) v += diag;
+        if (hasB) v -= B.p[c * B.ps + ii[u] * B.ld + jj[u]];
+        s = fma(v, v, s);
       }
     }
   }

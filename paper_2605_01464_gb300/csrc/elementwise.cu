@@ -558,9 +558,9 @@ __global__ void k_max(const double* v, int n, double* out) {
 // ||scale A + diag I - B||_F^2 (B optional; diag on plane s) and the
 // non-finite count of A.  Work is split into tasks of one row and FRO_COLS
 // consecutive columns; a block takes tasks blockIdx.x + k gridDim.x, FRO_U of
-// them at a time with all their loads issued before the first use (bytes in
-// flight, not the FP64 pipe, bound this pass).  Per element four FP64 FMAs
-// (and the scaling and the subtraction of B where asked).
+// them at a time with all their loads of A issued before the first use.  Per
+// element four FP64 FMAs (and the scaling and the subtraction of B where
+// asked).
 constexpr int FRO_COLS = 256, FRO_U = 2;
 __global__ void __launch_bounds__(FRO_COLS) k_fro2(Planes<const double> A, Planes<const double> B, int hasB, int m,
                                                    int n, double scale, double diag, double* partials) {

@@ -70,3 +70,33 @@ def test_invalid_options_rejected():
     h = ctypes.c_void_p()
     rc = qpinv.lib().qpinv_init(ctypes.byref(h), 0, ctypes.byref(o))
     assert rc in (-1, -2)  # invalid (or no device, checked first)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors in the binding have the size and field offsets of
+    the structs include/qpinv.h declares, as a C compiler lays them out."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = [qpinv.qpinv_options, qpinv.qpinv_result, qpinv.qpinv_stats, qpinv.qpinv_cur_result,
+               qpinv.qpinv_krylov_result]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "qpinv.h"', "int main(void) {"]
+    for S in mirrors:
+        name = S.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in S._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for S in mirrors:
+        name = S.__name__
+        assert int(got[name]) == ctypes.sizeof(S), name
+        for field, _ in S._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(S, field).offset, (name, field)

@@ -137,7 +137,9 @@ typedef struct {
                         k = 1, X_{j+1} = X_j, makes no progress and is rejected) */
   int fuse_epilogue; /* 1 (default): the combine pass after a BF16 tensor-core product (residual
                         R = I - A X, the polynomial blocks in R, the X update with its stop norms)
-                        runs in the GEMM's epilogue; 0: separate combine kernel (same arithmetic) */
+                        runs in the GEMM's epilogue, on FP32 masters and, in the FP64 polish
+                        steps, on FP64 masters (passes that carry FP64 stop norms excepted);
+                        0: separate combine kernel (same arithmetic) */
   int emu_pair;      /* 1: FP64-accurate exact-slice products with more than 128 rows on pairs of SMs
                         (256 x 64 tiles, one MMA for both CTAs, half of the B operand staged per SM);
                         0 or -1 (default): one SM per 128 x 128 tile and component pair, which was
